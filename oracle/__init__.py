@@ -1,0 +1,243 @@
+"""CPU oracle for the ZeroCheck prover (test infrastructure only).
+
+Plain, slow reference implementation of both ZeroCheck forms of the paper
+(Fig. side-by-side-zc): the SumCheck prover and verifier (Sec. 3.3, 3.4) and
+the NTT prover and verifier (Sec. 3.2).  The arithmetic lives in
+``zc_oracle.c``; this module only builds it with gcc and marshals arguments
+through ctypes.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA
+library and does not import it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "zc_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+GATE_PLONK = 1
+GATE_PRODUCT = 2
+
+
+def build(force: bool = False) -> str:
+    """Compile zc_oracle.c into a shared library (gcc, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=gnu11",
+                    "-o", tmp, _SRC], check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB_PATH)
+            u32, sz, p = ctypes.c_uint32, ctypes.c_size_t, ctypes.c_void_p
+            L.zo_prove_sumcheck.argtypes = [u32, u32, u32, p, p, p, sz, ctypes.POINTER(sz), p, p]
+            L.zo_verify_sumcheck.argtypes = [u32, u32, u32, p, p, p, sz, ctypes.POINTER(ctypes.c_int)]
+            L.zo_prove_ntt.argtypes = [u32, u32, u32, u32, p, p, p, sz, ctypes.POINTER(sz), p]
+            L.zo_verify_ntt.argtypes = [u32, u32, u32, p, p, p, sz, p, ctypes.POINTER(ctypes.c_int)]
+            L.zo_proof_size.argtypes = [u32, u32, u32, u32, ctypes.POINTER(sz)]
+            L.zo_fr.argtypes = [ctypes.c_int, p, p, p]
+            L.zo_root_of_unity.argtypes = [u32, p]
+            L.zo_sha256.argtypes = [p, sz, p]
+            L.zo_root.argtypes = [p, sz, p]
+            L.zo_ntt.argtypes = [p, u32, ctypes.c_int, p]
+            L.zo_coset_lde.argtypes = [p, u32, u32, p]
+            L.zo_transcript_demo.argtypes = [u32, u32, u32, u32, u32, p, sz, p]
+            _lib = L
+    return _lib
+
+
+def _buf(x) -> np.ndarray:
+    a = np.ascontiguousarray(np.frombuffer(x, dtype=np.uint8) if isinstance(x, (bytes, bytearray)) else x)
+    return a.view(np.uint8).reshape(-1)
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+class _Cols:
+    """Keeps the column buffers alive and exposes a ``const uint8_t*[]``."""
+
+    def __init__(self, cols):
+        self.arrs = [_buf(c) for c in cols]
+        self.ptrs = (ctypes.c_void_p * len(self.arrs))(*[_ptr(a) for a in self.arrs])
+
+    @property
+    def p(self):
+        return ctypes.cast(self.ptrs, ctypes.c_void_p)
+
+
+def _roots_buf(roots):
+    if roots is None:
+        return None, None
+    b = np.frombuffer(b"".join(bytes(r) for r in roots), dtype=np.uint8).copy()
+    return b, _ptr(b)
+
+
+def ncols(gate: int, d: int) -> int:
+    return 8 if gate == GATE_PLONK else d + 1
+
+
+def proof_size(form: int, gate: int, n: int, d: int) -> int:
+    out = ctypes.c_size_t()
+    if lib().zo_proof_size(form, gate, n, d, ctypes.byref(out)) != 0:
+        raise ValueError("bad gate/degree")
+    return out.value
+
+
+def prove_sumcheck(gate, n, d, cols, roots=None, with_challenges=False):
+    """SumCheck ZeroCheck proof bytes (and r, alpha as canonical bytes)."""
+    C = _Cols(cols)
+    rb, rp = _roots_buf(roots)
+    cap = proof_size(1, gate, n, d)
+    proof = np.zeros(cap, np.uint8)
+    ln = ctypes.c_size_t()
+    r_out = np.zeros(32 * n, np.uint8)
+    a_out = np.zeros(32 * n, np.uint8)
+    st = lib().zo_prove_sumcheck(gate, n, d, C.p, rp, _ptr(proof), cap, ctypes.byref(ln),
+                                 _ptr(r_out), _ptr(a_out))
+    if st != 0:
+        raise ValueError(f"oracle prove_sumcheck status {st}")
+    pb = proof.tobytes()[: ln.value]
+    if with_challenges:
+        return pb, [r_out[32 * i:32 * i + 32].tobytes() for i in range(n)], \
+            [a_out[32 * i:32 * i + 32].tobytes() for i in range(n)]
+    return pb
+
+
+def verify_sumcheck(gate, n, d, cols, proof, roots=None) -> bool:
+    C = _Cols(cols)
+    rb, rp = _roots_buf(roots)
+    pr = _buf(proof)
+    acc = ctypes.c_int(0)
+    st = lib().zo_verify_sumcheck(gate, n, d, C.p, rp, _ptr(pr), pr.size, ctypes.byref(acc))
+    if st != 0:
+        return False
+    return bool(acc.value)
+
+
+def prove_ntt(gate, n, d, cols, roots=None, log_blowup=0):
+    """NTT ZeroCheck proof bytes and the quotient q (canonical, M*32 bytes)."""
+    C = _Cols(cols)
+    rb, rp = _roots_buf(roots)
+    lb = log_blowup or (max(d, 1) - 1).bit_length()
+    M = 1 << (n + lb)
+    cap = proof_size(2, gate, n, d)
+    proof = np.zeros(cap, np.uint8)
+    q = np.zeros(M * 32, np.uint8)
+    ln = ctypes.c_size_t()
+    st = lib().zo_prove_ntt(gate, n, d, lb, C.p, rp, _ptr(proof), cap, ctypes.byref(ln), _ptr(q))
+    if st != 0:
+        raise ValueError(f"oracle prove_ntt status {st}")
+    return proof.tobytes()[: ln.value], q
+
+
+def verify_ntt(gate, n, d, cols, proof, q, roots=None) -> bool:
+    C = _Cols(cols)
+    rb, rp = _roots_buf(roots)
+    pr = _buf(proof)
+    qb = _buf(q)
+    acc = ctypes.c_int(0)
+    st = lib().zo_verify_ntt(gate, n, d, C.p, rp, _ptr(pr), pr.size, _ptr(qb), ctypes.byref(acc))
+    if st != 0:
+        return False
+    return bool(acc.value)
+
+
+# ---- hooks used by the pin tests (canonical integers in and out) ----
+
+def _to32(x: int) -> np.ndarray:
+    return np.frombuffer(int(x).to_bytes(32, "little"), dtype=np.uint8).copy()
+
+
+def _from32(a) -> int:
+    return int.from_bytes(bytes(a), "little")
+
+
+def fr(op: str, a: int, b: int | None = None) -> int:
+    code = {"add": 0, "sub": 1, "mul": 2, "inv": 3, "neg": 4}[op]
+    A = _to32(a)
+    B = _to32(b) if b is not None else None
+    out = np.zeros(32, np.uint8)
+    st = lib().zo_fr(code, _ptr(A), _ptr(B) if B is not None else None, _ptr(out))
+    if st != 0:
+        raise ValueError("oracle field op rejected input")
+    return _from32(out)
+
+
+def root_of_unity(logn: int) -> int:
+    out = np.zeros(32, np.uint8)
+    if lib().zo_root_of_unity(logn, _ptr(out)) != 0:
+        raise ValueError
+    return _from32(out)
+
+
+def sha256(msg: bytes) -> bytes:
+    m = np.frombuffer(bytes(msg) or b"\0", dtype=np.uint8).copy()
+    out = np.zeros(32, np.uint8)
+    lib().zo_sha256(_ptr(m), len(msg), _ptr(out))
+    return out.tobytes()
+
+
+def root(v) -> bytes:
+    a = _buf(v)
+    out = np.zeros(32, np.uint8)
+    if lib().zo_root(_ptr(a), a.size // 32, _ptr(out)) != 0:
+        raise ValueError("root needs a power-of-two length")
+    return out.tobytes()
+
+
+def ints_to_bytes(xs) -> np.ndarray:
+    return np.frombuffer(b"".join(int(x).to_bytes(32, "little") for x in xs), dtype=np.uint8).copy()
+
+
+def bytes_to_ints(b) -> list[int]:
+    b = bytes(_buf(b))
+    return [int.from_bytes(b[i:i + 32], "little") for i in range(0, len(b), 32)]
+
+
+def ntt(values, logn: int, inverse: bool = False) -> list[int]:
+    a = ints_to_bytes(values)
+    out = np.zeros_like(a)
+    if lib().zo_ntt(_ptr(a), logn, 1 if inverse else 0, _ptr(out)) != 0:
+        raise ValueError
+    return bytes_to_ints(out)
+
+
+def coset_lde(coeffs, n: int, logm: int) -> list[int]:
+    a = ints_to_bytes(coeffs)
+    out = np.zeros(32 << logm, np.uint8)
+    if lib().zo_coset_lde(_ptr(a), n, logm, _ptr(out)) != 0:
+        raise ValueError
+    return bytes_to_ints(out)
+
+
+def transcript_demo(form, gate, n, d, logm, msg: bytes) -> int:
+    m = np.frombuffer(bytes(msg) or b"\0", dtype=np.uint8).copy()
+    out = np.zeros(32, np.uint8)
+    lib().zo_transcript_demo(form, gate, n, d, logm, _ptr(m), len(msg), _ptr(out))
+    return _from32(out)
+
+
+def num_threads() -> int:
+    return int(lib().zo_num_threads())

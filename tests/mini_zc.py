@@ -1,0 +1,209 @@
+"""Independent big-integer restatement of the ZeroCheck definitions, used to pin
+the oracle on tiny inputs.
+
+Everything here follows the mathematical definitions directly and shares
+nothing with ``oracle/`` or the CUDA library: Python integers for the field,
+``hashlib`` for SHA-256, O(N^2) DFTs, schoolbook polynomial products and long
+division for the quotient (Sec. 3.2), and MLE evaluation by its interpolation
+formula f~(x) = sum_b f(b) eq_x(b) (Sec. 3.3) for the SumCheck round
+polynomials, with no folding.  Exponential or quadratic cost: tiny n only.
+"""
+from __future__ import annotations
+
+import hashlib
+import itertools
+import math
+
+R = 0x73eda753299d7d483339d80809a1d80553bda402fffe5bfeffffffff00000001
+TAG = b"zerocheck-gb300/v1"
+
+
+def inv(x):
+    return pow(x, R - 2, R)
+
+
+def omega(logn):
+    return pow(pow(7, (R - 1) >> 32, R), 1 << (32 - logn), R)
+
+
+def ints(buf) -> list[int]:
+    b = bytes(buf)
+    return [int.from_bytes(b[i:i + 32], "little") for i in range(0, len(b), 32)]
+
+
+def enc(x) -> bytes:
+    return int(x % R).to_bytes(32, "little")
+
+
+def sha(m: bytes) -> bytes:
+    return hashlib.sha256(m).digest()
+
+
+def merkle_root(vals) -> bytes:
+    L = len(vals)
+    assert L & (L - 1) == 0
+    per = min(L, 64)
+    nodes = [sha(b"".join(enc(v) for v in vals[i:i + per])) for i in range(0, L, per)]
+    while len(nodes) > 1:
+        nodes = [sha(nodes[2 * i] + nodes[2 * i + 1]) for i in range(len(nodes) // 2)]
+    return sha(L.to_bytes(8, "little") + nodes[0])
+
+
+class Transcript:
+    def __init__(self, form, gate, n, d, logm):
+        self.s = sha(TAG + b"".join(x.to_bytes(4, "little") for x in (form, gate, n, d, logm)))
+
+    def absorb(self, m: bytes):
+        self.s = sha(self.s + m)
+
+    def squeeze(self) -> int:
+        self.s = sha(self.s + b"\x43")
+        return int.from_bytes(self.s, "little") % R
+
+
+def gate_eval(gate, d, x):
+    if gate == 1:
+        qL, qR, qM, qO, qC, a, b, c = x
+        return (qL * a + qR * b + qM * a * b + qO * c + qC) % R
+    return (math.prod(x[:d]) - x[d]) % R
+
+
+# ---------------------------------------------------------------- MLE ---
+
+def eq(x, b):
+    """eq_x(b) = prod_i ((1-b_i)(1-x_i) + b_i x_i)"""
+    p = 1
+    for xi, bi in zip(x, b):
+        p = p * ((1 - bi) * (1 - xi) + bi * xi) % R
+    return p
+
+
+def bits_msb(k, n):
+    return [(k >> (n - 1 - i)) & 1 for i in range(n)]
+
+
+def mle(table, x):
+    """f~(x) = sum_b f(b) eq_x(b); b_1 is the most significant index bit."""
+    n = len(x)
+    return sum(table[k] * eq(x, bits_msb(k, n)) for k in range(1 << n)) % R
+
+
+def sumcheck_round_poly(gate, d, cols, r, alphas, i, t):
+    """G_i(t) = sum over x_{i+1..n} of f_M(a, t, x) eq_r(a, t, x)  (Fig. side-by-side-zc)."""
+    n = len(r)
+    tot = 0
+    for rest in itertools.product((0, 1), repeat=n - i - 1):
+        pt = list(alphas[:i]) + [t] + list(rest)
+        vals = [mle(c, pt) for c in cols]
+        tot += gate_eval(gate, d, vals) * eq(r, pt)
+    return tot % R
+
+
+def prove_sumcheck(gate, n, d, cols_int):
+    c = len(cols_int)
+    tr = Transcript(1, gate, n, d, 0)
+    for col in cols_int:
+        tr.absorb(merkle_root(col))
+    r = [tr.squeeze() for _ in range(n)]
+    out = b"ZCS1" + b"".join(x.to_bytes(4, "little") for x in (gate, n, d))
+    alphas = []
+    for i in range(n):
+        G = [sumcheck_round_poly(gate, d, cols_int, r, alphas, i, t) for t in range(d + 2)]
+        msg = b"".join(enc(g) for g in G)
+        out += msg
+        tr.absorb(msg)
+        alphas.append(tr.squeeze())
+    for col in cols_int:
+        out += enc(mle(col, alphas))
+    return out, r, alphas
+
+
+# ---------------------------------------------------------------- NTT ---
+
+def dft(a, w):
+    N = len(a)
+    return [sum(a[k] * pow(w, i * k, R) for k in range(N)) % R for i in range(N)]
+
+
+def interpolate_h(evals):
+    """coefficients of the degree < N polynomial with g(w_N^i) = evals[i]"""
+    N = len(evals)
+    w = omega(N.bit_length() - 1)
+    ninv = inv(N)
+    return [x * ninv % R for x in dft(evals, inv(w))]
+
+
+def horner(coef, x):
+    acc = 0
+    for cf in reversed(coef):
+        acc = (acc * x + cf) % R
+    return acc
+
+
+def pmul(a, b):
+    out = [0] * (len(a) + len(b) - 1)
+    for i, x in enumerate(a):
+        if x:
+            for j, y in enumerate(b):
+                out[i + j] = (out[i + j] + x * y) % R
+    return out
+
+
+def padd(a, b):
+    n = max(len(a), len(b))
+    return [((a[i] if i < len(a) else 0) + (b[i] if i < len(b) else 0)) % R for i in range(n)]
+
+
+def gate_poly(gate, d, polys):
+    if gate == 1:
+        qL, qR, qM, qO, qC, a, b, c = polys
+        f = padd(pmul(qL, a), pmul(qR, b))
+        f = padd(f, pmul(pmul(qM, a), b))
+        f = padd(f, pmul(qO, c))
+        return padd(f, qC)
+    f = polys[0]
+    for p in polys[1:d]:
+        f = pmul(f, p)
+    return padd(f, [(-x) % R for x in polys[d]])
+
+
+def divide_by_zh(f, N):
+    """long division of f by x^N - 1: returns (quotient, remainder)"""
+    f = list(f)
+    if len(f) <= N:
+        return [0], f
+    q = [0] * (len(f) - N)
+    for k in range(len(f) - 1, N - 1, -1):
+        cf = f[k]
+        if cf:
+            q[k - N] = cf
+            f[k] = 0
+            f[k - N] = (f[k - N] + cf) % R
+    return q, f[:N]
+
+
+def prove_ntt(gate, n, d, cols_int, logb=None):
+    N = 1 << n
+    if logb is None:
+        logb = (d - 1).bit_length()
+    logm = n + logb
+    M = 1 << logm
+    coefs = [interpolate_h(c) for c in cols_int]
+    f = gate_poly(gate, d, coefs)
+    q, rem = divide_by_zh(f, N)
+    assert all(x == 0 for x in rem), "witness does not vanish on H"
+    q = (q + [0] * M)[:M]
+    qroot = merkle_root(q)
+    tr = Transcript(2, gate, n, d, logm)
+    for col in cols_int:
+        tr.absorb(merkle_root(col))
+    tr.absorb(qroot)
+    while True:
+        z = tr.squeeze()
+        if pow(z, N, R) != 1:
+            break
+    out = b"ZCN1" + b"".join(x.to_bytes(4, "little") for x in (gate, n, d, logm)) + qroot
+    for cf in coefs:
+        out += enc(horner(cf, z))
+    out += enc(horner(q, z))
+    return out, q, z
