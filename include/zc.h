@@ -1,0 +1,157 @@
+/*
+ * zc.h -- C ABI of the ZeroCheck prover library (libzc.so).
+ *
+ * The library proves the ZeroCheck claim "f vanishes on the domain" in the
+ * two forms compared by the paper "When Proofs Meet Hardware: Comparing NTT
+ * and SumCheck in Zero-Knowledge Systems" (Fig. side-by-side-zc):
+ *   - SumCheck form (multilinear ZeroCheck, Sec. 3.3, Eq. multilinear_zc_sc):
+ *     sum_x f_M(x) eq_r(x) = 0 over {0,1}^n, proved in n Fiat-Shamir rounds;
+ *   - NTT form (univariate ZeroCheck, Sec. 3.2): z_H | f, proved by the
+ *     quotient q = f / z_H computed with INTT_H, a coset NTT over D, pointwise
+ *     gate evaluation, division by z_H and INTT_D.
+ * The field is the BLS12-381 scalar field
+ *   r = 0x73eda753299d7d483339d80809a1d80553bda402fffe5bfeffffffff00000001.
+ *
+ * Data layout at the ABI.  A column is N = 2^n field elements, each 32 bytes,
+ * the canonical integer in [0, r) as little-endian bytes, in natural order:
+ * element i of a column is the value of the witness polynomial at the i-th
+ * point of the domain (omega_N^i for the NTT form, the hypercube point whose
+ * binary expansion is i, x_1 = most significant bit, for the SumCheck form).
+ * Columns are passed as an array of c pointers.  Gates and column orders:
+ *   ZC_GATE_PLONK   (d = 3, c = 8): [qL, qR, qM, qO, qC, a, b, c],
+ *                   f = qL a + qR b + qM a b + qO c + qC;
+ *   ZC_GATE_PRODUCT (d >= 2, c = d + 1): [q, w1, ..., w_{d-1}, o],
+ *                   f = q w1 ... w_{d-1} - o.
+ *
+ * Ownership.  The caller owns every buffer it passes.  A context owns the
+ * device scratch memory, constant tables and streams it creates, and reuses
+ * them across calls; zc_destroy frees them.
+ *
+ * Errors.  No call throws; every call returns a zc_status.  On failure the
+ * context keeps a message readable with zc_last_error.  A proof that does
+ * not verify is reported as ZC_OK with *accept = 0; a malformed proof or
+ * argument is ZC_ERR_ARG.  Column values >= r are rejected (ZC_ERR_ARG),
+ * checked on the device.
+ *
+ * Threading.  Calls on one context are serialised by an internal mutex; use
+ * one context per stream for concurrent proving.
+ *
+ * Proof byte formats (all integers little-endian):
+ *   SumCheck: "ZCS1" | u32 gate | u32 n | u32 d | G_i(t) for i = 1..n,
+ *             t = 0..d+1 | v_j = the columns' MLEs at alpha, j = 1..c.
+ *             Size 16 + 32 (n (d + 2) + c).
+ *   NTT:      "ZCN1" | u32 gate | u32 n | u32 d | u32 log2 M | root(q) |
+ *             g_j(z), j = 1..c | q(z).  Size 20 + 32 + 32 (c + 1).
+ * Transcript: S0 = SHA-256("zerocheck-gb300/v1" | u32 form | u32 gate |
+ * u32 n | u32 d | u32 log2 M (0 for SumCheck)); absorb(m): S = SHA-256(S|m);
+ * squeeze: S = SHA-256(S | 0x43), challenge = int_le(S) mod r.  The column
+ * and quotient commitments are stood in by root(v): a binary SHA-256 Merkle
+ * tree over leaves of 64 canonical elements, root = SHA-256(u64 len | top).
+ */
+#ifndef ZC_H
+#define ZC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ZC_OK = 0,
+  ZC_ERR_ARG = 1,              /* bad argument, value >= r, malformed proof */
+  ZC_ERR_OOM = 2,              /* device or host allocation failed / over budget */
+  ZC_ERR_CUDA = 3,             /* a CUDA runtime call failed */
+  ZC_ERR_TIMEOUT = 4,          /* a bounded device wait gave up */
+  ZC_ERR_UNSUPPORTED = 5,      /* size or degree outside what the context was set up for */
+  ZC_ERR_BUFFER_TOO_SMALL = 6  /* proof capacity below zc_proof_size */
+} zc_status;
+
+typedef enum { ZC_GATE_PLONK = 1, ZC_GATE_PRODUCT = 2 } zc_gate;
+typedef enum { ZC_FORM_SUMCHECK = 1, ZC_FORM_NTT = 2 } zc_form;
+
+/* One ZeroCheck instance: gate, n (N = 2^n, 1 <= n <= 28), degree d
+ * (3 for Plonk, 2..64 for the product gate) and log2(|D| / N) for the NTT
+ * form (0 selects log2(next_pow2(d)); |D| must be >= d N).  SumCheck
+ * ignores log_blowup. */
+typedef struct {
+  uint32_t gate, n, d;
+  uint32_t log_blowup;
+} zc_params;
+
+/* device: CUDA ordinal.  max_n / max_d: largest instance the context will
+ * accept (scratch grows on demand up to mem_budget_bytes; 0 = no budget). */
+typedef struct {
+  int device;
+  uint32_t max_n, max_d;
+  uint64_t mem_budget_bytes;
+} zc_setup_opts;
+
+typedef struct zc_ctx zc_ctx;
+
+/* Create a context on opts->device: field and twiddle constants, streams.
+ * Returns ZC_ERR_ARG for a null pointer, ZC_ERR_CUDA if the device cannot be
+ * used.  Paper: the set-up the hardware designs of Sec. 4 assume (twiddle
+ * buffers, Build-MLE unit). */
+zc_status zc_setup(const zc_setup_opts* opts, zc_ctx** out);
+
+/* Free everything the context owns.  Null is ignored. */
+void zc_destroy(zc_ctx* ctx);
+
+/* Proof size in bytes for params and form (formats above). */
+zc_status zc_proof_size(const zc_params* params, zc_form form, size_t* bytes);
+
+/* SumCheck-form ZeroCheck proof (Fig. side-by-side-zc right; Sec. 3.3).
+ * cols: c pointers to N*32-byte canonical columns, device pointers when
+ * cols_on_device != 0, host pointers otherwise (copied to the device inside
+ * the call).  col_roots: the c column commitments root(col_j) if the caller
+ * has them (stage (1) of the prover workflow, Sec. 3.1), or NULL to compute
+ * them on the device.  cuda_stream: a cudaStream_t (NULL = legacy default).
+ * proof: cap bytes, host or device memory; *len receives the proof size.
+ * With device columns and a device proof buffer the call is asynchronous on
+ * cuda_stream; otherwise it returns after the proof is written. */
+zc_status zc_prove_sumcheck(zc_ctx* ctx, const zc_params* params, const void* const* cols,
+                            int cols_on_device, const uint8_t (*col_roots)[32],
+                            void* cuda_stream, uint8_t* proof, size_t cap, size_t* len);
+
+/* NTT-form ZeroCheck proof (Fig. side-by-side-zc left; Sec. 3.2).
+ * Arguments as for zc_prove_sumcheck.  q_out: NULL, or M*32 bytes
+ * (M = N 2^log_blowup) that receive the quotient coefficients q_0..q_{M-1},
+ * canonical, device memory when q_on_device != 0.  Asynchronous when the
+ * columns, proof and q_out are all device memory. */
+zc_status zc_prove_ntt(zc_ctx* ctx, const zc_params* params, const void* const* cols,
+                       int cols_on_device, const uint8_t (*col_roots)[32], void* cuda_stream,
+                       uint8_t* proof, size_t cap, size_t* len, void* q_out, int q_on_device);
+
+/* Verify a proof on the host (no device needed).  cols: host columns (oracle
+ * access in place of a commitment opening).  q: the quotient (NTT form,
+ * M*32 bytes host memory; ignored for SumCheck).  *accept = 1 iff every
+ * check passes: per-round G_i(0)+G_i(1) = G_{i-1}(alpha_{i-1}) (Sec. 3.4),
+ * the final eq-weighted gate check and v_j = MLE_j(alpha) (Sec. 3.3); or
+ * root(q), deg q <= deg f - N, q(z), the openings g_j(z) and
+ * gate(g(z)) = z_H(z) q(z) (Sec. 3.2).  Malformed input: ZC_ERR_ARG. */
+zc_status zc_verify(const zc_params* params, zc_form form, const void* const* cols,
+                    const uint8_t (*col_roots)[32], const uint8_t* proof, size_t len,
+                    const void* q, int* accept);
+
+/* Column commitments root(col_j) for j < c, computed on the device
+ * (Fig. side-by-side-zc, "Commit"; stand-in described above).  roots_out:
+ * host memory, c entries.  Synchronous. */
+zc_status zc_roots(zc_ctx* ctx, const zc_params* params, const void* const* cols,
+                   int cols_on_device, void* cuda_stream, uint8_t (*roots_out)[32]);
+
+/* Per-phase device time of the last prove call in milliseconds, cudaEvent
+ * based: [0] roots, [1] challenges r / eq tables, [2] SumCheck rounds or
+ * INTT_H, [3] SumCheck last rounds or LDE+gate+divide, [4] q INTT,
+ * [5] q root + z, [6] openings / proof out.  Writes min(cap, 7) values. */
+zc_status zc_stats(zc_ctx* ctx, double* phase_ms, uint32_t cap);
+
+/* Message describing the last failure on ctx ("" if none). */
+const char* zc_last_error(zc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZC_H */

@@ -1,0 +1,339 @@
+// zc_field.cuh -- arithmetic in the BLS12-381 scalar field r on sm_103a.
+//
+// Elements are 8 x 32-bit little-endian limbs (32 bytes).  The device
+// multiplier is a CIOS Montgomery product (Koc, Acar, Kaliski 1996) written
+// as PTX carry chains (mad.lo.cc / madc.hi.cc) on the integer pipe; r's low
+// limb is 1, so -r^{-1} mod 2^32 = 0xffffffff and the per-row quotient digit
+// is just the negated low word.  r < 2^255 keeps every intermediate of a row
+// inside nine words.
+//
+// "Level" bookkeeping: a Montgomery product of values x (stored as x R^i)
+// and y (stored as y R^j) returns x y R^(i+j-1).  Canonical storage is level
+// 0, the usual Montgomery form level 1.  The provers keep tables at whatever
+// level makes the gate need no conversions and fold the R powers into
+// per-proof constants.
+#pragma once
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define ZC_HD __host__ __device__ __forceinline__
+#define ZC_D __device__ __forceinline__
+#else
+#define ZC_HD inline
+#define ZC_D inline
+#endif
+
+namespace zc {
+
+struct fr {
+  uint32_t v[8];
+};
+
+// r = 0x73eda753299d7d483339d80809a1d80553bda402fffe5bfeffffffff00000001
+#define ZC_P0 0x00000001u
+#define ZC_P1 0xffffffffu
+#define ZC_P2 0xfffe5bfeu
+#define ZC_P3 0x53bda402u
+#define ZC_P4 0x09a1d805u
+#define ZC_P5 0x3339d808u
+#define ZC_P6 0x299d7d48u
+#define ZC_P7 0x73eda753u
+
+// limb i of r (i is a compile-time constant after unrolling)
+ZC_HD uint32_t p_limb(int i) {
+  switch (i) {
+    case 0: return ZC_P0;
+    case 1: return ZC_P1;
+    case 2: return ZC_P2;
+    case 3: return ZC_P3;
+    case 4: return ZC_P4;
+    case 5: return ZC_P5;
+    case 6: return ZC_P6;
+    default: return ZC_P7;
+  }
+}
+
+ZC_HD fr fr_zero() {
+  fr z;
+  for (int i = 0; i < 8; i++) z.v[i] = 0;
+  return z;
+}
+
+ZC_HD bool fr_is_zero(const fr& a) {
+  uint32_t x = 0;
+  for (int i = 0; i < 8; i++) x |= a.v[i];
+  return x == 0;
+}
+
+ZC_HD bool fr_equal(const fr& a, const fr& b) {
+  uint32_t x = 0;
+  for (int i = 0; i < 8; i++) x |= a.v[i] ^ b.v[i];
+  return x == 0;
+}
+
+// a < r as an integer (canonical check)
+ZC_HD bool fr_is_canonical(const fr& a) {
+  const uint32_t P[8] = {ZC_P0, ZC_P1, ZC_P2, ZC_P3, ZC_P4, ZC_P5, ZC_P6, ZC_P7};
+  for (int i = 7; i >= 0; i--) {
+    if (a.v[i] != P[i]) return a.v[i] < P[i];
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------- generic --
+// Portable versions (host verifier, set-up constants).  64-bit intermediates.
+
+ZC_HD fr fr_add_g(const fr& a, const fr& b) {
+  const uint32_t P[8] = {ZC_P0, ZC_P1, ZC_P2, ZC_P3, ZC_P4, ZC_P5, ZC_P6, ZC_P7};
+  fr s, t;
+  uint64_t c = 0;
+  for (int i = 0; i < 8; i++) {
+    c += (uint64_t)a.v[i] + b.v[i];
+    s.v[i] = (uint32_t)c;
+    c >>= 32;
+  }
+  int64_t br = 0;
+  for (int i = 0; i < 8; i++) {
+    int64_t d = (int64_t)s.v[i] - P[i] + br;
+    t.v[i] = (uint32_t)d;
+    br = d >> 32;  // 0 or -1
+  }
+  return (c == 0 && br < 0) ? s : t;
+}
+
+ZC_HD fr fr_sub_g(const fr& a, const fr& b) {
+  const uint32_t P[8] = {ZC_P0, ZC_P1, ZC_P2, ZC_P3, ZC_P4, ZC_P5, ZC_P6, ZC_P7};
+  fr s;
+  int64_t br = 0;
+  for (int i = 0; i < 8; i++) {
+    int64_t d = (int64_t)a.v[i] - b.v[i] + br;
+    s.v[i] = (uint32_t)d;
+    br = d >> 32;
+  }
+  if (br < 0) {
+    uint64_t c = 0;
+    for (int i = 0; i < 8; i++) {
+      c += (uint64_t)s.v[i] + P[i];
+      s.v[i] = (uint32_t)c;
+      c >>= 32;
+    }
+  }
+  return s;
+}
+
+// Montgomery product a b 2^-256 mod r, inputs < r, output < r.
+ZC_HD fr fr_mul_g(const fr& a, const fr& b) {
+  const uint32_t P[8] = {ZC_P0, ZC_P1, ZC_P2, ZC_P3, ZC_P4, ZC_P5, ZC_P6, ZC_P7};
+  uint32_t t[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int i = 0; i < 8; i++) {
+    uint64_t c = 0;
+    for (int j = 0; j < 8; j++) {
+      c += (uint64_t)a.v[j] * b.v[i] + t[j];
+      t[j] = (uint32_t)c;
+      c >>= 32;
+    }
+    c += t[8];
+    t[8] = (uint32_t)c;
+    t[9] = (uint32_t)(c >> 32);
+    uint32_t m = 0u - t[0];  // t0 * (-r^{-1}) mod 2^32, r0 = 1
+    c = (uint64_t)m * P[0] + t[0];
+    c >>= 32;
+    for (int j = 1; j < 8; j++) {
+      c += (uint64_t)m * P[j] + t[j];
+      t[j - 1] = (uint32_t)c;
+      c >>= 32;
+    }
+    c += t[8];
+    t[7] = (uint32_t)c;
+    t[8] = t[9] + (uint32_t)(c >> 32);
+  }
+  fr r;
+  for (int i = 0; i < 8; i++) r.v[i] = t[i];
+  if (t[8] != 0 || !fr_is_canonical(r)) {
+    int64_t br = 0;
+    for (int i = 0; i < 8; i++) {
+      int64_t d = (int64_t)r.v[i] - P[i] + br;
+      r.v[i] = (uint32_t)d;
+      br = d >> 32;
+    }
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------- device --
+#if defined(__CUDACC__)
+
+ZC_D fr fr_add(const fr& a, const fr& b) {
+  fr s, t;
+  uint32_t bw;
+  asm("add.cc.u32 %0, %8, %16;\n\t"
+      "addc.cc.u32 %1, %9, %17;\n\t"
+      "addc.cc.u32 %2, %10, %18;\n\t"
+      "addc.cc.u32 %3, %11, %19;\n\t"
+      "addc.cc.u32 %4, %12, %20;\n\t"
+      "addc.cc.u32 %5, %13, %21;\n\t"
+      "addc.cc.u32 %6, %14, %22;\n\t"
+      "addc.u32 %7, %15, %23;"
+      : "=r"(s.v[0]), "=r"(s.v[1]), "=r"(s.v[2]), "=r"(s.v[3]), "=r"(s.v[4]), "=r"(s.v[5]),
+        "=r"(s.v[6]), "=r"(s.v[7])
+      : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]),
+        "r"(a.v[6]), "r"(a.v[7]), "r"(b.v[0]), "r"(b.v[1]), "r"(b.v[2]), "r"(b.v[3]),
+        "r"(b.v[4]), "r"(b.v[5]), "r"(b.v[6]), "r"(b.v[7]));
+  asm("sub.cc.u32 %0, %9, %17;\n\t"
+      "subc.cc.u32 %1, %10, %18;\n\t"
+      "subc.cc.u32 %2, %11, %19;\n\t"
+      "subc.cc.u32 %3, %12, %20;\n\t"
+      "subc.cc.u32 %4, %13, %21;\n\t"
+      "subc.cc.u32 %5, %14, %22;\n\t"
+      "subc.cc.u32 %6, %15, %23;\n\t"
+      "subc.cc.u32 %7, %16, %24;\n\t"
+      "subc.u32 %8, 0, 0;"
+      : "=r"(t.v[0]), "=r"(t.v[1]), "=r"(t.v[2]), "=r"(t.v[3]), "=r"(t.v[4]), "=r"(t.v[5]),
+        "=r"(t.v[6]), "=r"(t.v[7]), "=r"(bw)
+      : "r"(s.v[0]), "r"(s.v[1]), "r"(s.v[2]), "r"(s.v[3]), "r"(s.v[4]), "r"(s.v[5]),
+        "r"(s.v[6]), "r"(s.v[7]), "n"(ZC_P0), "n"(ZC_P1), "n"(ZC_P2), "n"(ZC_P3), "n"(ZC_P4),
+        "n"(ZC_P5), "n"(ZC_P6), "n"(ZC_P7));
+  // bw == 0xffffffff: s < r, keep s
+#pragma unroll
+  for (int i = 0; i < 8; i++) s.v[i] = bw ? s.v[i] : t.v[i];
+  return s;
+}
+
+ZC_D fr fr_sub(const fr& a, const fr& b) {
+  fr s;
+  uint32_t bw;
+  asm("sub.cc.u32 %0, %9, %17;\n\t"
+      "subc.cc.u32 %1, %10, %18;\n\t"
+      "subc.cc.u32 %2, %11, %19;\n\t"
+      "subc.cc.u32 %3, %12, %20;\n\t"
+      "subc.cc.u32 %4, %13, %21;\n\t"
+      "subc.cc.u32 %5, %14, %22;\n\t"
+      "subc.cc.u32 %6, %15, %23;\n\t"
+      "subc.cc.u32 %7, %16, %24;\n\t"
+      "subc.u32 %8, 0, 0;"
+      : "=r"(s.v[0]), "=r"(s.v[1]), "=r"(s.v[2]), "=r"(s.v[3]), "=r"(s.v[4]), "=r"(s.v[5]),
+        "=r"(s.v[6]), "=r"(s.v[7]), "=r"(bw)
+      : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]),
+        "r"(a.v[6]), "r"(a.v[7]), "r"(b.v[0]), "r"(b.v[1]), "r"(b.v[2]), "r"(b.v[3]),
+        "r"(b.v[4]), "r"(b.v[5]), "r"(b.v[6]), "r"(b.v[7]));
+  asm("add.cc.u32 %0, %0, %8;\n\t"
+      "addc.cc.u32 %1, %1, %9;\n\t"
+      "addc.cc.u32 %2, %2, %10;\n\t"
+      "addc.cc.u32 %3, %3, %11;\n\t"
+      "addc.cc.u32 %4, %4, %12;\n\t"
+      "addc.cc.u32 %5, %5, %13;\n\t"
+      "addc.cc.u32 %6, %6, %14;\n\t"
+      "addc.u32 %7, %7, %15;"
+      : "+r"(s.v[0]), "+r"(s.v[1]), "+r"(s.v[2]), "+r"(s.v[3]), "+r"(s.v[4]), "+r"(s.v[5]),
+        "+r"(s.v[6]), "+r"(s.v[7])
+      : "r"(bw & ZC_P0), "r"(bw & ZC_P1), "r"(bw & ZC_P2), "r"(bw & ZC_P3), "r"(bw & ZC_P4),
+        "r"(bw & ZC_P5), "r"(bw & ZC_P6), "r"(bw & ZC_P7));
+  return s;
+}
+
+// One CIOS row: t += a * b; then t += m r with m = -t0, and shift one word.
+// t holds nine words; t8 is zero on entry and becomes the new top word.
+#define ZC_ROW(B)                                                                        \
+  asm("mad.lo.cc.u32 %0, %9, %17, %0;\n\t"                                               \
+      "madc.lo.cc.u32 %1, %10, %17, %1;\n\t"                                             \
+      "madc.lo.cc.u32 %2, %11, %17, %2;\n\t"                                             \
+      "madc.lo.cc.u32 %3, %12, %17, %3;\n\t"                                             \
+      "madc.lo.cc.u32 %4, %13, %17, %4;\n\t"                                             \
+      "madc.lo.cc.u32 %5, %14, %17, %5;\n\t"                                             \
+      "madc.lo.cc.u32 %6, %15, %17, %6;\n\t"                                             \
+      "madc.lo.cc.u32 %7, %16, %17, %7;\n\t"                                             \
+      "addc.u32 %8, 0, 0;\n\t"                                                           \
+      "mad.hi.cc.u32 %1, %9, %17, %1;\n\t"                                               \
+      "madc.hi.cc.u32 %2, %10, %17, %2;\n\t"                                             \
+      "madc.hi.cc.u32 %3, %11, %17, %3;\n\t"                                             \
+      "madc.hi.cc.u32 %4, %12, %17, %4;\n\t"                                             \
+      "madc.hi.cc.u32 %5, %13, %17, %5;\n\t"                                             \
+      "madc.hi.cc.u32 %6, %14, %17, %6;\n\t"                                             \
+      "madc.hi.cc.u32 %7, %15, %17, %7;\n\t"                                             \
+      "madc.hi.u32 %8, %16, %17, %8;"                                                    \
+      : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3), "+r"(t4), "+r"(t5), "+r"(t6), "+r"(t7), \
+        "+r"(t8)                                                                         \
+      : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]),    \
+        "r"(a.v[6]), "r"(a.v[7]), "r"(B));                                               \
+  {                                                                                      \
+    uint32_t m = 0u - t0;                                                                \
+    asm("add.cc.u32 %0, %0, %9;\n\t"                                                     \
+        "madc.lo.cc.u32 %1, %9, %10, %1;\n\t"                                            \
+        "madc.lo.cc.u32 %2, %9, %11, %2;\n\t"                                            \
+        "madc.lo.cc.u32 %3, %9, %12, %3;\n\t"                                            \
+        "madc.lo.cc.u32 %4, %9, %13, %4;\n\t"                                            \
+        "madc.lo.cc.u32 %5, %9, %14, %5;\n\t"                                            \
+        "madc.lo.cc.u32 %6, %9, %15, %6;\n\t"                                            \
+        "madc.lo.cc.u32 %7, %9, %16, %7;\n\t"                                            \
+        "addc.u32 %8, %8, 0;\n\t"                                                        \
+        "mad.hi.cc.u32 %2, %9, %10, %2;\n\t"                                             \
+        "madc.hi.cc.u32 %3, %9, %11, %3;\n\t"                                            \
+        "madc.hi.cc.u32 %4, %9, %12, %4;\n\t"                                            \
+        "madc.hi.cc.u32 %5, %9, %13, %5;\n\t"                                            \
+        "madc.hi.cc.u32 %6, %9, %14, %6;\n\t"                                            \
+        "madc.hi.cc.u32 %7, %9, %15, %7;\n\t"                                            \
+        "madc.hi.u32 %8, %9, %16, %8;"                                                   \
+        : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3), "+r"(t4), "+r"(t5), "+r"(t6), "+r"(t7), \
+          "+r"(t8)                                                                       \
+        : "r"(m), "n"(ZC_P1), "n"(ZC_P2), "n"(ZC_P3), "n"(ZC_P4), "n"(ZC_P5), "n"(ZC_P6), \
+          "n"(ZC_P7));                                                                   \
+  }                                                                                      \
+  t0 = t1; t1 = t2; t2 = t3; t3 = t4; t4 = t5; t5 = t6; t6 = t7; t7 = t8; t8 = 0;
+
+// In the reduction asm, %9 is m and %10..%16 are r1..r7; r0 = 1 turns its
+// low product into a plain add and its high product into zero.
+
+ZC_D fr fr_reduce_final(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3, uint32_t t4,
+                        uint32_t t5, uint32_t t6, uint32_t t7) {
+  fr s, r;
+  uint32_t bw;
+  asm("sub.cc.u32 %0, %9, %17;\n\t"
+      "subc.cc.u32 %1, %10, %18;\n\t"
+      "subc.cc.u32 %2, %11, %19;\n\t"
+      "subc.cc.u32 %3, %12, %20;\n\t"
+      "subc.cc.u32 %4, %13, %21;\n\t"
+      "subc.cc.u32 %5, %14, %22;\n\t"
+      "subc.cc.u32 %6, %15, %23;\n\t"
+      "subc.cc.u32 %7, %16, %24;\n\t"
+      "subc.u32 %8, 0, 0;"
+      : "=r"(s.v[0]), "=r"(s.v[1]), "=r"(s.v[2]), "=r"(s.v[3]), "=r"(s.v[4]), "=r"(s.v[5]),
+        "=r"(s.v[6]), "=r"(s.v[7]), "=r"(bw)
+      : "r"(t0), "r"(t1), "r"(t2), "r"(t3), "r"(t4), "r"(t5), "r"(t6), "r"(t7), "n"(ZC_P0),
+        "n"(ZC_P1), "n"(ZC_P2), "n"(ZC_P3), "n"(ZC_P4), "n"(ZC_P5), "n"(ZC_P6), "n"(ZC_P7));
+  r.v[0] = bw ? t0 : s.v[0];
+  r.v[1] = bw ? t1 : s.v[1];
+  r.v[2] = bw ? t2 : s.v[2];
+  r.v[3] = bw ? t3 : s.v[3];
+  r.v[4] = bw ? t4 : s.v[4];
+  r.v[5] = bw ? t5 : s.v[5];
+  r.v[6] = bw ? t6 : s.v[6];
+  r.v[7] = bw ? t7 : s.v[7];
+  return r;
+}
+
+ZC_D fr fr_mul(const fr& a, const fr& b) {
+  uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0, t7 = 0, t8 = 0;
+  ZC_ROW(b.v[0])
+  ZC_ROW(b.v[1])
+  ZC_ROW(b.v[2])
+  ZC_ROW(b.v[3])
+  ZC_ROW(b.v[4])
+  ZC_ROW(b.v[5])
+  ZC_ROW(b.v[6])
+  ZC_ROW(b.v[7])
+  return fr_reduce_final(t0, t1, t2, t3, t4, t5, t6, t7);
+}
+
+#else
+inline fr fr_add(const fr& a, const fr& b) { return fr_add_g(a, b); }
+inline fr fr_sub(const fr& a, const fr& b) { return fr_sub_g(a, b); }
+inline fr fr_mul(const fr& a, const fr& b) { return fr_mul_g(a, b); }
+#endif
+
+ZC_HD fr fr_from_u32(uint32_t x) {
+  fr z = fr_zero();
+  z.v[0] = x;
+  return z;
+}
+
+}  // namespace zc

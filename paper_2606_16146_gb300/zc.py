@@ -1,0 +1,224 @@
+"""Python binding of libzc.so (the C ABI declared in include/zc.h).
+
+Argument marshalling only: every step of proving runs in the library's CUDA
+kernels.  Columns may be ``torch.Tensor`` objects on a CUDA device (passed by
+``data_ptr()``) or host buffers (``numpy`` arrays, ``bytes``); the proof
+buffer is host memory unless a device tensor is given.  There is no CPU
+fallback: importing this module on a machine without the built library
+raises, and every call reports the library's status code as an exception.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ZC_OK = 0
+STATUS = {0: "ZC_OK", 1: "ZC_ERR_ARG", 2: "ZC_ERR_OOM", 3: "ZC_ERR_CUDA", 4: "ZC_ERR_TIMEOUT",
+          5: "ZC_ERR_UNSUPPORTED", 6: "ZC_ERR_BUFFER_TOO_SMALL"}
+ZC_GATE_PLONK, ZC_GATE_PRODUCT = 1, 2
+ZC_FORM_SUMCHECK, ZC_FORM_NTT = 1, 2
+
+
+class ZCError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class zc_params(ctypes.Structure):
+    _fields_ = [("gate", ctypes.c_uint32), ("n", ctypes.c_uint32), ("d", ctypes.c_uint32),
+                ("log_blowup", ctypes.c_uint32)]
+
+
+class zc_setup_opts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("max_n", ctypes.c_uint32), ("max_d", ctypes.c_uint32),
+                ("mem_budget_bytes", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def lib(path: str | None = None):
+    """Load libzc.so (building it first if it is missing)."""
+    global _lib
+    if _lib is None:
+        p = path or _build.LIB
+        if not os.path.exists(p):
+            _build.build()
+        L = ctypes.CDLL(p)
+        vp, sz, u8p = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p
+        P = ctypes.POINTER
+        L.zc_setup.argtypes = [P(zc_setup_opts), P(vp)]
+        L.zc_setup.restype = ctypes.c_int
+        L.zc_destroy.argtypes = [vp]
+        L.zc_destroy.restype = None
+        L.zc_proof_size.argtypes = [P(zc_params), ctypes.c_int, P(sz)]
+        L.zc_proof_size.restype = ctypes.c_int
+        L.zc_prove_sumcheck.argtypes = [vp, P(zc_params), vp, ctypes.c_int, vp, vp, u8p, sz, P(sz)]
+        L.zc_prove_sumcheck.restype = ctypes.c_int
+        L.zc_prove_ntt.argtypes = [vp, P(zc_params), vp, ctypes.c_int, vp, vp, u8p, sz, P(sz), vp,
+                                   ctypes.c_int]
+        L.zc_prove_ntt.restype = ctypes.c_int
+        L.zc_verify.argtypes = [P(zc_params), ctypes.c_int, vp, vp, u8p, sz, vp, P(ctypes.c_int)]
+        L.zc_verify.restype = ctypes.c_int
+        L.zc_roots.argtypes = [vp, P(zc_params), vp, ctypes.c_int, vp, vp]
+        L.zc_roots.restype = ctypes.c_int
+        L.zc_stats.argtypes = [vp, P(ctypes.c_double), ctypes.c_uint32]
+        L.zc_stats.restype = ctypes.c_int
+        L.zc_last_error.argtypes = [vp]
+        L.zc_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _addr(x) -> int:
+    if _is_torch(x):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _host_array(x) -> np.ndarray:
+    if isinstance(x, (bytes, bytearray)):
+        return np.frombuffer(bytes(x), dtype=np.uint8)
+    return np.ascontiguousarray(x)
+
+
+class _Ptrs:
+    def __init__(self, bufs):
+        self.keep = list(bufs)
+        self.arr = (ctypes.c_void_p * len(self.keep))(*[_addr(b) for b in self.keep])
+
+    @property
+    def p(self):
+        return ctypes.cast(self.arr, ctypes.c_void_p)
+
+
+def _roots_arg(roots):
+    if roots is None:
+        return None, None
+    b = np.frombuffer(b"".join(bytes(r) for r in roots), dtype=np.uint8).copy()
+    return b, b.ctypes.data
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def proof_size(gate, n, d, form, log_blowup=0) -> int:
+    p = zc_params(gate, n, d, log_blowup)
+    out = ctypes.c_size_t()
+    st = lib().zc_proof_size(ctypes.byref(p), form, ctypes.byref(out))
+    if st != ZC_OK:
+        raise ZCError(st, "zc_proof_size")
+    return out.value
+
+
+class Context:
+    """A zc_ctx: owns device scratch, constants and events for one GPU."""
+
+    def __init__(self, device: int = 0, max_n: int = 24, max_d: int = 8, mem_budget_bytes: int = 0):
+        opts = zc_setup_opts(device, max_n, max_d, mem_budget_bytes)
+        h = ctypes.c_void_p()
+        st = lib().zc_setup(ctypes.byref(opts), ctypes.byref(h))
+        if st != ZC_OK:
+            raise ZCError(st, "zc_setup")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().zc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != ZC_OK:
+            msg = lib().zc_last_error(self.h)
+            raise ZCError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def _cols(self, cols):
+        on_dev = all(_is_torch(c) and c.is_cuda for c in cols)
+        if not on_dev:
+            cols = [_host_array(c) for c in cols]
+        return _Ptrs(cols), 1 if on_dev else 0
+
+    def prove_sumcheck(self, gate, n, d, cols, roots=None, stream=None, proof_out=None):
+        """SumCheck-form proof.  Returns the proof (numpy uint8) unless proof_out
+        (a device tensor) is given, in which case the call is asynchronous."""
+        p = zc_params(gate, n, d, 0)
+        P, on_dev = self._cols(cols)
+        rb, rp = _roots_arg(roots)
+        cap = proof_size(gate, n, d, ZC_FORM_SUMCHECK)
+        out = proof_out if proof_out is not None else np.zeros(cap, np.uint8)
+        ln = ctypes.c_size_t()
+        st = lib().zc_prove_sumcheck(self.h, ctypes.byref(p), P.p, on_dev, rp, _stream_ptr(stream),
+                                     _addr(out), cap, ctypes.byref(ln))
+        self._check(st, "zc_prove_sumcheck")
+        return out
+
+    def prove_ntt(self, gate, n, d, cols, roots=None, stream=None, proof_out=None, q_out=None,
+                  log_blowup=0):
+        """NTT-form proof.  Returns (proof, q); q_out may be a device tensor of
+        M*32 bytes, or None for a host array."""
+        p = zc_params(gate, n, d, log_blowup)
+        P, on_dev = self._cols(cols)
+        rb, rp = _roots_arg(roots)
+        cap = proof_size(gate, n, d, ZC_FORM_NTT, log_blowup)
+        lb = log_blowup or (d - 1).bit_length()
+        M = 1 << (n + lb)
+        out = proof_out if proof_out is not None else np.zeros(cap, np.uint8)
+        q = q_out if q_out is not None else np.zeros(M * 32, np.uint8)
+        q_dev = 1 if (_is_torch(q) and q.is_cuda) else 0
+        ln = ctypes.c_size_t()
+        st = lib().zc_prove_ntt(self.h, ctypes.byref(p), P.p, on_dev, rp, _stream_ptr(stream),
+                                _addr(out), cap, ctypes.byref(ln), _addr(q), q_dev)
+        self._check(st, "zc_prove_ntt")
+        return out, q
+
+    def roots(self, gate, n, d, cols, stream=None) -> list[bytes]:
+        p = zc_params(gate, n, d, 0)
+        P, on_dev = self._cols(cols)
+        c = len(cols)
+        out = np.zeros(32 * c, np.uint8)
+        st = lib().zc_roots(self.h, ctypes.byref(p), P.p, on_dev, _stream_ptr(stream), out.ctypes.data)
+        self._check(st, "zc_roots")
+        return [out[32 * j:32 * j + 32].tobytes() for j in range(c)]
+
+    def stats(self) -> list[float]:
+        a = (ctypes.c_double * 7)()
+        self._check(lib().zc_stats(self.h, a, 7), "zc_stats")
+        return list(a)
+
+
+def verify(gate, n, d, form, cols, proof, q=None, roots=None, log_blowup=0) -> bool:
+    """Host-side verifier (no GPU needed).  cols/q: host buffers."""
+    p = zc_params(gate, n, d, log_blowup)
+    P = _Ptrs([_host_array(c) for c in cols])
+    rb, rp = _roots_arg(roots)
+    pr = _host_array(proof)
+    qa = _host_array(q) if q is not None else None
+    acc = ctypes.c_int(0)
+    st = lib().zc_verify(ctypes.byref(p), form, P.p, rp, pr.ctypes.data, pr.size,
+                         qa.ctypes.data if qa is not None else None, ctypes.byref(acc))
+    if st == 1:
+        return False
+    if st != ZC_OK:
+        raise ZCError(st, "zc_verify")
+    return bool(acc.value)

@@ -1,0 +1,72 @@
+"""The C ABI library loads, exports what include/zc.h declares, and its host
+verifier agrees with the oracle (CPU only; no kernel is launched)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_16146_gb300 import build, witness
+from paper_2606_16146_gb300 import zc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "zc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(zc_[a-z_]+)\s*\(", src)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = build.build()
+    L = zc.lib(path)
+    names = declared_functions()
+    assert "zc_prove_sumcheck" in names and "zc_prove_ntt" in names and "zc_verify" in names
+    for name in names:
+        assert hasattr(L, name), name
+
+
+@pytest.mark.parametrize("gate,n,d", [(1, 5, 3), (2, 7, 2), (2, 3, 32), (1, 24, 3)])
+def test_proof_size_matches_oracle(gate, n, d):
+    for form in (1, 2):
+        assert zc.proof_size(gate, n, d, form) == oracle.proof_size(form, gate, n, d)
+
+
+def test_bad_params_rejected():
+    with pytest.raises(zc.ZCError):
+        zc.proof_size(1, 5, 4, 1)          # Plonk needs d = 3
+    with pytest.raises(zc.ZCError):
+        zc.proof_size(2, 0, 2, 1)          # n >= 1
+    with pytest.raises(zc.ZCError):
+        zc.proof_size(3, 5, 3, 1)          # unknown gate
+
+
+def test_setup_fails_loudly_without_a_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(zc.ZCError):
+        zc.Context(0, 12, 3)
+
+
+@pytest.mark.parametrize("gate,n,d", [(1, 6, 3), (2, 5, 4), (2, 1, 2), (1, 1, 3)])
+def test_host_verifier_agrees_with_oracle(gate, n, d):
+    cols = witness.generate(gate, n, d, 40 + n)
+    bad = witness.generate(gate, n, d, 40 + n, tamper=True)
+    ps = oracle.prove_sumcheck(gate, n, d, cols)
+    assert zc.verify(gate, n, d, 1, cols, ps)
+    assert not zc.verify(gate, n, d, 1, bad, oracle.prove_sumcheck(gate, n, d, bad))
+    x = bytearray(ps)
+    x[40] ^= 4
+    assert not zc.verify(gate, n, d, 1, cols, bytes(x))
+    pn, q = oracle.prove_ntt(gate, n, d, cols)
+    assert zc.verify(gate, n, d, 2, cols, pn, q=q)
+    pb, qb = oracle.prove_ntt(gate, n, d, bad)
+    assert not zc.verify(gate, n, d, 2, bad, pb, q=qb)
+    q2 = np.array(q, copy=True)
+    q2[-1] ^= 1                      # top coefficient: breaks root and degree bound
+    assert not zc.verify(gate, n, d, 2, cols, pn, q=q2)
+    roots = [oracle.root(c) for c in cols]
+    assert zc.verify(gate, n, d, 1, cols, ps, roots=roots)
