@@ -323,14 +323,17 @@ static int root_of(const uint8_t *canon, size_t L, uint8_t out[32]) {
     #pragma omp parallel for schedule(static)
     for (long t = 0; t < (long)nl; t++)
         sha256(canon + (size_t)t * per * 32, per * 32, nodes + (size_t)t * 32);
+    /* each level is written to a fresh buffer: a parallel in-place update
+     * would let node i be overwritten while node i/2 is still reading it */
+    uint8_t *next = (uint8_t *)malloc((nl / 2 + 1) * 32);
+    if (!next) { free(nodes); return 0; }
     for (size_t cnt = nl; cnt > 1; cnt /= 2) {
         #pragma omp parallel for schedule(static)
-        for (long i = 0; i < (long)(cnt / 2); i++) {
-            uint8_t tmp[64];
-            memcpy(tmp, nodes + (size_t)(2 * i) * 32, 64);
-            sha256(tmp, 64, nodes + (size_t)i * 32);
-        }
+        for (long i = 0; i < (long)(cnt / 2); i++)
+            sha256(nodes + (size_t)(2 * i) * 32, 64, next + (size_t)i * 32);
+        memcpy(nodes, next, (cnt / 2) * 32);
     }
+    free(next);
     uint8_t msg[40];
     for (int i = 0; i < 8; i++) msg[i] = (uint8_t)((uint64_t)L >> (8 * i));
     memcpy(msg + 8, nodes, 32);
