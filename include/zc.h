@@ -141,10 +141,14 @@ zc_status zc_verify(const zc_params* params, zc_form form, const void* const* co
 zc_status zc_roots(zc_ctx* ctx, const zc_params* params, const void* const* cols,
                    int cols_on_device, void* cuda_stream, uint8_t (*roots_out)[32]);
 
-/* Per-phase device time of the last prove call in milliseconds, cudaEvent
- * based: [0] roots, [1] challenges r / eq tables, [2] SumCheck rounds or
- * INTT_H, [3] SumCheck last rounds or LDE+gate+divide, [4] q INTT,
- * [5] q root + z, [6] openings / proof out.  Writes min(cap, 7) values. */
+/* Device-side timing of the last prove call on ctx, from CUDA events the
+ * library records on the call's stream.  Writes min(cap, 10) values:
+ * [0..5] phase times in ms.  SumCheck: roots, transcript r + eq tables,
+ * round-1 evaluation kernel, rounds 2..n, final values + proof out.  NTT:
+ * roots, INTT_H, slice LDE + gate + divide, q INTT, q root + z, openings +
+ * proof out.  [6] time of the dominant kernel launch (ms), [7] its
+ * algorithmic modular multiplications, [8] its algorithmic DRAM bytes,
+ * [9] number of kernels the call launched.  Waits for the call's events. */
 zc_status zc_stats(zc_ctx* ctx, double* phase_ms, uint32_t cap);
 
 /* Message describing the last failure on ctx ("" if none). */

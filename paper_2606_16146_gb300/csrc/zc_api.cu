@@ -755,15 +755,21 @@ zc_status zc_roots(zc_ctx* ctx, const zc_params* params, const void* const* cols
 zc_status zc_stats(zc_ctx* ctx, double* phase_ms, uint32_t cap) {
   if (!ctx || !phase_ms) return ZC_ERR_ARG;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  float ms[7] = {0, 0, 0, 0, 0, 0, 0};
-  for (int i = 0; i < 6; i++) {
+  double out[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int i = 0; i + 1 < ctx->nev && i < 6; i++) {
+    float ms = 0;
     if (cudaEventSynchronize(ctx->ev[i + 1]) != cudaSuccess ||
-        cudaEventElapsedTime(&ms[i], ctx->ev[i], ctx->ev[i + 1]) != cudaSuccess) {
+        cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]) != cudaSuccess) {
       cudaGetLastError();
-      ms[i] = 0;
+      ms = 0;
     }
+    out[i] = ms;
   }
-  for (uint32_t i = 0; i < cap && i < 7; i++) phase_ms[i] = ms[i];
+  out[6] = ctx->dom_phase < 6 ? out[ctx->dom_phase] : 0;
+  out[7] = ctx->dom_mulmods;
+  out[8] = ctx->dom_bytes;
+  out[9] = ctx->launches;
+  for (uint32_t i = 0; i < cap && i < 10; i++) phase_ms[i] = out[i];
   return ZC_OK;
 }
 

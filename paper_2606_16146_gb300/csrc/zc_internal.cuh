@@ -91,7 +91,11 @@ struct zc_ctx {
   void* pinned = nullptr;        // small pinned staging buffer
   size_t pinned_cap = 0;
   cudaEvent_t ev[8] = {};
-  double phase_ms[7] = {0, 0, 0, 0, 0, 0, 0};
+  int nev = 0;                   // events recorded by the last prove call
+  uint32_t launches = 0;         // kernels launched by the last prove call
+  double dom_mulmods = 0;        // algorithmic work of the dominant kernel launch
+  double dom_bytes = 0;
+  int dom_phase = 2;             // phase index holding that launch
   int skip_point = 0;            // 0: derive H(1) from the claim (default), 1: derive H(0)
 };
 

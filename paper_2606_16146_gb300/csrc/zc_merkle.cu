@@ -181,6 +181,7 @@ zc_status launch_roots(zc_ctx* ctx, const fr* const* dcols, int c, uint64_t L, u
   la.nodes = nodes;
   dim3 grid(la.ctas, c);
   k_root_leaves<<<grid, kLeafCta, 0, st>>>(la);
+  ctx->launches++;
   RootTopArgs ta{};
   ta.nodes = nodes;
   ta.tmp = tmp;
@@ -188,6 +189,7 @@ zc_status launch_roots(zc_ctx* ctx, const fr* const* dcols, int c, uint64_t L, u
   ta.L = L;
   ta.roots = droots;
   k_root_top<<<c, 256, 0, st>>>(ta);
+  ctx->launches++;
   ZC_CUDA_TRY(ctx, cudaGetLastError());
   return ZC_OK;
 }

@@ -671,6 +671,13 @@ zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* col
       src[j] = tab[j];
     }
   }
+  ctx->launches = 0;
+  ctx->nev = 6;
+  ctx->dom_phase = 2;
+  // round-1 evaluation: per pair (d+1)(g+1)+1 mulmods, reads c*N*32 bytes
+  const double g_mul = plonk ? 5.0 : (double)(d - 1);
+  ctx->dom_mulmods = (double)(N / 2) * ((d + 1) * (g_mul + 1) + 1);
+  ctx->dom_bytes = 32.0 * (double)c * (double)N;
   ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[0], st));
   if (roots) {
     std::memcpy(ctx->pinned, roots, 32 * (size_t)c);
@@ -689,6 +696,7 @@ zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* col
   sa.n = (int)n;
   sa.C = ctx->dconst;
   k_sc_setup<<<1, 32, 0, st>>>(sa);
+  ctx->launches++;
   ScEqArgs ea{};
   ea.st = dst;
   ea.E = E;
@@ -699,6 +707,7 @@ zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* col
   ea.skip_point = ctx->skip_point;
   ea.C = ctx->dconst;
   k_sc_eq<<<1 + (eq_total + 255) / 256, 256, 0, st>>>(ea);
+  ctx->launches++;
   ZC_CUDA_TRY(ctx, cudaGetLastError());
   ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[2], st));
 
@@ -726,10 +735,12 @@ zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* col
       if (i == 0) {
         np = 4;
         k_sc_plonk_round<true><<<nblk, 256, 0, st>>>(pa);
+  ctx->launches++;
         for (int j = 5; j < 8; j++) cur[j] = tab[j];  // wires now at level 1 in scratch
       } else {
         np = 3;
         k_sc_plonk_round<false><<<nblk, 256, 0, st>>>(pa);
+  ctx->launches++;
         for (int j = 0; j < 8; j++) cur[j] = tab[j];
       }
     } else {
@@ -746,6 +757,7 @@ zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* col
         uint64_t tot = 2 * h * (uint64_t)c;
         int fb = (int)std::min<uint64_t>((tot + 255) / 256, (uint64_t)SMs * 8);
         k_sc_fold<<<fb, 256, 0, st>>>(fa);
+  ctx->launches++;
         for (int j = 0; j < c; j++) cur[j] = tab[j];
       }
       np = i == 0 ? (int)d + 1 : (int)d;
@@ -767,6 +779,7 @@ zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* col
       uint64_t want = (h + slots_per_blk - 1) / slots_per_blk;
       nblk = (int)std::min<uint64_t>(want, (uint64_t)grid_max_prod);
       k_sc_prod_eval<4><<<nblk, 256, 0, st>>>(pa);
+  ctx->launches++;
     }
     ScChalArgs ca{};
     ca.partials = partials;
@@ -779,8 +792,9 @@ zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* col
     ca.proof = dproof;
     ca.C = ctx->dconst;
     ca.tabs = ctx->dtabs;
-    k_sc_challenge<<<1, 256, 0, st>>>(ca);
     if (i == 0) ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[3], st));
+    k_sc_challenge<<<1, 256, 0, st>>>(ca);
+    ctx->launches++;
   }
   ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[4], st));
   ScFinalArgs fa{};
@@ -795,6 +809,7 @@ zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* col
   fa.st = dst;
   fa.proof = dproof;
   k_sc_final<<<1, 128, 0, st>>>(fa);
+  ctx->launches++;
   ZC_CUDA_TRY(ctx, cudaGetLastError());
   ZC_CUDA_TRY(ctx, cudaMemcpyAsync(proof, dproof, psize,
                                    proof_on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,

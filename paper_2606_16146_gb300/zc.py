@@ -202,8 +202,8 @@ class Context:
         return [out[32 * j:32 * j + 32].tobytes() for j in range(c)]
 
     def stats(self) -> list[float]:
-        a = (ctypes.c_double * 7)()
-        self._check(lib().zc_stats(self.h, a, 7), "zc_stats")
+        a = (ctypes.c_double * 10)()
+        self._check(lib().zc_stats(self.h, a, 10), "zc_stats")
         return list(a)
 
 
