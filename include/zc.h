@@ -151,6 +151,40 @@ zc_status zc_roots(zc_ctx* ctx, const zc_params* params, const void* const* cols
  * [9] number of kernels the call launched.  Waits for the call's events. */
 zc_status zc_stats(zc_ctx* ctx, double* phase_ms, uint32_t cap);
 
+/* SumCheck-form proof without any device allocation (the paper has no
+ * counterpart; this is a deployment variant of zc_prove_sumcheck).
+ *
+ * For callers that cannot allocate device memory while proving: code whose
+ * memory is handed out by an external pool reserved up front, pipelines
+ * that must not incur the implicit device synchronisation of
+ * cudaMalloc/cudaFree, or processes whose device memory is already fully
+ * reserved.  All scratch memory lives in fixed-size file-scope device arrays
+ * of the library (32 MiB of scratch plus constant tables, held by every GPU
+ * that loads the library until the process exits).  No context is used and
+ * nothing is allocated: no cudaMalloc, cudaFree or allocating routine.
+ *
+ * params: as for zc_prove_sumcheck.  cols: c DEVICE pointers (N*32 canonical
+ * bytes each) on the current device.  col_roots: host array of c roots, or
+ * NULL to compute them inside the static scratch.  cuda_stream: the stream
+ * the work is queued on.  proof: DEVICE buffer of cap bytes; *len receives
+ * the proof size.  The call is asynchronous: the proof is ready when the
+ * stream reaches it.  The bytes equal zc_prove_sumcheck's.
+ *
+ * Limits: the instance must fit the 32 MiB scratch (tables c*N*32 bytes plus
+ * small per-round buffers, e.g. the Plonk gate up to n = 16); larger
+ * instances return ZC_ERR_UNSUPPORTED without launching anything.
+ * Set-up: the first call on each device looks up the device addresses of the
+ * static arrays (cudaGetSymbolAddress) with that device current and copies
+ * the field constants into them with synchronous copies, so make that first
+ * call outside any stream capture.  Sharing: every call on a device uses the
+ * same arrays and leaves its data in them (the per-proof state is reset by
+ * the call itself), so calls whose work overlaps on the GPU (different
+ * streams, or different host threads) race and corrupt each other; order
+ * them on one stream. */
+zc_status zc_prove_sumcheck_static(const zc_params* params, const void* const* cols,
+                                   const uint8_t (*col_roots)[32], void* cuda_stream,
+                                   uint8_t* proof, size_t cap, size_t* len);
+
 /* Message describing the last failure on ctx ("" if none). */
 const char* zc_last_error(zc_ctx* ctx);
 

@@ -568,6 +568,15 @@ static const DevConst& host_constants() {
   return C;
 }
 
+// Field constants and per-degree tables as plain host values (used by the
+// static-scratch entry point, which has no context).
+void static_constants(DevConst* C, std::vector<fr>* tabs) {
+  zc_ctx tmp;
+  build_constants(&tmp);
+  *C = tmp.hconst;
+  *tabs = tmp.htabs;
+}
+
 }  // namespace zc
 
 using namespace zc;

@@ -131,6 +131,7 @@ void transcript_init_words(uint32_t S[8], uint32_t form, uint32_t gate, uint32_t
 zc_status launch_roots(zc_ctx* ctx, const fr* const* dcols, int c, uint64_t L, uint8_t* droots,
                        cudaStream_t st);
 size_t root_scratch_bytes(int c, uint64_t L);
+void static_constants(DevConst* C, std::vector<fr>* tabs);
 
 zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, int on_dev,
                          const uint8_t (*roots)[32], cudaStream_t st, uint8_t* proof,

@@ -826,3 +826,258 @@ zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* col
 }
 
 }  // namespace zc
+
+// ------------------------------------------------- static-scratch variant --
+//
+// zc_prove_sumcheck_static: the SumCheck prover for callers that cannot
+// allocate device memory at proving time -- code running under an allocator
+// that forbids new device allocations (a fixed memory pool reserved up
+// front), a stream-ordered pipeline that must not insert the implicit
+// synchronisation a cudaMalloc/cudaFree brings, or a host that links the
+// library into a process whose device memory is already fully reserved.
+// Everything the prover needs beyond the caller's inputs and output lives in
+// file-scope device arrays of fixed size: every GPU that loads the library
+// holds them until the process exits.  Host code never dereferences these
+// symbols: it asks the runtime for their device addresses once per device.
+
+namespace zc {
+
+constexpr size_t kStaticScratchBytes = 32ull << 20;  // 32 MiB
+constexpr int kStaticTabCap = 8192;                   // per-degree table entries
+constexpr int kStaticMaxDevices = 64;
+
+static __device__ __align__(256) uint8_t g_static_scratch[kStaticScratchBytes];
+static __device__ __align__(256) DevConst g_static_const;
+static __device__ __align__(256) fr g_static_tabs[kStaticTabCap];
+
+struct StaticDev {
+  bool ready = false;
+  void* scratch = nullptr;
+  DevConst* dconst = nullptr;
+  fr* dtabs = nullptr;
+  DevConst hconst;
+};
+static StaticDev g_static_dev[kStaticMaxDevices];
+static std::mutex g_static_mu;
+
+// Set-up for the current device: look up the device addresses of the static
+// arrays and copy the field constants into them.  Runs on the first call per
+// device (synchronous copies), so that first call must not be inside a
+// stream capture.
+static zc_status static_setup(int dev, StaticDev** out) {
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  StaticDev& S = g_static_dev[dev];
+  if (!S.ready) {
+    std::vector<fr> tabs;
+    static_constants(&S.hconst, &tabs);
+    if (tabs.size() > (size_t)kStaticTabCap) return ZC_ERR_UNSUPPORTED;
+    if (cudaGetSymbolAddress(&S.scratch, g_static_scratch) != cudaSuccess ||
+        cudaGetSymbolAddress((void**)&S.dconst, g_static_const) != cudaSuccess ||
+        cudaGetSymbolAddress((void**)&S.dtabs, g_static_tabs) != cudaSuccess) {
+      cudaGetLastError();
+      return ZC_ERR_CUDA;
+    }
+    if (cudaMemcpy(S.dconst, &S.hconst, sizeof(DevConst), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(S.dtabs, tabs.data(), sizeof(fr) * tabs.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return ZC_ERR_CUDA;
+    }
+    S.ready = true;
+  }
+  *out = &S;
+  return ZC_OK;
+}
+
+static zc_status static_prove(const zc_params* p, const void* const* cols,
+                              const uint8_t (*roots)[32], cudaStream_t st, uint8_t* proof,
+                              StaticDev& S) {
+  const uint32_t gate = p->gate, n = p->n, d = p->d;
+  const int c = gate_ncols(gate, d);
+  const uint64_t N = 1ull << n;
+  const bool plonk = gate == ZC_GATE_PLONK;
+  int SMs = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&SMs, cudaDevAttrMultiProcessorCount, dev);
+  const int grid_max_plonk = 2 * SMs / 8 * 8 > 0 ? 2 * SMs / 8 * 8 : 8;
+  const int PP = 4;
+  int G = 1;
+  while (G * PP < (int)d + 1) G *= 2;
+  const int grid_max_prod = 2 * SMs;
+  const int npmax = (int)d + 1;
+  uint32_t eq_total = 0;
+  EqTask tasks[2 * kMaxN];
+  uint32_t eq_off_hi[kMaxN], eq_off_lo[kMaxN], mlo_r[kMaxN];
+  for (uint32_t i = 0; i < n; i++) {
+    uint32_t mlo, mhi;
+    eq_round_split((int)n, (int)i, &mlo, &mhi);
+    mlo_r[i] = mlo;
+    tasks[2 * i] = EqTask{eq_total, i + 1, mhi, plonk ? 1u : d};
+    eq_off_hi[i] = eq_total;
+    eq_total += 1u << mhi;
+    tasks[2 * i + 1] = EqTask{eq_total, n - mlo, mlo, 1u};
+    eq_off_lo[i] = eq_total;
+    eq_total += 1u << mlo;
+  }
+  // carve the static array; reject instances that do not fit
+  Arena ar;
+  ar.base = static_cast<char*>(S.scratch);
+  ar.cap = kStaticScratchBytes;
+  fr* tab[kMaxCols];
+  for (int j = 0; j < c; j++) tab[j] = ar.take<fr>(N);
+  fr* partials = ar.take<fr>((size_t)std::max(grid_max_plonk, grid_max_prod) * (npmax + 1));
+  fr* E = ar.take<fr>(eq_total);
+  ScState* dst = ar.take<ScState>(1);
+  uint8_t* droots = ar.take<uint8_t>(32 * (size_t)c);
+  if (!tab[c - 1] || !partials || !E || !dst || !droots ||
+      (!roots && ar.used + root_scratch_bytes(c, N) > ar.cap))
+    return ZC_ERR_UNSUPPORTED;  // instance larger than the static scratch
+
+  const fr* src[kMaxCols];
+  for (int j = 0; j < c; j++) src[j] = reinterpret_cast<const fr*>(cols[j]);
+  if (roots) {
+    if (cudaMemcpyAsync(droots, roots, 32 * (size_t)c, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return ZC_ERR_CUDA;
+  } else {
+    // the root kernels take their node scratch from the rest of the static array
+    zc_ctx tmp;
+    tmp.arena = ar;
+    zc_status rs = launch_roots(&tmp, src, c, N, droots, st);
+    tmp.arena.base = nullptr;
+    if (rs != ZC_OK) return rs;
+  }
+  ScSetupArgs sa{};
+  sa.st = dst;
+  sa.roots = droots;
+  transcript_init_words(sa.S0, ZC_FORM_SUMCHECK, gate, n, d, 0);
+  sa.c = c;
+  sa.n = (int)n;
+  sa.C = S.dconst;
+  k_sc_setup<<<1, 32, 0, st>>>(sa);  // also clears the error flag and the claim
+  ScEqArgs ea{};
+  ea.st = dst;
+  ea.E = E;
+  for (uint32_t t = 0; t < 2 * n; t++) ea.task[t] = tasks[t];
+  ea.ntask = 2 * n;
+  ea.total = eq_total;
+  ea.n = (int)n;
+  ea.skip_point = 0;
+  ea.C = S.dconst;
+  k_sc_eq<<<1 + (eq_total + 255) / 256, 256, 0, st>>>(ea);
+  const fr* cur[kMaxCols];
+  for (int j = 0; j < c; j++) cur[j] = src[j];
+  for (uint32_t i = 0; i < n; i++) {
+    const uint64_t h = N >> (i + 1);
+    int nblk, np;
+    if (plonk) {
+      ScPlonkArgs pa{};
+      for (int j = 0; j < 8; j++) {
+        pa.src[j] = cur[j];
+        pa.dst[j] = tab[j];
+      }
+      pa.h = h;
+      pa.ehi = E + eq_off_hi[i];
+      pa.elo = E + eq_off_lo[i];
+      pa.m_lo = mlo_r[i];
+      pa.round = (int)i;
+      pa.st = dst;
+      pa.partials = partials;
+      pa.C = S.dconst;
+      nblk = (int)std::min<uint64_t>((h + 255) / 256, (uint64_t)grid_max_plonk);
+      if (i == 0) {
+        np = 4;
+        k_sc_plonk_round<true><<<nblk, 256, 0, st>>>(pa);
+        for (int j = 5; j < 8; j++) cur[j] = tab[j];
+      } else {
+        np = 3;
+        k_sc_plonk_round<false><<<nblk, 256, 0, st>>>(pa);
+        for (int j = 0; j < 8; j++) cur[j] = tab[j];
+      }
+    } else {
+      if (i > 0) {
+        ScFoldArgs fa{};
+        for (int j = 0; j < c; j++) {
+          fa.src[j] = cur[j];
+          fa.dst[j] = tab[j];
+        }
+        fa.h = 2 * h;
+        fa.c = c;
+        fa.round = (int)i;
+        fa.st = dst;
+        uint64_t tot = 2 * h * (uint64_t)c;
+        int fb = (int)std::min<uint64_t>((tot + 255) / 256, (uint64_t)SMs * 8);
+        k_sc_fold<<<fb, 256, 0, st>>>(fa);
+        for (int j = 0; j < c; j++) cur[j] = tab[j];
+      }
+      np = i == 0 ? (int)d + 1 : (int)d;
+      ScProdArgs pa{};
+      for (int j = 0; j < c; j++) pa.col[j] = cur[j];
+      pa.h = h;
+      pa.ehi = E + eq_off_hi[i];
+      pa.elo = E + eq_off_lo[i];
+      pa.m_lo = mlo_r[i];
+      pa.d = (int)d;
+      pa.np = np;
+      pa.G = G;
+      pa.round = (int)i;
+      pa.st = dst;
+      pa.partials = partials;
+      pa.kcomp = S.hconst.rnegpow[d - 2];
+      pa.C = S.dconst;
+      uint64_t slots_per_blk = 256 / G;
+      nblk = (int)std::min<uint64_t>((h + slots_per_blk - 1) / slots_per_blk, (uint64_t)grid_max_prod);
+      k_sc_prod_eval<4><<<nblk, 256, 0, st>>>(pa);
+    }
+    ScChalArgs ca{};
+    ca.partials = partials;
+    ca.nblk = nblk;
+    ca.np = np;
+    ca.d = (int)d;
+    ca.round = (int)i;
+    ca.n = (int)n;
+    ca.st = dst;
+    ca.proof = proof;
+    ca.C = S.dconst;
+    ca.tabs = S.dtabs;
+    k_sc_challenge<<<1, 256, 0, st>>>(ca);
+  }
+  ScFinalArgs fa{};
+  for (int j = 0; j < c; j++) {
+    fa.src[j] = cur[j];
+    fa.level[j] = (plonk && j >= 5) ? 1u : 0u;
+  }
+  fa.c = c;
+  fa.n = (int)n;
+  fa.gate = gate;
+  fa.d = d;
+  fa.st = dst;
+  fa.proof = proof;
+  k_sc_final<<<1, 128, 0, st>>>(fa);
+  return cudaGetLastError() == cudaSuccess ? ZC_OK : ZC_ERR_CUDA;
+}
+
+}  // namespace zc
+
+extern "C" zc_status zc_prove_sumcheck_static(const zc_params* params, const void* const* cols,
+                                              const uint8_t (*col_roots)[32], void* cuda_stream,
+                                              uint8_t* proof, size_t cap, size_t* len) {
+  using namespace zc;
+  zc_status s = check_params(nullptr, params, ZC_FORM_SUMCHECK);
+  if (s != ZC_OK) return s;
+  if (!cols || !proof || !len) return ZC_ERR_ARG;
+  const int c = gate_ncols(params->gate, params->d);
+  for (int j = 0; j < c; j++)
+    if (!cols[j]) return ZC_ERR_ARG;
+  const size_t need = 16 + 32 * ((size_t)params->n * (params->d + 2) + c);
+  *len = need;
+  if (cap < need) return ZC_ERR_BUFFER_TOO_SMALL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) {
+    cudaGetLastError();
+    return ZC_ERR_CUDA;
+  }
+  StaticDev* S = nullptr;
+  s = static_setup(dev, &S);
+  if (s != ZC_OK) return s;
+  return static_prove(params, cols, col_roots, static_cast<cudaStream_t>(cuda_stream), proof, *S);
+}

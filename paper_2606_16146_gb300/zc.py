@@ -69,6 +69,8 @@ def lib(path: str | None = None):
         L.zc_roots.restype = ctypes.c_int
         L.zc_stats.argtypes = [vp, P(ctypes.c_double), ctypes.c_uint32]
         L.zc_stats.restype = ctypes.c_int
+        L.zc_prove_sumcheck_static.argtypes = [P(zc_params), vp, vp, vp, u8p, sz, P(sz)]
+        L.zc_prove_sumcheck_static.restype = ctypes.c_int
         L.zc_last_error.argtypes = [vp]
         L.zc_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -222,3 +224,20 @@ def verify(gate, n, d, form, cols, proof, q=None, roots=None, log_blowup=0) -> b
     if st != ZC_OK:
         raise ZCError(st, "zc_verify")
     return bool(acc.value)
+
+
+def prove_sumcheck_static(gate, n, d, cols, proof_out, roots=None, stream=None) -> None:
+    """zc_prove_sumcheck_static: SumCheck proof with no device allocation.
+
+    cols: CUDA tensors on the current device; proof_out: a CUDA uint8 tensor
+    of at least proof_size(...) bytes.  Asynchronous on ``stream``.  For
+    callers that may not allocate device memory while proving; the library's
+    fixed static scratch (32 MiB) bounds the instance size."""
+    p = zc_params(gate, n, d, 0)
+    P = _Ptrs(cols)
+    rb, rp = _roots_arg(roots)
+    ln = ctypes.c_size_t()
+    st = lib().zc_prove_sumcheck_static(ctypes.byref(p), P.p, rp, _stream_ptr(stream),
+                                        _addr(proof_out), proof_out.numel(), ctypes.byref(ln))
+    if st != ZC_OK:
+        raise ZCError(st, "zc_prove_sumcheck_static")
