@@ -774,7 +774,14 @@ zc_status zc_stats(zc_ctx* ctx, double* phase_ms, uint32_t cap) {
     }
     out[i] = ms;
   }
-  out[6] = ctx->dom_phase < 6 ? out[ctx->dom_phase] : 0;
+  {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, ctx->ev[ctx->dom_a], ctx->ev[ctx->dom_b]) != cudaSuccess) {
+      cudaGetLastError();
+      ms = 0;
+    }
+    out[6] = ms;
+  }
   out[7] = ctx->dom_mulmods;
   out[8] = ctx->dom_bytes;
   out[9] = ctx->launches;

@@ -95,7 +95,7 @@ struct zc_ctx {
   uint32_t launches = 0;         // kernels launched by the last prove call
   double dom_mulmods = 0;        // algorithmic work of the dominant kernel launch
   double dom_bytes = 0;
-  int dom_phase = 2;             // phase index holding that launch
+  int dom_a = 2, dom_b = 3;      // events bracketing that launch
   int skip_point = 0;            // 0: derive H(1) from the claim (default), 1: derive H(0)
 };
 

@@ -1,13 +1,952 @@
-// zc_ntt.cu -- NTT-form ZeroCheck prover (Fig. side-by-side-zc, left).
+// zc_ntt.cu -- NTT-form ZeroCheck prover (Fig. side-by-side-zc, left;
+// Sec. 3.2).
+//
+//   N1  g_j <- INTT_H(e_j)                    (per column, size N)
+//   N2  for each coset slice s_j = 7 w_M^j H (j < s = M/N):
+//         ghat_j = NTT_N(g_j(k) (7 w_M^j)^k / N), fhat = gate(ghat),
+//         qhat = fhat / z_H, with z_H constant on the slice: 7^N w_s^j - 1
+//   N3  q <- INTT_D(qhat) = 7^-k M^-1 DFT_M^-1(qhat)
+//   N4  root(q), z = squeeze (again while z^N = 1)
+//   N5  openings g_j(z), q(z)
+//
+// Transforms are "four-step" (Bailey) factorisations done as passes over
+// HBM; each pass runs many sub-DFTs of length L <= 4096 in shared memory
+// (self-sorting Stockham stages of radix 8/4/2).  Digit orders are chosen so
+// that no pass ever transposes:
+//   * N1 is the reversed-input structure: its first pass reads the natural
+//     evaluations with a stride (a gather), its output is natural.
+//   * N2 is the natural-input structure: each slice comes out digit-reversed.
+//   * The gate is pointwise, so qhat keeps that order, which is exactly the
+//     input order of N3 written as a three-digit reversed-input transform
+//     (slice digit outermost); N3's output, q, is natural.
+// Twiddles between passes come from two-level power tables of the 2^30-th
+// root of unity (w^e = HI[e >> 15] * LO[e & 32767]).  The coset factor
+// (7 w_M^j)^k / N of N2 is a two-level table per slice applied on load, with
+// the Montgomery conversion folded in (inputs are canonical, "level 0").
+#include <algorithm>
+#include <cstring>
+
 #include "zc_internal.cuh"
 
 namespace zc {
 
+constexpr int kLog30 = 30;
+constexpr uint32_t kLoBits = 15;
+constexpr uint32_t kLoMask = (1u << kLoBits) - 1;
+constexpr int kMaxNttN = 24;
+
+struct NttTables {
+  bool ready = false;
+  fr* dft_fwd = nullptr;   // w_4096^m, m < 4096 (level 1)
+  fr* dft_inv = nullptr;
+  fr* wf_lo = nullptr;     // w_2^30^b, b < 2^15 (level 1)
+  fr* wf_hi = nullptr;     // w_2^30^(a 2^15)
+  fr* wi_lo = nullptr;     // inverse root
+  fr* wi_hi = nullptr;
+  fr* s7_lo = nullptr;     // 7^-b (level 0)
+  fr* s7_hi = nullptr;     // 7^-(a 2^15) (level 1)
+  void* mem = nullptr;
+};
+
+static NttTables g_tabs_by_dev[64];
+static std::mutex g_tabs_mu;
+
+struct NttTabArgs {
+  fr* dft_fwd; fr* dft_inv; fr* wf_lo; fr* wf_hi; fr* wi_lo; fr* wi_hi; fr* s7_lo; fr* s7_hi;
+  fr w30;        // 2^30-th root (level 1)
+  fr w30i;       // its inverse (level 1)
+  fr seveninv;   // 7^-1 (level 1)
+  const DevConst* C;
+};
+
+__device__ fr fr_pow_dev(fr base, uint64_t e, const DevConst* C) {  // level 1 in/out
+  fr acc = C->one;
+  while (e) {
+    if (e & 1) acc = fr_mul(acc, base);
+    base = fr_mul(base, base);
+    e >>= 1;
+  }
+  return acc;
+}
+
+__global__ void k_ntt_tables(NttTabArgs A) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const DevConst* C = A.C;
+  if (i < 4096) {
+    // w_4096 = w30^(2^18)
+    A.dft_fwd[i] = fr_pow_dev(A.w30, (uint64_t)i << 18, C);
+    A.dft_inv[i] = fr_pow_dev(A.w30i, (uint64_t)i << 18, C);
+  }
+  if (i < (1u << kLoBits)) {
+    A.wf_lo[i] = fr_pow_dev(A.w30, i, C);
+    A.wf_hi[i] = fr_pow_dev(A.w30, (uint64_t)i << kLoBits, C);
+    A.wi_lo[i] = fr_pow_dev(A.w30i, i, C);
+    A.wi_hi[i] = fr_pow_dev(A.w30i, (uint64_t)i << kLoBits, C);
+    A.s7_lo[i] = from_mont(fr_pow_dev(A.seveninv, i, C));          // level 0
+    A.s7_hi[i] = fr_pow_dev(A.seveninv, (uint64_t)i << kLoBits, C);  // level 1
+  }
+}
+
+// w^e for the 2^30-th root (or its inverse), e < 2^30, level 1
+__device__ __forceinline__ fr root_pow(const fr* lo, const fr* hi, uint32_t e) {
+  return fr_mul(ld_fr(hi + (e >> kLoBits)), ld_fr(lo + (e & kLoMask)));
+}
+
+// ---------------------------------------------------------------- passes --
+
+enum { PRE_NONE = 0, PRE_COSET = 1 };
+enum { POST_NONE = 0, POST_TW = 1, POST_OUTER = 2, POST_FINAL = 3 };
+
+struct NttPassArgs {
+  const fr* in[kMaxCols];
+  fr* out[kMaxCols];
+  uint32_t logL;          // sub-DFT length
+  uint32_t logW;          // sub-DFTs per CTA
+  // element (b, t) address: ((b >> lbdiv) * bs_hi) + (b & (bdiv-1)) * bs_lo + t * ts
+  uint32_t in_lbdiv, out_lbdiv;
+  uint64_t in_bs_hi, in_bs_lo, in_ts;
+  uint64_t out_bs_hi, out_bs_lo, out_ts;
+  const fr* dft;          // 4096-th roots, forward or inverse
+  int pre;
+  const fr* pre_lo;       // per-item coset tables (item stride pre_stride)
+  const fr* pre_hi;
+  uint32_t pre_shift;     // k = b * pre_kb + t * pre_kt; factor = hi[k >> shift] * lo[k & mask]
+  uint64_t pre_kb, pre_kt;
+  int post;
+  const fr* tw_lo;
+  const fr* tw_hi;
+  uint32_t tw_lbmod;      // POST_TW: e = (b mod 2^lbmod) * t
+  uint32_t tw_shift;      // exponent in the 2^30 table: (e mod 2^(30-shift)) << shift
+  uint32_t outer_lbdiv;   // POST_OUTER: e = (b >> lbdiv) * ((t << lbdiv) + (b mod 2^lbdiv))
+  uint64_t fin_N;         // POST_FINAL: k = fin_N * t + b
+};
+
+// radix-2/4/8 butterflies on x[0..R) in registers, X[k] = sum_r x[r] w_R^(rk)
+__device__ __forceinline__ void dft4(fr& a0, fr& a1, fr& a2, fr& a3, const fr& w4) {
+  fr u0 = fr_add(a0, a2), u1 = fr_sub(a0, a2);
+  fr v0 = fr_add(a1, a3), v1 = fr_mul(fr_sub(a1, a3), w4);
+  a0 = fr_add(u0, v0);
+  a2 = fr_sub(u0, v0);
+  a1 = fr_add(u1, v1);
+  a3 = fr_sub(u1, v1);
+}
+
+__device__ __forceinline__ void dft8(fr (&x)[8], const fr* tab) {
+  const fr w4 = ld_fr(tab + 1024), w8 = ld_fr(tab + 512), w83 = ld_fr(tab + 1536);
+  fr e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
+  fr o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+  dft4(e0, e1, e2, e3, w4);
+  dft4(o0, o1, o2, o3, w4);
+  o1 = fr_mul(o1, w8);
+  o2 = fr_mul(o2, w4);
+  o3 = fr_mul(o3, w83);
+  x[0] = fr_add(e0, o0);
+  x[4] = fr_sub(e0, o0);
+  x[1] = fr_add(e1, o1);
+  x[5] = fr_sub(e1, o1);
+  x[2] = fr_add(e2, o2);
+  x[6] = fr_sub(e2, o2);
+  x[3] = fr_add(e3, o3);
+  x[7] = fr_sub(e3, o3);
+}
+
+// One Stockham stage of radix R = 2^lr on the CTA tile sm[t * W + w]; each
+// thread owns 8 elements (8 / R independent groups).
+template <int LR>
+__device__ __forceinline__ void stockham_stage(fr* sm, uint32_t logL, uint32_t logW, uint32_t logNs,
+                                               const fr* tab) {
+  constexpr int R = 1 << LR;
+  constexpr int GROUPS = 8 / R;
+  const uint32_t L = 1u << logL, W = 1u << logW;
+  const uint32_t qL = L >> LR;   // L / R
+  const uint32_t ngroups = (L << logW) >> LR;
+  fr x[8];
+  uint32_t jj[GROUPS], ww[GROUPS];
+#pragma unroll
+  for (int g = 0; g < GROUPS; g++) {
+    uint32_t j_all = threadIdx.x * GROUPS + g;
+    uint32_t w = j_all & (W - 1), j = j_all >> logW;
+    jj[g] = j;
+    ww[g] = w;
+    if (j_all < ngroups) {
+#pragma unroll
+      for (int r = 0; r < R; r++) x[g * R + r] = sm[(j + r * qL) * W + w];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int g = 0; g < GROUPS; g++) {
+    if (threadIdx.x * GROUPS + g >= ngroups) continue;
+    const uint32_t j = jj[g];
+    const uint32_t k = j & ((1u << logNs) - 1);
+    if (logNs > 0) {
+      // twiddle w_{Ns R}^{r k} = tab[r k 4096 / (Ns R)]
+      const uint32_t sh = 12 - (logNs + LR);
+#pragma unroll
+      for (int r = 1; r < R; r++) x[g * R + r] = fr_mul(x[g * R + r], ld_fr(tab + ((r * k) << sh)));
+    }
+    if (R == 8) {
+      fr y[8];
+#pragma unroll
+      for (int r = 0; r < 8; r++) y[r] = x[r];
+      dft8(y, tab);
+#pragma unroll
+      for (int r = 0; r < 8; r++) x[r] = y[r];
+    } else if (R == 4) {
+      dft4(x[g * 4], x[g * 4 + 1], x[g * 4 + 2], x[g * 4 + 3], ld_fr(tab + 1024));
+    } else {
+      fr a = x[g * 2], b = x[g * 2 + 1];
+      x[g * 2] = fr_add(a, b);
+      x[g * 2 + 1] = fr_sub(a, b);
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < GROUPS; g++) {
+    if (threadIdx.x * GROUPS + g >= ngroups) continue;
+    const uint32_t j = jj[g], w = ww[g];
+    const uint32_t k = j & ((1u << logNs) - 1);
+    const uint32_t idxD = ((j >> logNs) << (logNs + LR)) + k;
+#pragma unroll
+    for (int r = 0; r < R; r++) sm[(idxD + (r << logNs)) * W + w] = x[g * R + r];
+  }
+  __syncthreads();
+}
+
+template <int TILE>
+__global__ void __launch_bounds__(TILE / 8, 1) k_ntt_pass(NttPassArgs A) {
+  extern __shared__ __align__(16) fr sm[];
+  const int item = blockIdx.y;
+  const fr* __restrict__ in = A.in[item];
+  fr* out = A.out[item];
+  const uint32_t logL = A.logL, logW = A.logW;
+  const uint32_t L = 1u << logL, W = 1u << logW;
+  const uint64_t b0 = (uint64_t)blockIdx.x << logW;
+  const uint32_t n_el = L << logW;  // <= TILE (smaller only for tiny transforms)
+  const bool in_t_fast = A.in_ts == 1, out_t_fast = A.out_ts == 1;
+  const uint64_t in_bdiv_mask = (1ull << A.in_lbdiv) - 1, out_bdiv_mask = (1ull << A.out_lbdiv) - 1;
+
+  // ---- load (with the coset factor when asked)
+  for (uint32_t idx = threadIdx.x; idx < n_el; idx += blockDim.x) {
+    uint32_t w, t;
+    if (in_t_fast) { t = idx & (L - 1); w = idx >> logL; }
+    else { w = idx & (W - 1); t = idx >> logW; }
+    const uint64_t b = b0 + w;
+    const uint64_t a = (b >> A.in_lbdiv) * A.in_bs_hi + (b & in_bdiv_mask) * A.in_bs_lo + t * A.in_ts;
+    fr x = ld_fr(in + a);
+    if (A.pre == PRE_COSET) {
+      const uint64_t k = b * A.pre_kb + t * A.pre_kt;
+      // one slice per launch: every column uses the same tables
+      fr f = fr_mul(ld_fr(A.pre_hi + (k >> A.pre_shift)),
+                    ld_fr(A.pre_lo + (k & ((1ull << A.pre_shift) - 1))));
+      x = fr_mul(x, f);
+    }
+    sm[t * W + w] = x;
+  }
+  __syncthreads();
+
+  // ---- Stockham stages: radix 8 while >= 3 bits remain, then 4 or 2
+  uint32_t logNs = 0;
+  while (logL - logNs >= 3) {
+    stockham_stage<3>(sm, logL, logW, logNs, A.dft);
+    logNs += 3;
+  }
+  if (logL - logNs == 2) stockham_stage<2>(sm, logL, logW, logNs, A.dft);
+  else if (logL - logNs == 1) stockham_stage<1>(sm, logL, logW, logNs, A.dft);
+
+  // ---- store (with the twiddle / final scale)
+  for (uint32_t idx = threadIdx.x; idx < n_el; idx += blockDim.x) {
+    uint32_t w, t;
+    if (out_t_fast) { t = idx & (L - 1); w = idx >> logL; }
+    else { w = idx & (W - 1); t = idx >> logW; }
+    const uint64_t b = b0 + w;
+    fr y = sm[t * W + w];
+    if (A.post == POST_TW) {
+      const uint64_t e = (b & ((1ull << A.tw_lbmod) - 1)) * t;
+      const uint32_t ex = (uint32_t)((e << A.tw_shift) & ((1ull << kLog30) - 1));
+      if (ex) y = fr_mul(y, root_pow(A.tw_lo, A.tw_hi, ex));
+    } else if (A.post == POST_OUTER) {
+      const uint64_t jsl = b >> A.outer_lbdiv;
+      const uint64_t kp = ((uint64_t)t << A.outer_lbdiv) + (b & ((1ull << A.outer_lbdiv) - 1));
+      const uint64_t e = jsl * kp;
+      const uint32_t ex = (uint32_t)((e << A.tw_shift) & ((1ull << kLog30) - 1));
+      if (ex) y = fr_mul(y, root_pow(A.tw_lo, A.tw_hi, ex));
+    } else if (A.post == POST_FINAL) {
+      const uint64_t k = A.fin_N * t + b;
+      fr f = fr_mul(ld_fr(A.tw_hi + (k >> kLoBits)), ld_fr(A.tw_lo + (k & kLoMask)));  // level 0
+      y = fr_mul(y, f);
+    }
+    const uint64_t a = (b >> A.out_lbdiv) * A.out_bs_hi + (b & out_bdiv_mask) * A.out_bs_lo + t * A.out_ts;
+    st_fr(out + a, y);
+  }
+}
+
+// ------------------------------------------------------- per-proof kernels --
+
+struct NttSliceTabArgs {
+  fr* lo;            // [s][2^hbits] c_j^b (level 1)
+  fr* hi;            // [s][2^(n-hbits)] c_j^(a 2^hbits) / N (level 2)
+  fr* zinv;          // [s] (7^N w_s^j - 1)^-1 M^-1 (level 1)
+  uint32_t s, n, hbits, logm;
+  fr ninv_l2;        // N^-1 at level 2
+  fr minv_l1;        // M^-1 at level 1
+  const fr* wf_lo; const fr* wf_hi;
+  const DevConst* C;
+};
+
+__global__ void k_ntt_slice_tables(NttSliceTabArgs A) {
+  const DevConst* C = A.C;
+  const uint32_t nlo = 1u << A.hbits, nhi = 1u << (A.n - A.hbits);
+  const uint32_t per = nlo + nhi;
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < (uint64_t)A.s * per) {
+    const uint32_t j = (uint32_t)(i / per), e = (uint32_t)(i % per);
+    // c_j = 7 w_M^j
+    const uint32_t ex = (j << (kLog30 - A.logm)) & ((1u << kLog30) - 1);
+    fr cj = fr_mul(C->small[7], root_pow(A.wf_lo, A.wf_hi, ex));
+    if (e < nlo) {
+      A.lo[(size_t)j * nlo + e] = fr_pow_dev(cj, e, C);
+    } else {
+      const uint32_t a = e - nlo;
+      fr v = fr_pow_dev(cj, (uint64_t)a << A.hbits, C);
+      A.hi[(size_t)j * nhi + a] = fr_mul(v, A.ninv_l2);  // level 2
+    }
+  }
+  if (i < A.s) {
+    // z_H on slice j: (7 w_M^j w_N^i)^N - 1 = 7^N w_s^j - 1
+    const uint32_t j = (uint32_t)i;
+    fr s7n = fr_pow_dev(C->small[7], 1ull << A.n, C);
+    const uint32_t ex = (j << (kLog30 - (A.logm - A.n))) & ((1u << kLog30) - 1);
+    fr zj = fr_sub(fr_mul(s7n, root_pow(A.wf_lo, A.wf_hi, ex)), C->one);
+    fr inv = fr_inv_binary(from_mont(zj));        // canonical
+    A.zinv[j] = fr_mul(fr_mul(inv, C->r2), A.minv_l1);
+  }
+}
+
+struct NttGateArgs {
+  const fr* col[kMaxCols];  // slice evaluations, level 1
+  fr* qhat;                 // slice output
+  const fr* zinv;           // constant of this slice
+  uint64_t N;
+  uint32_t gate, d;
+};
+
+__global__ void __launch_bounds__(256) k_ntt_gate(NttGateArgs A) {
+  const fr zi = ld_fr(A.zinv);
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < A.N;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    fr f;
+    if (A.gate == ZC_GATE_PLONK) {
+      fr b = ld_fr(A.col[6] + p);
+      fr u = fr_add(ld_fr(A.col[0] + p), fr_mul(ld_fr(A.col[2] + p), b));
+      f = fr_mul(ld_fr(A.col[5] + p), u);
+      f = fr_add(f, fr_mul(ld_fr(A.col[1] + p), b));
+      f = fr_add(f, fr_mul(ld_fr(A.col[3] + p), ld_fr(A.col[7] + p)));
+      f = fr_add(f, ld_fr(A.col[4] + p));
+    } else {
+      f = ld_fr(A.col[0] + p);
+      for (uint32_t j = 1; j < A.d; j++) f = fr_mul(f, ld_fr(A.col[j] + p));
+      f = fr_sub(f, ld_fr(A.col[A.d] + p));
+    }
+    st_fr(A.qhat + p, fr_mul(f, zi));
+  }
+}
+
+// ----------------------------------------------------- transcript (words) --
+
+// S <- SHA-256(S | m) for a 32-byte message m (one block + padding block)
+__device__ void tr_absorb32(uint32_t S[8], const uint8_t* m) {
+  uint32_t w[16];
+  for (int i = 0; i < 8; i++) w[i] = S[i];
+  for (int i = 0; i < 8; i++)
+    w[8 + i] = ((uint32_t)m[4 * i] << 24) | ((uint32_t)m[4 * i + 1] << 16) |
+               ((uint32_t)m[4 * i + 2] << 8) | m[4 * i + 3];
+  uint32_t h[8];
+  sha256_init(h);
+  sha256_compress(h, w);
+  for (int i = 0; i < 16; i++) w[i] = 0;
+  w[0] = 0x80000000u;
+  w[15] = 512;
+  sha256_compress(h, w);
+  for (int i = 0; i < 8; i++) S[i] = h[i];
+}
+
+__device__ fr tr_squeeze_canon(uint32_t S[8]) {
+  uint32_t w[16];
+  for (int i = 0; i < 8; i++) w[i] = S[i];
+  w[8] = 0x43800000u;
+  for (int i = 9; i < 15; i++) w[i] = 0;
+  w[15] = 33 * 8;
+  uint32_t h[8];
+  sha256_init(h);
+  sha256_compress(h, w);
+  for (int i = 0; i < 8; i++) S[i] = h[i];
+  fr x;
+  for (int i = 0; i < 8; i++) x.v[i] = sha_bswap(h[i]);
+  for (int k = 0; k < 2; k++) {
+    if (!fr_is_canonical(x)) {
+      int64_t br = 0;
+      for (int i = 0; i < 8; i++) {
+        int64_t dd = (int64_t)x.v[i] - p_limb(i) + br;
+        x.v[i] = (uint32_t)dd;
+        br = dd >> 32;
+      }
+    }
+  }
+  return x;
+}
+
+struct NttZArgs {
+  NttState* st;
+  const uint8_t* roots;  // c column roots then root(q)
+  int c;
+  uint32_t n;
+  uint32_t S0[8];
+  fr* zpow;              // z^(2^i), i < 31 (level 1)
+  const DevConst* C;
+};
+
+__global__ void k_ntt_z(NttZArgs A) {
+  if (threadIdx.x != 0) return;
+  const DevConst* C = A.C;
+  uint32_t S[8];
+  for (int i = 0; i < 8; i++) S[i] = A.S0[i];
+  for (int j = 0; j <= A.c; j++) tr_absorb32(S, A.roots + 32 * j);
+  fr z;
+  uint32_t err = 1;
+  for (int tries = 0; tries < 64; tries++) {
+    z = fr_mul(tr_squeeze_canon(S), C->r2);
+    fr zn = z;
+    for (uint32_t i = 0; i < A.n; i++) zn = fr_mul(zn, zn);
+    if (!fr_equal(zn, C->one)) {
+      err = 0;
+      A.st->zpow_n = zn;
+      break;
+    }
+  }
+  A.st->z = z;
+  A.st->err |= err;
+  fr p = z;
+  for (int i = 0; i < 31; i++) {
+    A.zpow[i] = p;
+    p = fr_mul(p, p);
+  }
+}
+
+// Evaluate sum_k x[k] z^k for each item (level-0 x); every warp takes a
+// contiguous segment, lane l the elements seg + l + 32 m, Horner in z^32.
+struct NttOpenArgs {
+  const fr* x[kMaxCols + 1];
+  uint64_t len[kMaxCols + 1];
+  const fr* zpow;     // z^(2^i)
+  fr* partials;       // [item][blocks]
+  uint32_t nblk;
+  uint32_t seg;       // elements per warp segment (multiple of 32)
+};
+
+__device__ fr zpow_of(const fr* zp, uint64_t e, const fr& one) {
+  fr acc = one;
+  for (int i = 0; e; i++, e >>= 1)
+    if (e & 1) acc = fr_mul(acc, ld_fr(zp + i));
+  return acc;
+}
+
+__global__ void __launch_bounds__(256) k_ntt_open(NttOpenArgs A, const DevConst* C) {
+  const int item = blockIdx.y;
+  const fr* x = A.x[item];
+  const uint64_t len = A.len[item];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const fr z32 = ld_fr(A.zpow + 5);
+  fr tot = fr_zero();
+  const uint64_t nseg = (len + A.seg - 1) / A.seg;
+  for (uint64_t sgi = (uint64_t)blockIdx.x * 8 + warp; sgi < nseg; sgi += (uint64_t)gridDim.x * 8) {
+    const uint64_t base = sgi * A.seg;
+    const uint64_t cnt = A.seg < len - base ? A.seg : len - base;
+    const uint32_t mcount = (uint32_t)((cnt + 31) / 32);
+    fr acc = fr_zero();
+    for (int32_t m = (int32_t)mcount - 1; m >= 0; m--) {
+      acc = fr_mul(acc, z32);
+      const uint64_t k = base + lane + 32ull * (uint32_t)m;
+      if (k < len) acc = fr_add(acc, ld_fr(x + k));
+    }
+    acc = fr_mul(acc, zpow_of(A.zpow, base + lane, C->one));
+    tot = fr_add(tot, acc);
+  }
+  __shared__ fr red[8];
+  tot = warp_sum(tot);
+  if (lane == 0) red[warp] = tot;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    fr s = fr_zero();
+    for (int w = 0; w < 8; w++) s = fr_add(s, red[w]);
+    st_fr(A.partials + (size_t)item * A.nblk + blockIdx.x, s);
+  }
+}
+
+struct NttFinalArgs {
+  const fr* partials;
+  uint32_t nblk;
+  int c;
+  uint32_t gate, n, d, logm;
+  fr ninv_l1;
+  const uint8_t* qroot;
+  NttState* st;
+  uint8_t* proof;
+};
+
+__global__ void k_ntt_final(NttFinalArgs A) {
+  const int item = threadIdx.x;
+  if (item <= A.c) {
+    fr s = fr_zero();
+    for (uint32_t b = 0; b < A.nblk; b++) s = fr_add(s, ld_fr_cg(A.partials + (size_t)item * A.nblk + b));
+    if (item < A.c) s = fr_mul(s, A.ninv_l1);  // coefficients carry the factor N
+    uint8_t* o = A.proof + 52 + 32 * item;
+    for (int i = 0; i < 8; i++)
+      for (int b = 0; b < 4; b++) o[4 * i + b] = (uint8_t)(s.v[i] >> (8 * b));
+  }
+  if (item == 0) {
+    const char* mg = A.st->err ? "ZCE!" : "ZCN1";
+    for (int b = 0; b < 4; b++) A.proof[b] = (uint8_t)mg[b];
+    uint32_t hv[4] = {A.gate, A.n, A.d, A.logm};
+    for (int q = 0; q < 4; q++)
+      for (int b = 0; b < 4; b++) A.proof[4 + 4 * q + b] = (uint8_t)(hv[q] >> (8 * b));
+    for (int b = 0; b < 32; b++) A.proof[20 + b] = A.qroot[b];
+  }
+}
+
+struct NttCheckArgs {
+  const fr* col[kMaxCols];
+  uint64_t N;
+  int c;
+  NttState* st;
+};
+
+// canonical check of the input columns (a value >= r sets the error flag)
+__global__ void k_ntt_check(NttCheckArgs A) {
+  const int j = blockIdx.y;
+  uint32_t bad = 0;
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < A.N;
+       p += (uint64_t)gridDim.x * blockDim.x)
+    bad |= !fr_is_canonical(ld_fr(A.col[j] + p));
+  if (bad) atomicOr(&A.st->err, 1u);
+}
+
+__global__ void k_ntt_state_init(NttState* st) {
+  if (threadIdx.x == 0) st->err = 0;
+}
+
+// ------------------------------------------------------------------ host --
+
+static zc_status ensure_tables(zc_ctx* ctx, cudaStream_t st, NttTables** out) {
+  std::lock_guard<std::mutex> lk(g_tabs_mu);
+  NttTables& T = g_tabs_by_dev[ctx->device];
+  if (!T.ready) {
+    const size_t n4 = 4096, n15 = 1u << kLoBits;
+    size_t bytes = sizeof(fr) * (2 * n4 + 6 * n15);
+    if (cudaMalloc(&T.mem, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->err = "cudaMalloc NTT tables";
+      return ZC_ERR_OOM;
+    }
+    fr* p = static_cast<fr*>(T.mem);
+    T.dft_fwd = p; p += n4;
+    T.dft_inv = p; p += n4;
+    T.wf_lo = p; p += n15;
+    T.wf_hi = p; p += n15;
+    T.wi_lo = p; p += n15;
+    T.wi_hi = p; p += n15;
+    T.s7_lo = p; p += n15;
+    T.s7_hi = p; p += n15;
+    const DevConst& C = ctx->hconst;
+    // w_2^32 = 7^((r-1)/2^32); w_2^30 = (w_2^32)^4
+    uint32_t e[8];
+    for (int i = 0; i < 7; i++) e[i] = p_limb(i + 1);
+    e[7] = 0;
+    fr seven = h_from_u64(7);
+    fr acc = h_from_u64(1), base = seven;
+    for (int i = 0; i < 8; i++)
+      for (int b = 0; b < 32; b++) {
+        if ((e[i] >> b) & 1) acc = h_canon_mul(acc, base, C);
+        base = h_canon_mul(base, base, C);
+      }
+    fr w30 = h_canon_mul(acc, acc, C);
+    w30 = h_canon_mul(w30, w30, C);
+    NttTabArgs a{};
+    a.dft_fwd = T.dft_fwd; a.dft_inv = T.dft_inv;
+    a.wf_lo = T.wf_lo; a.wf_hi = T.wf_hi; a.wi_lo = T.wi_lo; a.wi_hi = T.wi_hi;
+    a.s7_lo = T.s7_lo; a.s7_hi = T.s7_hi;
+    a.w30 = fr_mul_g(w30, C.r2);
+    a.w30i = fr_mul_g(h_inv(w30, C), C.r2);
+    a.seveninv = fr_mul_g(h_inv(seven, C), C.r2);
+    a.C = ctx->dconst;
+    k_ntt_tables<<<(n15 + 255) / 256, 256, 0, st>>>(a);
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+      ctx->err = "NTT table set-up failed";
+      return ZC_ERR_CUDA;
+    }
+    T.ready = true;
+  }
+  *out = &T;
+  return ZC_OK;
+}
+
+// launch one batched pass over `items` columns
+static zc_status run_pass(zc_ctx* ctx, cudaStream_t st, NttPassArgs& a, int items, uint64_t B) {
+  const uint32_t logL = a.logL;
+  const uint32_t logTile = logL >= 11 ? 12 : 11;
+  a.logW = logTile - logL;
+  while (a.logW > 0 && (1ull << a.logW) > B) a.logW--;
+  const uint64_t W = 1ull << a.logW;
+  uint64_t blocks = (B + W - 1) / W;
+  if (B % W) {
+    ctx->err = "NTT pass: batch not a multiple of the tile";
+    return ZC_ERR_ARG;
+  }
+  dim3 grid((unsigned)blocks, (unsigned)items);
+  if (logTile == 12) {
+    k_ntt_pass<4096><<<grid, 512, 4096 * sizeof(fr), st>>>(a);
+  } else {
+    k_ntt_pass<2048><<<grid, 256, 2048 * sizeof(fr), st>>>(a);
+  }
+  ctx->launches++;
+  return ZC_OK;
+}
+
+static void pass_defaults(NttPassArgs& a) {
+  std::memset(&a, 0, sizeof a);
+  a.in_lbdiv = 63;
+  a.out_lbdiv = 63;
+}
+
 zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, int on_dev,
                     const uint8_t (*roots)[32], cudaStream_t st, uint8_t* proof,
                     bool proof_on_dev, void* q_out, int q_on_dev) {
-  ctx->err = "NTT form not built yet";
-  return ZC_ERR_UNSUPPORTED;
+  const uint32_t gate = p->gate, n = p->n, d = p->d;
+  if (n > (uint32_t)kMaxNttN) {
+    ctx->err = "NTT form supports n <= 24";
+    return ZC_ERR_UNSUPPORTED;
+  }
+  uint32_t lb = p->log_blowup;
+  if (!lb) while ((1u << lb) < d) lb++;
+  const uint32_t logm = n + lb;
+  if (logm > (uint32_t)kLog30) {
+    ctx->err = "domain larger than 2^30";
+    return ZC_ERR_UNSUPPORTED;
+  }
+  const int c = gate_ncols(gate, d);
+  const uint64_t N = 1ull << n, M = 1ull << logm, s = 1ull << lb;
+  const size_t psize = 20 + 32 + 32 * ((size_t)c + 1);
+  static int attr_done[64] = {0};
+  if (!attr_done[ctx->device]) {
+    cudaFuncSetAttribute(k_ntt_pass<4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4096 * 32);
+    cudaFuncSetAttribute(k_ntt_pass<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2048 * 32);
+    attr_done[ctx->device] = 1;
+  }
+  NttTables* T = nullptr;
+  zc_status s0 = ensure_tables(ctx, st, &T);
+  if (s0 != ZC_OK) return s0;
+
+  const uint32_t hbits = (n + 1) / 2;
+  const uint32_t nlo = 1u << hbits, nhi = 1u << (n - hbits);
+  const uint32_t nblk_open = 2 * (uint32_t)ctx->sm_count;
+  const bool q_direct = q_out && q_on_dev;
+  size_t need = 0;
+  need += 2 * align_up(sizeof(fr) * N, 256) * c;    // coefficients + slice buffer
+  need += align_up(sizeof(fr) * M, 256);            // qhat
+  if (!q_direct) need += align_up(sizeof(fr) * M, 256);
+  need += align_up(sizeof(fr) * s * (nlo + nhi), 256) + align_up(sizeof(fr) * s, 256);
+  need += align_up(sizeof(fr) * (c + 1) * nblk_open, 256) + align_up(sizeof(fr) * 32, 256);
+  need += align_up(sizeof(NttState), 256) + align_up(psize, 256) + align_up(32 * (size_t)(c + 1), 256);
+  need += root_scratch_bytes(c, N) + root_scratch_bytes(1, M) + 8192;
+  zc_status s1 = ensure_arena(ctx, need);
+  if (s1 != ZC_OK) return s1;
+  Arena& ar = ctx->arena;
+  ar.reset();
+  fr* coef[kMaxCols];
+  fr* slb[kMaxCols];
+  for (int j = 0; j < c; j++) coef[j] = ar.take<fr>(N);
+  for (int j = 0; j < c; j++) slb[j] = ar.take<fr>(N);
+  fr* qhat = ar.take<fr>(M);
+  fr* qv = q_direct ? static_cast<fr*>(q_out) : ar.take<fr>(M);
+  fr* tlo = ar.take<fr>(s * nlo);
+  fr* thi = ar.take<fr>(s * nhi);
+  fr* zinv = ar.take<fr>(s);
+  fr* opart = ar.take<fr>((size_t)(c + 1) * nblk_open);
+  fr* zpow = ar.take<fr>(32);
+  NttState* dstate = ar.take<NttState>(1);
+  uint8_t* dproof = ar.take<uint8_t>(psize);
+  uint8_t* droots = ar.take<uint8_t>(32 * (size_t)(c + 1));
+  if (!droots) {
+    ctx->err = "scratch arena too small";
+    return ZC_ERR_OOM;
+  }
+  ctx->launches = 0;
+  ctx->nev = 7;
+
+  const fr* src[kMaxCols];
+  if (on_dev) {
+    for (int j = 0; j < c; j++) src[j] = static_cast<const fr*>(cols[j]);
+  } else {
+    for (int j = 0; j < c; j++) {
+      ZC_CUDA_TRY(ctx, cudaMemcpyAsync(slb[j], cols[j], N * sizeof(fr), cudaMemcpyHostToDevice, st));
+      src[j] = slb[j];
+    }
+  }
+  ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[0], st));
+  k_ntt_state_init<<<1, 32, 0, st>>>(dstate);
+  ctx->launches++;
+  {
+    NttCheckArgs ca{};
+    for (int j = 0; j < c; j++) ca.col[j] = src[j];
+    ca.N = N;
+    ca.c = c;
+    ca.st = dstate;
+    uint32_t gx = (uint32_t)std::min<uint64_t>((N + 255) / 256, 64);
+    k_ntt_check<<<dim3(gx, c), 256, 0, st>>>(ca);
+    ctx->launches++;
+  }
+  if (roots) {
+    std::memcpy(ctx->pinned, roots, 32 * (size_t)c);
+    ZC_CUDA_TRY(ctx, cudaMemcpyAsync(droots, ctx->pinned, 32 * (size_t)c, cudaMemcpyHostToDevice, st));
+  } else {
+    zc_status rs = launch_roots(ctx, src, c, N, droots, st);
+    if (rs != ZC_OK) return rs;
+  }
+  ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[1], st));
+
+  // per-slice coset tables and z_H inverses
+  const DevConst& C = ctx->hconst;
+  fr ninv = h_inv(h_from_u64(N), C), minv = h_inv(h_from_u64(M), C);
+  {
+    NttSliceTabArgs ta{};
+    ta.lo = tlo;
+    ta.hi = thi;
+    ta.zinv = zinv;
+    ta.s = (uint32_t)s;
+    ta.n = n;
+    ta.hbits = hbits;
+    ta.logm = logm;
+    ta.ninv_l2 = fr_mul_g(fr_mul_g(ninv, C.r2), C.r2);
+    ta.minv_l1 = fr_mul_g(minv, C.r2);
+    ta.wf_lo = T->wf_lo;
+    ta.wf_hi = T->wf_hi;
+    ta.C = ctx->dconst;
+    uint64_t tot = s * (nlo + nhi);
+    k_ntt_slice_tables<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(ta);
+    ctx->launches++;
+  }
+
+  const bool two = n > 12;
+  const uint32_t l1 = two ? (n + 1) / 2 : n;   // first digit
+  const uint32_t l2 = two ? n / 2 : 0;         // second digit
+  const uint64_t L1 = 1ull << l1, L2 = 1ull << l2;
+  zc_status rs;
+
+  // ---- N1: g_j = DFT^-1(e_j) (the factor 1/N is applied later), natural out
+  if (two) {
+    NttPassArgs a;
+    pass_defaults(a);
+    for (int j = 0; j < c; j++) {
+      a.in[j] = src[j];
+      a.out[j] = coef[j];
+    }
+    a.logL = l2;                       // rows of length L2 over i2
+    a.in_bs_lo = 1; a.in_ts = L1;      // element (i1, i2) read from e[i1 + L1 i2]
+    a.out_bs_lo = L2; a.out_ts = 1;
+    a.dft = T->dft_inv;
+    a.post = POST_TW; a.tw_lo = T->wi_lo; a.tw_hi = T->wi_hi;
+    a.tw_lbmod = l1; a.tw_shift = kLog30 - n;
+    if ((rs = run_pass(ctx, st, a, c, L1)) != ZC_OK) return rs;
+    pass_defaults(a);
+    for (int j = 0; j < c; j++) {
+      a.in[j] = coef[j];
+      a.out[j] = coef[j];
+    }
+    a.logL = l1;                       // columns of length L1
+    a.in_bs_lo = 1; a.in_ts = L2;
+    a.out_bs_lo = 1; a.out_ts = L2;
+    a.dft = T->dft_inv;
+    if ((rs = run_pass(ctx, st, a, c, L2)) != ZC_OK) return rs;
+  } else {
+    NttPassArgs a;
+    pass_defaults(a);
+    for (int j = 0; j < c; j++) {
+      a.in[j] = src[j];
+      a.out[j] = coef[j];
+    }
+    a.logL = n;
+    a.in_bs_lo = 0; a.in_ts = 1;
+    a.out_bs_lo = 0; a.out_ts = 1;
+    a.dft = T->dft_inv;
+    if ((rs = run_pass(ctx, st, a, c, 1)) != ZC_OK) return rs;
+  }
+  ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[2], st));
+
+  // ---- N2: per slice, coset NTT of every column, gate, divide by z_H
+  for (uint64_t j = 0; j < s; j++) {
+    NttPassArgs a;
+    pass_defaults(a);
+    for (int i = 0; i < c; i++) {
+      a.in[i] = coef[i];
+      a.out[i] = slb[i];
+    }
+    a.pre = PRE_COSET;
+    a.pre_lo = tlo + j * nlo;
+    a.pre_hi = thi + j * nhi;
+    a.pre_shift = hbits;
+    a.dft = T->dft_fwd;
+    if (two) {
+      a.logL = l1;                     // columns over k1: k = L2 k1 + k2
+      a.in_bs_lo = 1; a.in_ts = L2;
+      a.out_bs_lo = 1; a.out_ts = L2;
+      a.pre_kb = 1; a.pre_kt = L2;
+      a.post = POST_TW; a.tw_lo = T->wf_lo; a.tw_hi = T->wf_hi;
+      a.tw_lbmod = l2; a.tw_shift = kLog30 - n;
+      if ((rs = run_pass(ctx, st, a, c, L2)) != ZC_OK) return rs;
+      if (j == 0) ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[7], st));
+      pass_defaults(a);
+      for (int i = 0; i < c; i++) {
+        a.in[i] = slb[i];
+        a.out[i] = slb[i];
+      }
+      a.logL = l2;                     // rows over k2
+      a.in_bs_lo = L2; a.in_ts = 1;
+      a.out_bs_lo = L2; a.out_ts = 1;
+      a.dft = T->dft_fwd;
+      if ((rs = run_pass(ctx, st, a, c, L1)) != ZC_OK) return rs;
+    } else {
+      a.logL = n;
+      a.in_bs_lo = 0; a.in_ts = 1;
+      a.out_bs_lo = 0; a.out_ts = 1;
+      a.pre_kb = 0; a.pre_kt = 1;
+      if ((rs = run_pass(ctx, st, a, c, 1)) != ZC_OK) return rs;
+      if (j == 0) ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[7], st));
+    }
+    NttGateArgs ga{};
+    for (int i = 0; i < c; i++) ga.col[i] = slb[i];
+    ga.qhat = qhat + j * N;
+    ga.zinv = zinv + j;
+    ga.N = N;
+    ga.gate = gate;
+    ga.d = d;
+    uint32_t gb = (uint32_t)std::min<uint64_t>((N + 255) / 256, (uint64_t)ctx->sm_count * 8);
+    k_ntt_gate<<<gb, 256, 0, st>>>(ga);
+    ctx->launches++;
+  }
+  ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[3], st));
+
+  // ---- N3: q = 7^-k M^-1 DFT_M^-1(qhat), digits (s, L1, L2) or (s, N)
+  {
+    NttPassArgs a;
+    if (two) {
+      pass_defaults(a);
+      a.in[0] = qhat; a.out[0] = qhat;
+      a.logL = l2;                     // rows (j, i2) over i3
+      a.in_bs_lo = L2; a.in_ts = 1;
+      a.out_bs_lo = L2; a.out_ts = 1;
+      a.dft = T->dft_inv;
+      a.post = POST_TW; a.tw_lo = T->wi_lo; a.tw_hi = T->wi_hi;
+      a.tw_lbmod = l1; a.tw_shift = kLog30 - n;
+      if ((rs = run_pass(ctx, st, a, 1, s * L1)) != ZC_OK) return rs;
+      pass_defaults(a);
+      a.in[0] = qhat; a.out[0] = qhat;
+      a.logL = l1;                     // columns (j, k3) over i2 within a slice
+      a.in_lbdiv = l2; a.in_bs_hi = N; a.in_bs_lo = 1; a.in_ts = L2;
+      a.out_lbdiv = l2; a.out_bs_hi = N; a.out_bs_lo = 1; a.out_ts = L2;
+      a.dft = T->dft_inv;
+      a.post = POST_OUTER; a.tw_lo = T->wi_lo; a.tw_hi = T->wi_hi;
+      a.outer_lbdiv = l2; a.tw_shift = kLog30 - logm;
+      if ((rs = run_pass(ctx, st, a, 1, s * L2)) != ZC_OK) return rs;
+    } else {
+      pass_defaults(a);
+      a.in[0] = qhat; a.out[0] = qhat;
+      a.logL = n;                      // one row per slice
+      a.in_bs_lo = N; a.in_ts = 1;
+      a.out_bs_lo = N; a.out_ts = 1;
+      a.dft = T->dft_inv;
+      a.post = POST_OUTER; a.tw_lo = T->wi_lo; a.tw_hi = T->wi_hi;
+      a.outer_lbdiv = 0; a.tw_shift = kLog30 - logm;
+      if ((rs = run_pass(ctx, st, a, 1, s)) != ZC_OK) return rs;
+    }
+    pass_defaults(a);
+    a.in[0] = qhat; a.out[0] = qv;
+    a.logL = lb;                       // across slices
+    a.in_bs_lo = 1; a.in_ts = N;
+    a.out_bs_lo = 1; a.out_ts = N;
+    a.dft = T->dft_inv;
+    a.post = POST_FINAL; a.tw_lo = T->s7_lo; a.tw_hi = T->s7_hi;
+    a.fin_N = N;
+    if ((rs = run_pass(ctx, st, a, 1, N)) != ZC_OK) return rs;
+  }
+  ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[4], st));
+
+  // ---- N4: root(q), z
+  {
+    const fr* qp[1] = {qv};
+    if ((rs = launch_roots(ctx, qp, 1, M, droots + 32 * (size_t)c, st)) != ZC_OK) return rs;
+    NttZArgs za{};
+    za.st = dstate;
+    za.roots = droots;
+    za.c = c;
+    za.n = n;
+    transcript_init_words(za.S0, ZC_FORM_NTT, gate, n, d, logm);
+    za.zpow = zpow;
+    za.C = ctx->dconst;
+    k_ntt_z<<<1, 32, 0, st>>>(za);
+    ctx->launches++;
+  }
+  ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[5], st));
+
+  // ---- N5, N6: openings and the proof
+  {
+    NttOpenArgs oa{};
+    for (int j = 0; j < c; j++) {
+      oa.x[j] = coef[j];
+      oa.len[j] = N;
+    }
+    oa.x[c] = qv;
+    oa.len[c] = M;
+    oa.zpow = zpow;
+    oa.partials = opart;
+    oa.nblk = nblk_open;
+    oa.seg = 32 * 128;
+    k_ntt_open<<<dim3(nblk_open, c + 1), 256, 0, st>>>(oa, ctx->dconst);
+    ctx->launches++;
+    NttFinalArgs fa{};
+    fa.partials = opart;
+    fa.nblk = nblk_open;
+    fa.c = c;
+    fa.gate = gate;
+    fa.n = n;
+    fa.d = d;
+    fa.logm = logm;
+    fa.ninv_l1 = fr_mul_g(ninv, C.r2);
+    fa.qroot = droots + 32 * (size_t)c;
+    fa.st = dstate;
+    fa.proof = dproof;
+    k_ntt_final<<<1, 128, 0, st>>>(fa);
+    ctx->launches++;
+  }
+  ZC_CUDA_TRY(ctx, cudaGetLastError());
+  ZC_CUDA_TRY(ctx, cudaMemcpyAsync(proof, dproof, psize,
+                                   proof_on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                   st));
+  if (q_out && !q_direct)
+    ZC_CUDA_TRY(ctx, cudaMemcpyAsync(q_out, qv, M * sizeof(fr), cudaMemcpyDeviceToHost, st));
+  ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[6], st));
+  // dominant launch: one N2 column pass over all c columns of a slice
+  const double Lc = two ? (double)l1 : (double)n;
+  ctx->dom_mulmods = (double)c * (double)N / 2 * Lc + (double)c * (double)N;
+  ctx->dom_bytes = 2.0 * 32 * c * (double)N;
+  ctx->dom_a = 2;
+  ctx->dom_b = 7;
+  if (!proof_on_dev || !on_dev || (q_out && !q_direct)) {
+    ZC_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if (std::memcmp(proof, "ZCE!", 4) == 0) {
+      ctx->err = "column value >= r";
+      return ZC_ERR_ARG;
+    }
+  }
+  return ZC_OK;
 }
 
 }  // namespace zc

@@ -673,7 +673,8 @@ zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* col
   }
   ctx->launches = 0;
   ctx->nev = 6;
-  ctx->dom_phase = 2;
+  ctx->dom_a = 2;
+  ctx->dom_b = 3;
   // round-1 evaluation: per pair (d+1)(g+1)+1 mulmods, reads c*N*32 bytes
   const double g_mul = plonk ? 5.0 : (double)(d - 1);
   ctx->dom_mulmods = (double)(N / 2) * ((d + 1) * (g_mul + 1) + 1);

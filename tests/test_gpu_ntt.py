@@ -1,0 +1,95 @@
+"""NTT-form proofs and quotients from the CUDA library equal the oracle's,
+byte for byte (Fig. side-by-side-zc left; Sec. 3.2), from one-pass sizes
+through the two-pass four-step sizes, both gates, host and device buffers,
+satisfying and tampered witnesses; at the largest sizes the oracle's
+verifier checks the GPU output instead."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import proof_bytes, to_device
+from paper_2606_16146_gb300 import witness, zc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = zc.Context(0, max_n=24, max_d=32)
+    yield c
+    c.close()
+
+
+def _q_bytes(q):
+    import torch
+    if isinstance(q, torch.Tensor):
+        return q.cpu().numpy().tobytes()
+    return np.asarray(q).tobytes()
+
+
+def _check(ctx, gate, n, d, seed, tamper=False, device=True, roots=False, q_device=False):
+    import torch
+    cols = witness.generate(gate, n, d, seed, tamper=tamper)
+    want_p, want_q = oracle.prove_ntt(gate, n, d, cols)
+    rts = [oracle.root(c) for c in cols] if roots else None
+    q_out = None
+    if q_device:
+        q_out = torch.zeros(len(want_q), dtype=torch.uint8, device="cuda")
+    p, q = ctx.prove_ntt(gate, n, d, to_device(cols) if device else cols, roots=rts, q_out=q_out)
+    assert _q_bytes(q) == want_q.tobytes(), "quotient differs"
+    assert proof_bytes(p) == want_p, "proof differs"
+    return cols, proof_bytes(p), _q_bytes(q)
+
+
+@pytest.mark.parametrize("n", list(range(1, 16)))
+def test_plonk_sizes(ctx, n):
+    _check(ctx, 1, n, 3, 1000 + n)
+
+
+@pytest.mark.parametrize("d", [2, 3, 4, 5, 8, 16])
+@pytest.mark.parametrize("n", [2, 7, 13])
+def test_product_gate(ctx, n, d):
+    _check(ctx, 2, n, d, 2000 + d + n)
+
+
+@pytest.mark.parametrize("gate,n,d", [(1, 9, 3), (2, 13, 4)])
+def test_tampered_witness(ctx, gate, n, d):
+    cols, p, q = _check(ctx, gate, n, d, 55, tamper=True)
+    assert not zc.verify(gate, n, d, 2, cols, p, q=q)
+
+
+@pytest.mark.parametrize("device,roots,q_device", [(False, False, False), (True, True, True),
+                                                   (False, True, True), (True, False, False)])
+def test_buffers(ctx, device, roots, q_device):
+    _check(ctx, 1, 14, 3, 14, device=device, roots=roots, q_device=q_device)
+
+
+def test_noncanonical_rejected(ctx):
+    gate, n, d = 1, 6, 3
+    cols = witness.generate(gate, n, d, 3)
+    cols[5] = np.array(cols[5], copy=True)
+    cols[5][32 * 7 + 31] = 0xf0
+    with pytest.raises(zc.ZCError) as e:
+        ctx.prove_ntt(gate, n, d, cols)
+    assert e.value.status == 1
+
+
+@pytest.mark.parametrize("n", [20, 22])
+def test_plonk_config_sizes(ctx, n):
+    """Plonk gate at n = 20 and 22 (seeds 1000 + n), 4N coset."""
+    _check(ctx, 1, n, 3, 1000 + n, q_device=True)
+
+
+def test_product_degree32_mid(ctx):
+    _check(ctx, 2, 16, 32, 2032)
+
+
+@pytest.mark.parametrize("d", [2, 8, 32])
+def test_product_config_n22_verified(ctx, d):
+    """High-degree sweep at n = 22: the oracle's verifier accepts the GPU proof
+    and quotient (root of q, degree bound, q(z), openings, gate identity)."""
+    gate, n = 2, 22
+    cols = witness.generate(gate, n, d, 2000 + d)
+    p, q = ctx.prove_ntt(gate, n, d, to_device(cols))
+    pb = proof_bytes(p)
+    assert oracle.verify_ntt(gate, n, d, cols, pb, np.asarray(q))
