@@ -325,26 +325,28 @@ ZC_D fr fr_mul_cc(const fr& a, const fr& b) {
   return fr_reduce_final(t0, t1, t2, t3, t4, t5, t6, t7);
 }
 
-// CIOS with 64-bit partial products (mad.wide.u32, IMAD.WIDE on the integer
-// pipe).  Each row forms q_j = a_j b_i + t_j as one 64-bit value (it cannot
-// overflow), then a single add-with-carry chain joins lo(q_j) with
-// hi(q_{j-1}); the reduction row does the same with m r_j.  The wide
-// product issues at about 1.6x the combined rate of a mad.lo / mad.hi pair.
+// CIOS with 64-bit partial products (mul.wide.u32, IMAD.WIDE on the integer
+// pipe).  Each row forms the eight products q_j = a_j b_i as 64-bit values
+// with no addend (an addend pair costs extra register moves on the same
+// pipe), joins lo(q_j) with hi(q_{j-1}) in one add-with-carry chain and adds
+// that to t in a second chain on the ALU pipe.  The reduction row does the
+// same with m r_j; r_0 = 1 and r_1 = 2^32 - 1 need no multiplication
+// (m (2^32 - 1) has low word -m = t_0 and high word m - [m != 0]).
 #define ZC_LO(x) ((uint32_t)(x))
 #define ZC_HI(x) ((uint32_t)((x) >> 32))
 
 ZC_D void zc_row_wide(const fr& a, uint32_t bi, uint32_t& t0, uint32_t& t1, uint32_t& t2,
                       uint32_t& t3, uint32_t& t4, uint32_t& t5, uint32_t& t6, uint32_t& t7) {
   uint64_t q0, q1, q2, q3, q4, q5, q6, q7;
-  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(q0) : "r"(a.v[0]), "r"(bi), "l"((uint64_t)t0));
-  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(q1) : "r"(a.v[1]), "r"(bi), "l"((uint64_t)t1));
-  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(q2) : "r"(a.v[2]), "r"(bi), "l"((uint64_t)t2));
-  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(q3) : "r"(a.v[3]), "r"(bi), "l"((uint64_t)t3));
-  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(q4) : "r"(a.v[4]), "r"(bi), "l"((uint64_t)t4));
-  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(q5) : "r"(a.v[5]), "r"(bi), "l"((uint64_t)t5));
-  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(q6) : "r"(a.v[6]), "r"(bi), "l"((uint64_t)t6));
-  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(q7) : "r"(a.v[7]), "r"(bi), "l"((uint64_t)t7));
-  uint32_t u0 = ZC_LO(q0), u1, u2, u3, u4, u5, u6, u7, u8;
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(q0) : "r"(a.v[0]), "r"(bi));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(q1) : "r"(a.v[1]), "r"(bi));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(q2) : "r"(a.v[2]), "r"(bi));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(q3) : "r"(a.v[3]), "r"(bi));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(q4) : "r"(a.v[4]), "r"(bi));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(q5) : "r"(a.v[5]), "r"(bi));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(q6) : "r"(a.v[6]), "r"(bi));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(q7) : "r"(a.v[7]), "r"(bi));
+  uint32_t s1, s2, s3, s4, s5, s6, s7, s8;
   asm("add.cc.u32 %0, %8, %9;\n\t"
       "addc.cc.u32 %1, %10, %11;\n\t"
       "addc.cc.u32 %2, %12, %13;\n\t"
@@ -353,21 +355,34 @@ ZC_D void zc_row_wide(const fr& a, uint32_t bi, uint32_t& t0, uint32_t& t1, uint
       "addc.cc.u32 %5, %18, %19;\n\t"
       "addc.cc.u32 %6, %20, %21;\n\t"
       "addc.u32 %7, %22, 0;"
-      : "=r"(u1), "=r"(u2), "=r"(u3), "=r"(u4), "=r"(u5), "=r"(u6), "=r"(u7), "=r"(u8)
+      : "=r"(s1), "=r"(s2), "=r"(s3), "=r"(s4), "=r"(s5), "=r"(s6), "=r"(s7), "=r"(s8)
       : "r"(ZC_LO(q1)), "r"(ZC_HI(q0)), "r"(ZC_LO(q2)), "r"(ZC_HI(q1)), "r"(ZC_LO(q3)),
         "r"(ZC_HI(q2)), "r"(ZC_LO(q4)), "r"(ZC_HI(q3)), "r"(ZC_LO(q5)), "r"(ZC_HI(q4)),
         "r"(ZC_LO(q6)), "r"(ZC_HI(q5)), "r"(ZC_LO(q7)), "r"(ZC_HI(q6)), "r"(ZC_HI(q7)));
+  uint32_t u0, u1, u2, u3, u4, u5, u6, u7, u8;
+  asm("add.cc.u32 %0, %9, %17;\n\t"
+      "addc.cc.u32 %1, %10, %18;\n\t"
+      "addc.cc.u32 %2, %11, %19;\n\t"
+      "addc.cc.u32 %3, %12, %20;\n\t"
+      "addc.cc.u32 %4, %13, %21;\n\t"
+      "addc.cc.u32 %5, %14, %22;\n\t"
+      "addc.cc.u32 %6, %15, %23;\n\t"
+      "addc.cc.u32 %7, %16, %24;\n\t"
+      "addc.u32 %8, %25, 0;"
+      : "=r"(u0), "=r"(u1), "=r"(u2), "=r"(u3), "=r"(u4), "=r"(u5), "=r"(u6), "=r"(u7), "=r"(u8)
+      : "r"(t0), "r"(t1), "r"(t2), "r"(t3), "r"(t4), "r"(t5), "r"(t6), "r"(t7), "r"(ZC_LO(q0)),
+        "r"(s1), "r"(s2), "r"(s3), "r"(s4), "r"(s5), "r"(s6), "r"(s7), "r"(s8));
   // reduction: m = -u0 (r0 = 1), add m r, drop the zero low word
-  uint32_t m = 0u - u0;
-  uint32_t c0 = u0 != 0 ? 1u : 0u;
-  uint64_t r1, r2, r3, r4, r5, r6, r7;
-  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r1) : "r"(m), "n"(ZC_P1), "l"((uint64_t)u1));
-  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r2) : "r"(m), "n"(ZC_P2), "l"((uint64_t)u2));
-  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r3) : "r"(m), "n"(ZC_P3), "l"((uint64_t)u3));
-  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r4) : "r"(m), "n"(ZC_P4), "l"((uint64_t)u4));
-  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r5) : "r"(m), "n"(ZC_P5), "l"((uint64_t)u5));
-  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r6) : "r"(m), "n"(ZC_P6), "l"((uint64_t)u6));
-  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r7) : "r"(m), "n"(ZC_P7), "l"((uint64_t)u7));
+  const uint32_t m = 0u - u0, c0 = u0 != 0 ? 1u : 0u;
+  const uint32_t r1lo = u0, r1hi = m - c0;  // m (2^32 - 1)
+  uint64_t r2, r3, r4, r5, r6, r7;
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(r2) : "r"(m), "n"(ZC_P2));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(r3) : "r"(m), "n"(ZC_P3));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(r4) : "r"(m), "n"(ZC_P4));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(r5) : "r"(m), "n"(ZC_P5));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(r6) : "r"(m), "n"(ZC_P6));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(r7) : "r"(m), "n"(ZC_P7));
+  uint32_t v1, v2, v3, v4, v5, v6, v7, v8;
   asm("add.cc.u32 %0, %8, %9;\n\t"
       "addc.cc.u32 %1, %10, %11;\n\t"
       "addc.cc.u32 %2, %12, %13;\n\t"
@@ -375,11 +390,22 @@ ZC_D void zc_row_wide(const fr& a, uint32_t bi, uint32_t& t0, uint32_t& t1, uint
       "addc.cc.u32 %4, %16, %17;\n\t"
       "addc.cc.u32 %5, %18, %19;\n\t"
       "addc.cc.u32 %6, %20, %21;\n\t"
-      "addc.u32 %7, %22, %23;"
-      : "=r"(t0), "=r"(t1), "=r"(t2), "=r"(t3), "=r"(t4), "=r"(t5), "=r"(t6), "=r"(t7)
-      : "r"(ZC_LO(r1)), "r"(c0), "r"(ZC_LO(r2)), "r"(ZC_HI(r1)), "r"(ZC_LO(r3)), "r"(ZC_HI(r2)),
+      "addc.u32 %7, %22, 0;"
+      : "=r"(v1), "=r"(v2), "=r"(v3), "=r"(v4), "=r"(v5), "=r"(v6), "=r"(v7), "=r"(v8)
+      : "r"(r1lo), "r"(c0), "r"(ZC_LO(r2)), "r"(r1hi), "r"(ZC_LO(r3)), "r"(ZC_HI(r2)),
         "r"(ZC_LO(r4)), "r"(ZC_HI(r3)), "r"(ZC_LO(r5)), "r"(ZC_HI(r4)), "r"(ZC_LO(r6)),
-        "r"(ZC_HI(r5)), "r"(ZC_LO(r7)), "r"(ZC_HI(r6)), "r"(u8), "r"(ZC_HI(r7)));
+        "r"(ZC_HI(r5)), "r"(ZC_LO(r7)), "r"(ZC_HI(r6)), "r"(ZC_HI(r7)));
+  asm("add.cc.u32 %0, %8, %16;\n\t"
+      "addc.cc.u32 %1, %9, %17;\n\t"
+      "addc.cc.u32 %2, %10, %18;\n\t"
+      "addc.cc.u32 %3, %11, %19;\n\t"
+      "addc.cc.u32 %4, %12, %20;\n\t"
+      "addc.cc.u32 %5, %13, %21;\n\t"
+      "addc.cc.u32 %6, %14, %22;\n\t"
+      "addc.u32 %7, %15, %23;"
+      : "=r"(t0), "=r"(t1), "=r"(t2), "=r"(t3), "=r"(t4), "=r"(t5), "=r"(t6), "=r"(t7)
+      : "r"(u1), "r"(u2), "r"(u3), "r"(u4), "r"(u5), "r"(u6), "r"(u7), "r"(u8), "r"(v1),
+        "r"(v2), "r"(v3), "r"(v4), "r"(v5), "r"(v6), "r"(v7), "r"(v8));
 }
 
 ZC_D fr fr_mul(const fr& a, const fr& b) {

@@ -47,6 +47,7 @@ struct ScState {        // SumCheck per-proof device state
   fr alpha[kMaxN];       // challenges, level 1
   fr claim;              // H_{i-1}(alpha_{i-1}), level 0
   fr ci;                 // prod_{j<i} eq(alpha_j, r_j), level 1
+  uint32_t counter[kMaxN];  // CTAs that finished round i (last one runs the challenge)
   uint32_t err;
   uint32_t pad[7];
 };

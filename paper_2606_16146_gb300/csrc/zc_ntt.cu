@@ -27,6 +27,7 @@
 #include <cstring>
 
 #include "zc_internal.cuh"
+#include "zc_transcript.cuh"
 
 namespace zc {
 
@@ -351,50 +352,6 @@ __global__ void __launch_bounds__(256) k_ntt_gate(NttGateArgs A) {
   }
 }
 
-// ----------------------------------------------------- transcript (words) --
-
-// S <- SHA-256(S | m) for a 32-byte message m (one block + padding block)
-__device__ void tr_absorb32(uint32_t S[8], const uint8_t* m) {
-  uint32_t w[16];
-  for (int i = 0; i < 8; i++) w[i] = S[i];
-  for (int i = 0; i < 8; i++)
-    w[8 + i] = ((uint32_t)m[4 * i] << 24) | ((uint32_t)m[4 * i + 1] << 16) |
-               ((uint32_t)m[4 * i + 2] << 8) | m[4 * i + 3];
-  uint32_t h[8];
-  sha256_init(h);
-  sha256_compress(h, w);
-  for (int i = 0; i < 16; i++) w[i] = 0;
-  w[0] = 0x80000000u;
-  w[15] = 512;
-  sha256_compress(h, w);
-  for (int i = 0; i < 8; i++) S[i] = h[i];
-}
-
-__device__ fr tr_squeeze_canon(uint32_t S[8]) {
-  uint32_t w[16];
-  for (int i = 0; i < 8; i++) w[i] = S[i];
-  w[8] = 0x43800000u;
-  for (int i = 9; i < 15; i++) w[i] = 0;
-  w[15] = 33 * 8;
-  uint32_t h[8];
-  sha256_init(h);
-  sha256_compress(h, w);
-  for (int i = 0; i < 8; i++) S[i] = h[i];
-  fr x;
-  for (int i = 0; i < 8; i++) x.v[i] = sha_bswap(h[i]);
-  for (int k = 0; k < 2; k++) {
-    if (!fr_is_canonical(x)) {
-      int64_t br = 0;
-      for (int i = 0; i < 8; i++) {
-        int64_t dd = (int64_t)x.v[i] - p_limb(i) + br;
-        x.v[i] = (uint32_t)dd;
-        br = dd >> 32;
-      }
-    }
-  }
-  return x;
-}
-
 struct NttZArgs {
   NttState* st;
   const uint8_t* roots;  // c column roots then root(q)
@@ -414,7 +371,7 @@ __global__ void k_ntt_z(NttZArgs A) {
   fr z;
   uint32_t err = 1;
   for (int tries = 0; tries < 64; tries++) {
-    z = fr_mul(tr_squeeze_canon(S), C->r2);
+    z = fr_mul(tr_squeeze(S), C->r2);
     fr zn = z;
     for (uint32_t i = 0; i < A.n; i++) zn = fr_mul(zn, zn);
     if (!fr_equal(zn, C->one)) {

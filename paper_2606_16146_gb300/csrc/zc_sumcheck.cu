@@ -21,6 +21,11 @@
 // writes the first half in place.  Round i >= 2 fuses the update by
 // alpha_{i-1} with the evaluation of round i (Plonk gate).
 //
+// Scheduling: large rounds run on the whole GPU and the last CTA to finish
+// (arrival counter) performs the challenge step in the same launch; once a
+// round has at most kTailPairs pairs, one CTA runs all remaining rounds, the
+// challenges and the final values in a single launch.
+//
 // Storage levels (see zc_field.cuh): Plonk selectors stay canonical (level
 // 0), the wires a, b, c are converted once to level 1, so every gate term
 // lands on level 0 and the sums need no conversion.  Product-gate tables stay
@@ -30,8 +35,13 @@
 #include <cstring>
 
 #include "zc_internal.cuh"
+#include "zc_transcript.cuh"
 
 namespace zc {
+
+constexpr uint64_t kTailPairsPlonk = 256;
+constexpr uint64_t kTailPairsProd = 64;
+constexpr int kPP = 4;  // product gate: points per thread
 
 // ------------------------------------------------------------------ args --
 
@@ -43,11 +53,11 @@ struct ScSetupArgs {
   const DevConst* C;
 };
 
-struct EqTask {      // one factor table
-  uint32_t offset;   // into the E array
+struct EqTask {        // one factor table
+  uint32_t offset;     // into the E array
   uint32_t first_var;  // 0-based index of its most significant variable
   uint32_t nvars;
-  uint32_t level;    // 1 or d (extra R^(level-1) factor)
+  uint32_t level;      // 1 or d
 };
 
 struct ScEqArgs {
@@ -55,139 +65,56 @@ struct ScEqArgs {
   fr* E;
   EqTask task[2 * kMaxN];
   uint32_t ntask;
-  uint32_t total;     // total entries
+  uint32_t total;      // total entries
   int n;
   int skip_point;
   const DevConst* C;
 };
 
-struct ScPlonkArgs {
-  const fr* src[8];
-  fr* dst[8];
-  uint64_t h;         // number of pairs this round
-  const fr* ehi;
-  const fr* elo;
-  uint32_t m_lo;
-  int round;          // 0-based
+// Everything one round (or the tail) needs.
+struct ScRoundArgs {
+  const fr* src[kMaxCols];
+  fr* dst[kMaxCols];
+  uint64_t h;          // pairs this round
+  const fr* E;
+  uint32_t eq_hi[kMaxN], eq_lo[kMaxN], m_lo[kMaxN];
+  int round;           // 0-based; first round of the tail for k_sc_tail
+  int n, c;
+  uint32_t gate, d;
+  int G;               // product gate: threads per pair
+  uint32_t nwork;      // CTAs that evaluate pairs (round 1 adds one for the inverses)
   ScState* st;
   fr* partials;
+  uint8_t* proof;
+  fr kcomp;            // product gate: R^(2-d) mod r
   const DevConst* C;
+  const fr* tabs;
 };
 
 struct ScFoldArgs {
   const fr* src[kMaxCols];
   fr* dst[kMaxCols];
-  uint64_t h;         // output size per column
+  uint64_t h;          // output size per column
   int c;
-  int round;          // alpha index
+  int round;           // alpha index
   ScState* st;
-};
-
-struct ScProdArgs {
-  const fr* col[kMaxCols];
-  uint64_t h;
-  const fr* ehi;
-  const fr* elo;
-  uint32_t m_lo;
-  int d;
-  int np;             // points this round
-  int G;              // threads per pair
-  int round;
-  ScState* st;
-  fr* partials;
-  fr kcomp;           // R^(2-d) mod r, canonical number
-  const DevConst* C;
-};
-
-struct ScChalArgs {
-  const fr* partials;
-  int nblk;
-  int np;
-  int d;
-  int round;
-  int n;
-  ScState* st;
-  uint8_t* proof;     // device proof buffer
-  const DevConst* C;
-  const fr* tabs;
-};
-
-struct ScFinalArgs {
-  const fr* src[kMaxCols];
-  uint32_t level[kMaxCols];
-  int c, n;
-  uint32_t gate, d;
-  ScState* st;
-  uint8_t* proof;
-  const uint32_t* in_err;
 };
 
 // ----------------------------------------------------------- helpers --
 
-__device__ __forceinline__ void fr_to_le_bytes(const fr& x, uint8_t* out) {
-#pragma unroll
-  for (int i = 0; i < 8; i++) {
-    out[4 * i] = (uint8_t)x.v[i];
-    out[4 * i + 1] = (uint8_t)(x.v[i] >> 8);
-    out[4 * i + 2] = (uint8_t)(x.v[i] >> 16);
-    out[4 * i + 3] = (uint8_t)(x.v[i] >> 24);
-  }
-}
-
-// 32-byte digest (big-endian words) -> integer mod r as a canonical fr
-__device__ __forceinline__ fr digest_to_canon(const uint32_t h[8]) {
+// load through L2 only (data written earlier in the same launch)
+__device__ __forceinline__ fr ld_fr_l2(const fr* p) {
+  const uint4* q = reinterpret_cast<const uint4*>(p);
+  uint4 a = __ldcg(q), b = __ldcg(q + 1);
   fr x;
-#pragma unroll
-  for (int i = 0; i < 8; i++) x.v[i] = sha_bswap(h[i]);  // bytes little-endian
-  // at most two subtractions: 2^256 < 3r
-  for (int k = 0; k < 2; k++) {
-    if (!fr_is_canonical(x)) {
-      int64_t br = 0;
-      for (int i = 0; i < 8; i++) {
-        int64_t dd = (int64_t)x.v[i] - p_limb(i) + br;
-        x.v[i] = (uint32_t)dd;
-        br = dd >> 32;
-      }
-    }
-  }
+  x.v[0] = a.x; x.v[1] = a.y; x.v[2] = a.z; x.v[3] = a.w;
+  x.v[4] = b.x; x.v[5] = b.y; x.v[6] = b.z; x.v[7] = b.w;
   return x;
 }
 
-// S <- SHA-256(S | msg)
-__device__ void tr_absorb(uint32_t S[8], const uint8_t* msg, uint32_t len) {
-  Sha256 s;
-  s.init();
-  for (int i = 0; i < 8; i++) {
-    uint32_t w = S[i];
-    s.put_byte((uint8_t)(w >> 24));
-    s.put_byte((uint8_t)(w >> 16));
-    s.put_byte((uint8_t)(w >> 8));
-    s.put_byte((uint8_t)w);
-  }
-  s.update(msg, len);
-  uint8_t out[32];
-  s.final(out);
-  for (int i = 0; i < 8; i++)
-    S[i] = ((uint32_t)out[4 * i] << 24) | ((uint32_t)out[4 * i + 1] << 16) |
-           ((uint32_t)out[4 * i + 2] << 8) | out[4 * i + 3];
-}
-
-// S <- SHA-256(S | 0x43), challenge = int_le(S) mod r (canonical)
-__device__ fr tr_squeeze(uint32_t S[8]) {
-  uint32_t w[16];
-  for (int i = 0; i < 8; i++) w[i] = S[i];
-  w[8] = 0x43800000u;  // 0x43, then the padding bit
-  for (int i = 9; i < 15; i++) w[i] = 0;
-  w[15] = 33 * 8;
-  uint32_t h[8];
-  sha256_init(h);
-  sha256_compress(h, w);
-  for (int i = 0; i < 8; i++) S[i] = h[i];
-  return digest_to_canon(h);
-}
-
-__device__ __forceinline__ bool fr_is_one_canon(const fr& x) {
-  return x.v[0] == 1 && (x.v[1] | x.v[2] | x.v[3] | x.v[4] | x.v[5] | x.v[6] | x.v[7]) == 0;
+template <bool COHERENT>
+__device__ __forceinline__ fr ldx(const fr* p) {
+  return COHERENT ? ld_fr_l2(p) : ld_fr(p);
 }
 
 // small integer t times x by double-and-add (t < 128), additions only
@@ -204,12 +131,12 @@ __device__ __forceinline__ fr fr_mul_small(const fr& x, uint32_t t) {
   return acc;
 }
 
-// Block-wide sum of NV field values per thread; result written by thread 0
-// to out[0..NV).  blockDim.x must be a multiple of 32 (<= 1024).
+// Block-wide sum of NV values per thread, result to out[0..NV) (any memory),
+// written by thread 0.  Ends with a barrier.
 template <int NV>
-__device__ void block_sum_store(fr (&v)[NV], fr* out) {
+__device__ void block_sum(fr (&v)[NV], fr* out) {
   __shared__ fr red[32][NV];
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int p = 0; p < NV; p++) {
     fr s = warp_sum(v[p]);
@@ -224,373 +151,502 @@ __device__ void block_sum_store(fr (&v)[NV], fr* out) {
       if (lane == 0) st_fr(out + p, s);
     }
   }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------ challenge --
+
+struct ChalSmem {
+  fr Hc[kMaxPts];
+  fr H[kMaxPts + 1];   // H(0..d+1)
+  fr Hinf;
+  fr tmp[2][kMaxPts];
+  fr alpha;
+  uint32_t msg[8 + 8 * kMaxPts];
+};
+
+// Finish round `i` from the sums Hc (shared memory, np values): derive the
+// missing point, extrapolate, G_i(t) = c_i l_i(t) H_i(t) into the proof,
+// absorb, squeeze alpha_i, next claim H_i(alpha_i).  All threads of the CTA.
+__device__ void sc_challenge(ChalSmem& S, int np, int d, int i, ScState* st, uint8_t* proof,
+                             const DevConst* C, const fr* tabs) {
+  const bool first = i == 0;
+  const fr r = st->r[i];
+  if (threadIdx.x == 0) {
+    S.Hinf = S.Hc[np - 1];
+    if (first) {
+      for (int t = 0; t < d; t++) S.H[t] = S.Hc[t];
+    } else {
+      const uint32_t p0 = st->p0[i];
+      for (int t = 2; t < d; t++) S.H[t] = S.Hc[t - 1];
+      const fr claim = st->claim;  // level 0
+      if (p0 == 0) {
+        S.H[0] = S.Hc[0];
+        S.H[1] = fr_mul(fr_sub(claim, fr_mul(fr_sub(C->one, r), S.H[0])), st->rinv[i]);
+      } else {
+        S.H[1] = S.Hc[0];
+        S.H[0] = fr_mul(fr_sub(claim, fr_mul(r, S.H[1])), st->r1inv[i]);
+      }
+    }
+  }
+  __syncthreads();
+  // extrapolate H(d), H(d+1) from H(0..d-1) and the leading coefficient
+  const fr* ext = tabs + C->ext_base[d];
+  if (threadIdx.x < (unsigned)d) {
+    const int s = threadIdx.x;
+    S.tmp[0][s] = fr_mul(S.H[s], ext[2 + s]);
+    S.tmp[1][s] = fr_mul(S.H[s], ext[2 + d + s]);
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    const int t = threadIdx.x;
+    fr s = fr_mul(S.Hinf, ext[t]);
+    for (int q = 0; q < d; q++) s = fr_add(s, S.tmp[t][q]);
+    S.H[d + t] = s;
+  }
+  __syncthreads();
+  // G(t) = c_i l_i(t) H(t), level 0 = canonical
+  const fr two_r_m1 = fr_sub(fr_add(r, r), C->one);
+  const fr one_m_r = fr_sub(C->one, r);
+  if (threadIdx.x < (unsigned)(d + 2)) {
+    const int t = threadIdx.x;
+    const fr l = fr_add(one_m_r, fr_mul(C->small[t], two_r_m1));
+    const fr g = fr_mul(S.H[t], fr_mul(st->ci, l));
+    uint8_t* pout = proof + 16 + 32 * ((size_t)i * (d + 2) + t);
+    for (int q = 0; q < 8; q++) {
+      S.msg[8 + 8 * t + q] = sha_bswap(g.v[q]);
+      for (int b = 0; b < 4; b++) pout[4 * q + b] = (uint8_t)(g.v[q] >> (8 * b));
+    }
+  }
+  if (threadIdx.x < 8) S.msg[threadIdx.x] = st->S[threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t Sn[8];
+    sha256_words(S.msg, 8 + 8 * (d + 2), Sn);
+    const fr a = fr_mul(tr_squeeze(Sn), C->r2);
+    for (int q = 0; q < 8; q++) st->S[q] = Sn[q];
+    st->alpha[i] = a;
+    S.alpha = a;
+  }
+  __syncthreads();
+  // next claim H_i(alpha) by Lagrange over the nodes 0..d
+  const fr a = S.alpha;
+  const fr* dinv = tabs + C->lag_base[d];
+  if (threadIdx.x <= (unsigned)d) {
+    const int s = threadIdx.x;
+    fr num = C->one;
+    for (int q = 0; q <= d; q++)
+      if (q != s) num = fr_mul(num, fr_sub(a, C->small[q]));
+    S.tmp[0][s] = fr_mul(fr_mul(S.H[s], num), dinv[s]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    fr s = fr_zero();
+    for (int q = 0; q <= d; q++) s = fr_add(s, S.tmp[0][q]);
+    st->claim = s;
+    const fr l = fr_add(one_m_r, fr_mul(a, two_r_m1));
+    st->ci = fr_mul(st->ci, l);
+  }
+  __syncthreads();
+}
+
+// The last CTA to arrive reduces the per-CTA sums and runs the challenge.
+__device__ void sc_finish_round(const ScRoundArgs& A, int np) {
+  __shared__ bool am_last;
+  __shared__ ChalSmem S;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(&A.st->counter[A.round], 1u);
+    am_last = prev == A.nwork - 1;
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int p = warp; p < np; p += nw) {
+    fr s = fr_zero();
+    for (uint32_t b = lane; b < A.nwork; b += 32) s = fr_add(s, ld_fr_l2(A.partials + (size_t)b * np + p));
+    s = warp_sum(s);
+    if (lane == 0) S.Hc[p] = s;
+  }
+  __syncthreads();
+  sc_challenge(S, np, (int)A.d, A.round, A.st, A.proof, A.C, A.tabs);
+}
+
+// ------------------------------------------------------- per-pair work --
+
+// Plonk gate, pair k of a round: loads (and, after round 1, folds by
+// alpha) every column, evaluates at the finite points and infinity and adds
+// eq-weighted values into acc.  Columns stream in the order b, qM, qL, a,
+// qR, qO, c, qC so only the running gate value per point stays live:
+//   f = a (qL + qM b) + qR b + qO c + qC.
+template <bool FIRST, bool COHERENT>
+__device__ __forceinline__ void plonk_pair(const fr* const* src, fr* const* dst, const DevConst* C,
+                                           uint64_t k, uint64_t h, const fr& alpha, uint32_t p0,
+                                           const fr& w, fr (&acc)[FIRST ? 4 : 3], uint32_t& bad) {
+  constexpr int NF = FIRST ? 3 : 2;
+  auto column = [&](int j, fr (&v)[NF], fr& dl) {
+    fr lo, hi;
+    if (FIRST) {
+      lo = ldx<COHERENT>(src[j] + k);
+      hi = ldx<COHERENT>(src[j] + k + h);
+      bad |= (!fr_is_canonical(lo)) | (!fr_is_canonical(hi));
+      if (j >= 5) {
+        lo = to_mont(lo, C);
+        hi = to_mont(hi, C);
+        st_fr(dst[j] + k, lo);
+        st_fr(dst[j] + k + h, hi);
+      }
+    } else {
+      const fr x0 = ldx<COHERENT>(src[j] + k), x1 = ldx<COHERENT>(src[j] + k + 2 * h);
+      const fr y0 = ldx<COHERENT>(src[j] + k + h), y1 = ldx<COHERENT>(src[j] + k + 3 * h);
+      lo = fr_add(x0, fr_mul(alpha, fr_sub(x1, x0)));
+      hi = fr_add(y0, fr_mul(alpha, fr_sub(y1, y0)));
+      st_fr(dst[j] + k, lo);
+      st_fr(dst[j] + k + h, hi);
+    }
+    dl = fr_sub(hi, lo);
+    if (FIRST) {
+      v[0] = lo;
+      v[1] = hi;
+    } else {
+      v[0] = p0 ? hi : lo;
+    }
+    v[NF - 1] = fr_add(hi, dl);
+  };
+  fr bv[NF], s[NF], t[NF], u[NF], db, dt, dinf;
+  column(6, bv, db);  // b
+  column(2, t, dt);   // qM
+  dinf = fr_mul(dt, db);
+#pragma unroll
+  for (int p = 0; p < NF; p++) s[p] = fr_mul(t[p], bv[p]);
+  column(0, t, dt);   // qL
+#pragma unroll
+  for (int p = 0; p < NF; p++) s[p] = fr_add(s[p], t[p]);
+  column(5, t, dt);   // a
+  dinf = fr_mul(dinf, dt);
+#pragma unroll
+  for (int p = 0; p < NF; p++) s[p] = fr_mul(t[p], s[p]);
+  column(1, t, dt);   // qR
+#pragma unroll
+  for (int p = 0; p < NF; p++) s[p] = fr_add(s[p], fr_mul(t[p], bv[p]));
+  column(3, t, dt);   // qO
+  column(7, u, db);   // c
+#pragma unroll
+  for (int p = 0; p < NF; p++) s[p] = fr_add(s[p], fr_mul(t[p], u[p]));
+  column(4, t, dt);   // qC
+#pragma unroll
+  for (int p = 0; p < NF; p++) s[p] = fr_add(s[p], t[p]);
+#pragma unroll
+  for (int p = 0; p < NF; p++) acc[p] = fr_add(acc[p], fr_mul(s[p], w));
+  acc[NF] = fr_add(acc[NF], fr_mul(dinf, w));
+}
+
+// point index -> evaluation point (kInf for infinity)
+constexpr uint32_t kInf = 0xffffffffu;
+__device__ __forceinline__ uint32_t prod_point(int p, int np, bool first, uint32_t p0) {
+  if (p == np - 1) return kInf;
+  if (first) return (uint32_t)p;         // 0, 1, ..., d-1
+  return p == 0 ? p0 : (uint32_t)p + 1;  // p0, 2, ..., d-1
+}
+
+// Product gate f = q w1 .. w_{d-1} - o, pair k: this thread's kPP points.
+template <bool COHERENT>
+__device__ __forceinline__ void prod_pair(const ScRoundArgs& A, const fr* const* col, uint64_t k,
+                                          uint64_t h, int pcnt, const uint32_t (&tpt)[kPP],
+                                          bool first, const fr& w, fr (&acc)[kPP], uint32_t& bad) {
+  const int d = (int)A.d;
+  fr prod[kPP];
+  for (int j = 0; j <= d; j++) {
+    const fr lo = ldx<COHERENT>(col[j] + k), hi = ldx<COHERENT>(col[j] + k + h);
+    if (first) bad |= (!fr_is_canonical(lo)) | (!fr_is_canonical(hi));
+    const fr dl = fr_sub(hi, lo);
+    fr e = lo;
+    uint32_t tcur = 0;
+#pragma unroll
+    for (int p = 0; p < kPP; p++) {
+      if (p >= pcnt) break;
+      fr x;
+      if (tpt[p] == kInf) {
+        x = dl;
+      } else {
+        if (p == 0) e = fr_add(lo, fr_mul_small(dl, tpt[p]));
+        else
+          for (uint32_t s2 = tcur; s2 < tpt[p]; s2++) e = fr_add(e, dl);
+        tcur = tpt[p];
+        x = e;
+      }
+      if (j == d) {
+        // o enters at level 0; bring it to level 1-d.  Infinity has no o term.
+        if (tpt[p] != kInf) prod[p] = fr_sub(prod[p], fr_mul(x, A.kcomp));
+      } else {
+        prod[p] = j == 0 ? x : fr_mul(prod[p], x);
+      }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < kPP; p++)
+    if (p < pcnt) acc[p] = fr_add(acc[p], fr_mul(prod[p], w));
 }
 
 // ---------------------------------------------------------------- kernels --
 
-// Transcript: absorb the column roots, squeeze r_1..r_n.
+// Transcript: absorb the column roots, squeeze r_1..r_n; reset per-proof state.
 __global__ void k_sc_setup(ScSetupArgs A) {
+  if (threadIdx.x < kMaxN) A.st->counter[threadIdx.x] = 0;
   if (threadIdx.x != 0) return;
   uint32_t S[8];
   for (int i = 0; i < 8; i++) S[i] = A.S0[i];
-  for (int j = 0; j < A.c; j++) tr_absorb(S, A.roots + 32 * j, 32);
-  for (int i = 0; i < A.n; i++) {
-    fr r = tr_squeeze(S);
-    A.st->r[i] = fr_mul(r, A.C->r2);
-  }
+  for (int j = 0; j < A.c; j++) tr_absorb32(S, A.roots + 32 * j);
+  for (int i = 0; i < A.n; i++) A.st->r[i] = fr_mul(tr_squeeze(S), A.C->r2);
   for (int i = 0; i < 8; i++) A.st->S[i] = S[i];
   A.st->claim = fr_zero();
   A.st->ci = A.C->one;
   A.st->err = 0;
 }
 
-// Factor tables of eq_{>i} for every round, and 1/r_i, 1/(1-r_i).
-// Blocks [0, ninv_blocks) compute inverses, the rest fill table entries.
+// Factor tables of eq_{>i} for every round, and the derived-point choice.
 __global__ void k_sc_eq(ScEqArgs A) {
   const DevConst* C = A.C;
-  if (blockIdx.x == 0) {
-    // inverses: thread t < 2n handles r_{t/2} (even t) or 1 - r_{t/2} (odd t)
-    int t = threadIdx.x;
-    if (t < 2 * A.n) {
-      int i = t >> 1;
-      fr r = A.st->r[i];
-      fr x = (t & 1) ? fr_sub(C->one, r) : r;   // level 1
-      fr xc = from_mont(x);                      // canonical
-      fr inv = fr_inv_binary(xc);                // canonical (0 -> 0)
-      fr invm = fr_mul(inv, C->r2);              // level 1
-      if (t & 1) A.st->r1inv[i] = invm;
-      else A.st->rinv[i] = invm;
-      if (!(t & 1)) {
-        bool rzero = fr_is_zero(r);
-        bool rone = fr_equal(r, C->one);
-        A.st->p0[i] = A.skip_point == 0 ? (rzero ? 1u : 0u) : (rone ? 0u : 1u);
-      }
-    }
-    return;
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < (uint32_t)A.n) {
+    const fr r = A.st->r[e];
+    const bool rzero = fr_is_zero(r), rone = fr_equal(r, C->one);
+    A.st->p0[e] = A.skip_point == 0 ? (rzero ? 1u : 0u) : (rone ? 0u : 1u);
   }
-  uint32_t e = (blockIdx.x - 1) * blockDim.x + threadIdx.x;
   if (e >= A.total) return;
   uint32_t ti = 0;
   while (ti + 1 < A.ntask && A.task[ti + 1].offset <= e) ti++;
   const EqTask& T = A.task[ti];
-  uint32_t x = e - T.offset;
+  const uint32_t x = e - T.offset;
   fr acc = C->one;
   for (uint32_t l = 0; l < T.nvars; l++) {
-    uint32_t bit = (x >> (T.nvars - 1 - l)) & 1;
-    fr r = A.st->r[T.first_var + l];
+    const uint32_t bit = (x >> (T.nvars - 1 - l)) & 1;
+    const fr r = A.st->r[T.first_var + l];
     acc = fr_mul(acc, bit ? r : fr_sub(C->one, r));
   }
   if (T.level > 1) acc = fr_mul(acc, C->rpow[T.level]);  // level 1 -> level L
   st_fr(A.E + e, acc);
 }
 
-// One round of the Plonk-gate SumCheck.  FIRST: round 1, reads the input
-// columns, converts a, b, c to level 1 (written to dst), evaluates t = 0, 1,
-// 2 and infinity.  Otherwise: folds by alpha_{round-1} (reading 4 entries,
-// writing 2 per column and pair) and evaluates t = p0, 2 and infinity.
-// Columns stream in the order b, qM, qL, a, qR, qO, c, qC so that only the
-// running gate value per point stays live:
-//   f = a (qL + qM b) + qR b + qO c + qC.
+// 1/r_i and 1/(1 - r_i) (level 1, 0 for a zero input), threads 0..2n-1
+__device__ void sc_inverses(ScState* st, int n, const DevConst* C) {
+  const int t = threadIdx.x;
+  if (t < 2 * n) {
+    const int i = t >> 1;
+    const fr r = st->r[i];
+    const fr x = (t & 1) ? fr_sub(C->one, r) : r;
+    const fr inv = fr_mul(fr_inv_binary(from_mont(x)), C->r2);
+    if (t & 1) st->r1inv[i] = inv;
+    else st->rinv[i] = inv;
+  }
+}
+
+// One large Plonk round on the whole GPU.  FIRST: round 1 (reads the input,
+// converts a, b, c, evaluates t = 0, 1, 2, inf; the extra last CTA computes
+// the inverses used from round 2 on).  Otherwise: folds by alpha_{i-1} and
+// evaluates t = p0, 2, inf.  The last CTA to finish runs the challenge.
 template <bool FIRST>
-__global__ void __launch_bounds__(256, 1) k_sc_plonk_round(ScPlonkArgs A) {
-  constexpr int NF = FIRST ? 3 : 2;   // finite points
-  constexpr int NP = NF + 1;
-  const DevConst* C = A.C;
+__global__ void __launch_bounds__(256, 1) k_sc_plonk_round(ScRoundArgs A) {
+  constexpr int NP = FIRST ? 4 : 3;
+  if (FIRST && blockIdx.x == A.nwork) {
+    sc_inverses(A.st, A.n, A.C);
+    return;
+  }
+  const int i = A.round;
   const uint64_t h = A.h;
+  const uint32_t mlo = A.m_lo[i];
+  const fr* ehi = A.E + A.eq_hi[i];
+  const fr* elo = A.E + A.eq_lo[i];
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t T = (uint64_t)A.nwork * blockDim.x;
   fr acc[NP];
 #pragma unroll
   for (int p = 0; p < NP; p++) acc[p] = fr_zero();
-  const fr alpha = FIRST ? fr_zero() : A.st->alpha[A.round - 1];
-  const uint32_t p0 = FIRST ? 0u : A.st->p0[A.round];
+  const fr alpha = FIRST ? fr_zero() : A.st->alpha[i - 1];
+  const uint32_t p0 = FIRST ? 0u : A.st->p0[i];
   uint32_t bad = 0;
-
-  for (uint64_t k = tid; k < h; k += T) {
-    // load (and fold) column j; returns its values at the finite points and its slope
-    auto column = [&](int j, fr (&v)[NF], fr& dl) {
-      fr lo, hi;
-      if (FIRST) {
-        lo = ld_fr(A.src[j] + k);
-        hi = ld_fr(A.src[j] + k + h);
-        bad |= (!fr_is_canonical(lo)) | (!fr_is_canonical(hi));
-        if (j >= 5) {
-          lo = to_mont(lo, C);
-          hi = to_mont(hi, C);
-          st_fr(A.dst[j] + k, lo);
-          st_fr(A.dst[j] + k + h, hi);
-        }
-      } else {
-        fr x0 = ld_fr(A.src[j] + k), x1 = ld_fr(A.src[j] + k + 2 * h);
-        fr y0 = ld_fr(A.src[j] + k + h), y1 = ld_fr(A.src[j] + k + 3 * h);
-        lo = fr_add(x0, fr_mul(alpha, fr_sub(x1, x0)));
-        hi = fr_add(y0, fr_mul(alpha, fr_sub(y1, y0)));
-        st_fr(A.dst[j] + k, lo);
-        st_fr(A.dst[j] + k + h, hi);
-      }
-      dl = fr_sub(hi, lo);
-      if (FIRST) {
-        v[0] = lo;
-        v[1] = hi;
-        v[NF - 1] = fr_add(hi, dl);
-      } else {
-        v[0] = p0 ? hi : lo;
-        v[NF - 1] = fr_add(hi, dl);
-      }
-    };
-    fr bv[NF], s[NF], t[NF], u[NF], db, dt, dinf;
-    column(6, bv, db);                              // b
-    column(2, t, dt);                               // qM
-    dinf = fr_mul(dt, db);
-#pragma unroll
-    for (int p = 0; p < NF; p++) s[p] = fr_mul(t[p], bv[p]);
-    column(0, t, dt);                               // qL
-#pragma unroll
-    for (int p = 0; p < NF; p++) s[p] = fr_add(s[p], t[p]);
-    column(5, t, dt);                               // a
-    dinf = fr_mul(dinf, dt);
-#pragma unroll
-    for (int p = 0; p < NF; p++) s[p] = fr_mul(t[p], s[p]);
-    column(1, t, dt);                               // qR
-#pragma unroll
-    for (int p = 0; p < NF; p++) s[p] = fr_add(s[p], fr_mul(t[p], bv[p]));
-    column(3, t, dt);                               // qO
-    column(7, u, db);                               // c
-#pragma unroll
-    for (int p = 0; p < NF; p++) s[p] = fr_add(s[p], fr_mul(t[p], u[p]));
-    column(4, t, dt);                               // qC
-#pragma unroll
-    for (int p = 0; p < NF; p++) s[p] = fr_add(s[p], t[p]);
-    const fr w = ld_fr(A.ehi + (k >> A.m_lo));
-#pragma unroll
-    for (int p = 0; p < NF; p++) acc[p] = fr_add(acc[p], fr_mul(s[p], w));
-    acc[NF] = fr_add(acc[NF], fr_mul(dinf, w));
-  }
+  for (uint64_t k = tid; k < h; k += T)
+    plonk_pair<FIRST, false>(A.src, A.dst, A.C, k, h, alpha, p0, ld_fr(ehi + (k >> mlo)), acc, bad);
   if (FIRST && bad) atomicOr(&A.st->err, 1u);
   // each thread handled pairs with one fixed low part k_lo
-  const fr wl = ld_fr(A.elo + (tid & ((1ull << A.m_lo) - 1)));
+  const fr wl = ld_fr(elo + (tid & ((1ull << mlo) - 1)));
 #pragma unroll
   for (int p = 0; p < NP; p++) acc[p] = fr_mul(acc[p], wl);
-  block_sum_store<NP>(acc, A.partials + (size_t)blockIdx.x * NP);
+  block_sum<NP>(acc, A.partials + (size_t)blockIdx.x * NP);
+  sc_finish_round(A, NP);
 }
 
 // MLE update by alpha_{round-1}: dst[j][k] = src[j][k] + alpha (src[j][k+h] - src[j][k])
 __global__ void __launch_bounds__(256) k_sc_fold(ScFoldArgs A) {
-  fr alpha = A.st->alpha[A.round - 1];
+  const fr alpha = A.st->alpha[A.round - 1];
   const uint64_t total = A.h * (uint64_t)A.c;
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (uint64_t)gridDim.x * blockDim.x) {
-    int j = (int)(e / A.h);
-    uint64_t k = e - (uint64_t)j * A.h;
-    fr x0 = ld_fr(A.src[j] + k), x1 = ld_fr(A.src[j] + k + A.h);
+    const int j = (int)(e / A.h);
+    const uint64_t k = e - (uint64_t)j * A.h;
+    const fr x0 = ld_fr(A.src[j] + k), x1 = ld_fr(A.src[j] + k + A.h);
     st_fr(A.dst[j] + k, fr_add(x0, fr_mul(alpha, fr_sub(x1, x0))));
   }
 }
 
-// point index -> evaluation point (kInf for infinity)
-constexpr uint32_t kInf = 0xffffffffu;
-__device__ __forceinline__ uint32_t prod_point(int p, int np, int d, bool first, uint32_t p0) {
-  if (p == np - 1) return kInf;
-  if (first) return (uint32_t)p;        // 0, 1, ..., d-1
-  return p == 0 ? p0 : (uint32_t)p + 1;  // p0, 2, ..., d-1
-}
-
-// Product-gate evaluation: f = q w1 .. w_{d-1} - o.  Each pair is shared by G
-// threads, each evaluating up to PP consecutive points; tables at level 0.
-template <int PP>
-__global__ void __launch_bounds__(256) k_sc_prod_eval(ScProdArgs A) {
-  const DevConst* C = A.C;
-  const int G = A.G, d = A.d, np = A.np;
-  const bool first = A.round == 0;
-  const uint32_t p0 = first ? 0u : A.st->p0[A.round];
+// Product-gate evaluation of one large round (columns already folded): G
+// threads share a pair, each evaluating kPP consecutive points.
+__global__ void __launch_bounds__(256) k_sc_prod_round(ScRoundArgs A) {
+  const int i = A.round;
+  const bool first = i == 0;
+  if (first && blockIdx.x == A.nwork) {
+    sc_inverses(A.st, A.n, A.C);
+    return;
+  }
+  const int G = A.G, d = (int)A.d;
+  const int np = first ? d + 1 : d;
+  const uint32_t p0 = first ? 0u : A.st->p0[i];
   const int g = threadIdx.x % G;
   const uint64_t slot = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-  const uint64_t nslots = (uint64_t)gridDim.x * blockDim.x / G;
-  const int pbeg = g * PP;
-  const int pcnt = max(0, min(PP, np - pbeg));
+  const uint64_t nslots = (uint64_t)A.nwork * blockDim.x / G;
+  const int pbeg = g * kPP;
+  const int pcnt = max(0, min(kPP, np - pbeg));
+  const uint32_t mlo = A.m_lo[i];
+  const fr* ehi = A.E + A.eq_hi[i];
+  const fr* elo = A.E + A.eq_lo[i];
   uint32_t bad = 0;
-  fr acc[PP];
+  fr acc[kPP];
+  uint32_t tpt[kPP];
 #pragma unroll
-  for (int p = 0; p < PP; p++) acc[p] = fr_zero();
-  uint32_t tpt[PP];
-#pragma unroll
-  for (int p = 0; p < PP; p++) tpt[p] = p < pcnt ? prod_point(pbeg + p, np, d, first, p0) : 0u;
-
+  for (int p = 0; p < kPP; p++) {
+    acc[p] = fr_zero();
+    tpt[p] = p < pcnt ? prod_point(pbeg + p, np, first, p0) : 0u;
+  }
   for (uint64_t k = slot; k < A.h && pcnt > 0; k += nslots) {
-    fr prod[PP];
-    for (int j = 0; j <= d; j++) {
-      fr lo = ld_fr(A.col[j] + k), hi = ld_fr(A.col[j] + k + A.h);
-      if (first) bad |= (!fr_is_canonical(lo)) | (!fr_is_canonical(hi));
-      fr dl = fr_sub(hi, lo);
-      // value at the first finite point, then step by dl
-      fr e = lo;
-      uint32_t tcur = 0;
-#pragma unroll
-      for (int p = 0; p < PP; p++) {
-        if (p >= pcnt) break;
-        fr x;
-        if (tpt[p] == kInf) {
-          x = dl;
-        } else {
-          if (p == 0) {
-            e = fr_add(lo, fr_mul_small(dl, tpt[p]));
-          } else {
-            for (uint32_t s = tcur; s < tpt[p]; s++) e = fr_add(e, dl);
-          }
-          tcur = tpt[p];
-          x = e;
-        }
-        if (j == d) {
-          // o enters at level 0; bring it to level 1-d with kcomp.  The
-          // leading coefficient has no o term.
-          if (tpt[p] != kInf) prod[p] = fr_sub(prod[p], fr_mul(x, A.kcomp));
-        } else {
-          prod[p] = j == 0 ? x : fr_mul(prod[p], x);
-        }
-      }
-    }
-    fr w = fr_mul(ld_fr(A.ehi + (k >> A.m_lo)), ld_fr(A.elo + (k & ((1ull << A.m_lo) - 1))));
-#pragma unroll
-    for (int p = 0; p < PP; p++)
-      if (p < pcnt) acc[p] = fr_add(acc[p], fr_mul(prod[p], w));
+    const fr w = fr_mul(ld_fr(ehi + (k >> mlo)), ld_fr(elo + (k & ((1ull << mlo) - 1))));
+    prod_pair<false>(A, A.src, k, A.h, pcnt, tpt, first, w, acc, bad);
   }
   if (bad) atomicOr(&A.st->err, 1u);
   // reduce over the threads of the CTA that share g
-  __shared__ fr red[256 / 32][32][PP];
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ fr red[256 / 32][32][kPP];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-  for (int p = 0; p < PP; p++) {
+  for (int p = 0; p < kPP; p++) {
     fr s = acc[p];
     for (int off = 16; off >= G; off >>= 1) s = fr_add(s, shfl_down_fr(s, off));
     if (lane < G) red[warp][lane][p] = s;
   }
   __syncthreads();
-  int nw = blockDim.x >> 5;
-  for (int q = threadIdx.x; q < G * PP; q += blockDim.x) {
-    int gg = q / PP, p = q % PP;
-    int pg = gg * PP + p;
+  for (int q = threadIdx.x; q < G * kPP; q += blockDim.x) {
+    const int gg = q / kPP, p = q % kPP, pg = gg * kPP + p;
     if (pg >= np) continue;
     fr s = fr_zero();
     for (int w2 = 0; w2 < nw; w2++) s = fr_add(s, red[w2][gg][p]);
     st_fr(A.partials + (size_t)blockIdx.x * np + pg, s);
   }
+  __syncthreads();
+  sc_finish_round(A, np);
 }
 
-// Reduce the per-CTA partial sums, finish G_i, hash, derive alpha_i and the
-// next claim.  One CTA of 256 threads.
-__global__ void __launch_bounds__(256) k_sc_challenge(ScChalArgs A) {
+// All rounds from A.round on, their challenges and the final values, in one
+// CTA of 256 threads.  Tables are read with coherent loads: they are
+// rewritten between rounds inside this launch.
+__global__ void __launch_bounds__(256, 1) k_sc_tail(ScRoundArgs A) {
+  __shared__ ChalSmem S;
+  __shared__ fr pg[kMaxPts];
   const DevConst* C = A.C;
-  const int d = A.d, np = A.np, i = A.round;
-  const bool first = i == 0;
-  __shared__ fr Hc[kMaxPts];
-  __shared__ fr H[kMaxPts + 1];   // H(0..d+1)
-  __shared__ fr Hinf;
-  __shared__ fr tmp[2][kMaxPts];
-  __shared__ uint8_t msg[32 * kMaxPts];
-  __shared__ fr s_alpha;
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int p = warp; p < np; p += nw) {
-    fr s = fr_zero();
-    for (int b = lane; b < A.nblk; b += 32) s = fr_add(s, ld_fr_cg(A.partials + (size_t)b * np + p));
-    s = warp_sum(s);
-    if (lane == 0) Hc[p] = s;
+  const int n = A.n, c = A.c, d = (int)A.d;
+  const bool plonk = A.gate == ZC_GATE_PLONK;
+  const uint64_t N = 1ull << n;
+  if (A.round == 0) {
+    sc_inverses(A.st, n, C);
+    __syncthreads();
   }
-  __syncthreads();
-  const fr r = A.st->r[i];
-  if (threadIdx.x == 0) {
-    Hinf = Hc[np - 1];
-    if (first) {
-      for (int t = 0; t < d; t++) H[t] = Hc[t];
-    } else {
-      uint32_t p0 = A.st->p0[i];
-      for (int t = 2; t < d; t++) H[t] = Hc[t - 1];
-      fr claim = A.st->claim;   // level 0
-      if (p0 == 0) {
-        H[0] = Hc[0];
-        // H(1) = (claim - (1-r) H(0)) / r
-        H[1] = fr_mul(fr_sub(claim, fr_mul(fr_sub(C->one, r), H[0])), A.st->rinv[i]);
+  uint32_t bad = 0;
+  // source of round i's pairs: the input for round 0, then the folded tables
+  const fr* cur[kMaxCols];
+  for (int j = 0; j < c; j++) cur[j] = A.src[j];
+  for (int i = A.round; i < n; i++) {
+    const uint64_t h = N >> (i + 1);
+    const uint32_t mlo = A.m_lo[i];
+    const fr* ehi = A.E + A.eq_hi[i];
+    const fr* elo = A.E + A.eq_lo[i];
+    int np;
+    if (plonk) {
+      if (i == 0) {
+        np = 4;
+        fr acc[4] = {fr_zero(), fr_zero(), fr_zero(), fr_zero()};
+        for (uint64_t k = threadIdx.x; k < h; k += blockDim.x)
+          plonk_pair<true, true>(
+              cur, A.dst, C, k, h, fr_zero(), 0u,
+              fr_mul(ld_fr_cg(ehi + (k >> mlo)), ld_fr_cg(elo + (k & ((1ull << mlo) - 1)))), acc, bad);
+        block_sum<4>(acc, pg);
       } else {
-        H[1] = Hc[0];
-        // H(0) = (claim - r H(1)) / (1-r)
-        H[0] = fr_mul(fr_sub(claim, fr_mul(r, H[1])), A.st->r1inv[i]);
+        np = 3;
+        fr acc[3] = {fr_zero(), fr_zero(), fr_zero()};
+        const fr alpha = A.st->alpha[i - 1];
+        const uint32_t p0 = A.st->p0[i];
+        for (uint64_t k = threadIdx.x; k < h; k += blockDim.x)
+          plonk_pair<false, true>(
+              cur, A.dst, C, k, h, alpha, p0,
+              fr_mul(ld_fr_cg(ehi + (k >> mlo)), ld_fr_cg(elo + (k & ((1ull << mlo) - 1)))), acc, bad);
+        block_sum<3>(acc, pg);
+      }
+      // the converted wires live in dst after round 1, everything after round 2
+      for (int j = (i == 0 ? 5 : 0); j < c; j++) cur[j] = A.dst[j];
+    } else {
+      if (i > 0) {
+        const fr alpha = A.st->alpha[i - 1];
+        for (uint64_t e = threadIdx.x; e < 2 * h * (uint64_t)c; e += blockDim.x) {
+          const int j = (int)(e / (2 * h));
+          const uint64_t k = e - (uint64_t)j * 2 * h;
+          const fr x0 = ld_fr_l2(cur[j] + k), x1 = ld_fr_l2(cur[j] + k + 2 * h);
+          st_fr(A.dst[j] + k, fr_add(x0, fr_mul(alpha, fr_sub(x1, x0))));
+        }
+        __syncthreads();
+        for (int j = 0; j < c; j++) cur[j] = A.dst[j];
+      }
+      const bool first = i == 0;
+      np = first ? d + 1 : d;
+      const uint32_t p0 = first ? 0u : A.st->p0[i];
+      const int G = A.G;
+      const int g = threadIdx.x % G;
+      const uint64_t nslots = blockDim.x / G;
+      const int pbeg = g * kPP, pcnt = max(0, min(kPP, np - pbeg));
+      fr acc[kPP];
+      uint32_t tpt[kPP];
+#pragma unroll
+      for (int p = 0; p < kPP; p++) {
+        acc[p] = fr_zero();
+        tpt[p] = p < pcnt ? prod_point(pbeg + p, np, first, p0) : 0u;
+      }
+      for (uint64_t k = threadIdx.x / G; k < h && pcnt > 0; k += nslots) {
+        const fr w = fr_mul(ld_fr_cg(ehi + (k >> mlo)), ld_fr_cg(elo + (k & ((1ull << mlo) - 1))));
+        prod_pair<true>(A, cur, k, h, pcnt, tpt, first, w, acc, bad);
+      }
+      // sum each point over all threads (threads outside its group add zero)
+      for (int p = 0; p < np; p++) {
+        fr v[1] = {(p >= pbeg && p < pbeg + pcnt) ? acc[p - pbeg] : fr_zero()};
+        block_sum<1>(v, pg + p);
       }
     }
+    for (int p = threadIdx.x; p < np; p += blockDim.x) S.Hc[p] = pg[p];
+    __syncthreads();
+    sc_challenge(S, np, d, i, A.st, A.proof, C, A.tabs);
   }
+  if (bad) atomicOr(&A.st->err, 1u);
   __syncthreads();
-  // extrapolate H(d), H(d+1) from H(0..d-1) and the leading coefficient
-  const fr* ext = A.tabs + C->ext_base[d];
-  if (threadIdx.x < d) {
-    int s = threadIdx.x;
-    tmp[0][s] = fr_mul(H[s], ext[2 + s]);
-    tmp[1][s] = fr_mul(H[s], ext[2 + d + s]);
-  }
-  __syncthreads();
-  if (threadIdx.x < 2) {
-    int t = threadIdx.x;
-    fr s = fr_mul(Hinf, ext[t]);
-    for (int q = 0; q < d; q++) s = fr_add(s, tmp[t][q]);
-    H[d + t] = s;
-  }
-  __syncthreads();
-  // G(t) = c_i l_i(t) H(t), level 0 = canonical
-  const fr two_r_m1 = fr_sub(fr_add(r, r), C->one);
-  const fr one_m_r = fr_sub(C->one, r);
-  if (threadIdx.x < d + 2) {
-    int t = threadIdx.x;
-    fr l = fr_add(one_m_r, fr_mul(C->small[t], two_r_m1));
-    fr g = fr_mul(H[t], fr_mul(A.st->ci, l));
-    uint8_t* out = msg + 32 * t;
-    fr_to_le_bytes(g, out);
-    uint8_t* pout = A.proof + 16 + 32 * ((size_t)i * (d + 2) + t);
-    for (int b = 0; b < 32; b++) pout[b] = out[b];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t S[8];
-    for (int q = 0; q < 8; q++) S[q] = A.st->S[q];
-    tr_absorb(S, msg, 32 * (d + 2));
-    fr a = fr_mul(tr_squeeze(S), C->r2);
-    for (int q = 0; q < 8; q++) A.st->S[q] = S[q];
-    A.st->alpha[i] = a;
-    s_alpha = a;
-  }
-  __syncthreads();
-  // next claim H_i(alpha) by Lagrange over the nodes 0..d
-  const fr a = s_alpha;
-  const fr* dinv = A.tabs + C->lag_base[d];
-  if (threadIdx.x <= d) {
-    int s = threadIdx.x;
-    fr num = C->one;
-    for (int q = 0; q <= d; q++)
-      if (q != s) num = fr_mul(num, fr_sub(a, C->small[q]));
-    tmp[0][s] = fr_mul(fr_mul(H[s], num), dinv[s]);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    fr s = fr_zero();
-    for (int q = 0; q <= d; q++) s = fr_add(s, tmp[0][q]);
-    A.st->claim = s;
-    fr l = fr_add(one_m_r, fr_mul(a, two_r_m1));
-    A.st->ci = fr_mul(A.st->ci, l);
-  }
-}
-
-// Final MLE values v_j = T_j[0] + alpha_n (T_j[1] - T_j[0]) and the header.
-__global__ void k_sc_final(ScFinalArgs A) {
-  int j = threadIdx.x;
-  uint8_t* pv = A.proof + 16 + 32 * ((size_t)A.n * (A.d + 2));
-  if (j < A.c) {
-    fr alpha = A.st->alpha[A.n - 1];
-    fr x0 = ld_fr_cg(A.src[j]), x1 = ld_fr_cg(A.src[j] + 1);
+  // final values v_j = T_j[0] + alpha_n (T_j[1] - T_j[0]); Plonk wires are at level 1
+  uint8_t* pv = A.proof + 16 + 32 * ((size_t)n * (d + 2));
+  if (threadIdx.x < (unsigned)c) {
+    const int j = threadIdx.x;
+    const fr alpha = A.st->alpha[n - 1];
+    const fr x0 = ld_fr_l2(cur[j]), x1 = ld_fr_l2(cur[j] + 1);
     fr v = fr_add(x0, fr_mul(alpha, fr_sub(x1, x0)));
-    if (A.level[j] == 1) v = from_mont(v);
-    fr_to_le_bytes(v, pv + 32 * j);
+    if (plonk && j >= 5) v = from_mont(v);
+    for (int q = 0; q < 8; q++)
+      for (int b = 0; b < 4; b++) pv[32 * j + 4 * q + b] = (uint8_t)(v.v[q] >> (8 * b));
   }
-  if (j == 0) {
-    uint32_t bad = A.st->err;
-    const char* mg = bad ? "ZCE!" : "ZCS1";
+  if (threadIdx.x == 0) {
+    const char* mg = A.st->err ? "ZCE!" : "ZCS1";
     for (int b = 0; b < 4; b++) A.proof[b] = (uint8_t)mg[b];
-    uint32_t hv[3] = {A.gate, (uint32_t)A.n, A.d};
+    const uint32_t hv[3] = {A.gate, (uint32_t)n, A.d};
     for (int q = 0; q < 3; q++)
       for (int b = 0; b < 4; b++) A.proof[4 + 4 * q + b] = (uint8_t)(hv[q] >> (8 * b));
   }
@@ -599,76 +655,207 @@ __global__ void k_sc_final(ScFinalArgs A) {
 // ------------------------------------------------------------------ host --
 
 static void eq_round_split(int n, int round, uint32_t* m_lo, uint32_t* m_hi) {
-  uint32_t m = (uint32_t)(n - 1 - round);  // variables after x_{round+1}
+  const uint32_t m = (uint32_t)(n - 1 - round);  // variables after x_{round+1}
   uint32_t lo = m / 2;
   if (lo > 11) lo = 11;
   *m_lo = lo;
   *m_hi = m - lo;
 }
 
-zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, int on_dev,
-                         const uint8_t (*roots)[32], cudaStream_t st, uint8_t* proof,
-                         bool proof_on_dev) {
-  const uint32_t gate = p->gate, n = p->n, d = p->d;
-  const int c = gate_ncols(gate, d);
-  const uint64_t N = 1ull << n;
-  const bool plonk = gate == ZC_GATE_PLONK;
-  const int SMs = ctx->sm_count;
-  const size_t psize = 16 + 32 * ((size_t)n * (d + 2) + c);
+// Buffers of one SumCheck proof (device).
+struct ScBuffers {
+  fr* tab[kMaxCols];
+  fr* partials;
+  fr* E;
+  ScState* st;
+  uint8_t* roots;
+  uint8_t* proof;
+};
 
-  // ---- scratch layout
-  const int grid_max_plonk = 2 * SMs / 8 * 8 > 0 ? 2 * SMs / 8 * 8 : 8;
-  const int PP = 4;
-  int G = 1;
-  while (G * PP < (int)d + 1) G *= 2;
-  const int grid_max_prod = 2 * SMs;
-  const int npmax = (int)d + 1;
-  uint32_t eq_total = 0;
+struct ScPlan {
+  int c, G, grid_plonk, grid_prod, npmax;
+  uint32_t eq_total, eq_hi[kMaxN], eq_lo[kMaxN], mlo[kMaxN];
   EqTask tasks[2 * kMaxN];
-  uint32_t eq_off_hi[kMaxN], eq_off_lo[kMaxN], mlo_r[kMaxN];
+};
+
+static ScPlan sc_plan(const zc_params* p, int SMs) {
+  ScPlan P{};
+  const uint32_t n = p->n, d = p->d;
+  const bool plonk = p->gate == ZC_GATE_PLONK;
+  P.c = gate_ncols(p->gate, d);
+  P.G = 1;
+  while (P.G * kPP < (int)d + 1) P.G *= 2;
+  P.grid_plonk = std::max(8, 2 * SMs / 8 * 8);
+  P.grid_prod = 2 * SMs;
+  P.npmax = (int)d + 1;
   for (uint32_t i = 0; i < n; i++) {
     uint32_t mlo, mhi;
     eq_round_split((int)n, (int)i, &mlo, &mhi);
-    mlo_r[i] = mlo;
-    tasks[2 * i] = EqTask{eq_total, i + 1, mhi, plonk ? 1u : d};
-    eq_off_hi[i] = eq_total;
-    eq_total += 1u << mhi;
-    tasks[2 * i + 1] = EqTask{eq_total, n - mlo, mlo, 1u};
-    eq_off_lo[i] = eq_total;
-    eq_total += 1u << mlo;
+    P.mlo[i] = mlo;
+    P.tasks[2 * i] = EqTask{P.eq_total, i + 1, mhi, plonk ? 1u : d};
+    P.eq_hi[i] = P.eq_total;
+    P.eq_total += 1u << mhi;
+    P.tasks[2 * i + 1] = EqTask{P.eq_total, n - mlo, mlo, 1u};
+    P.eq_lo[i] = P.eq_total;
+    P.eq_total += 1u << mlo;
   }
-  size_t need = 0;
-  need += align_up(sizeof(fr) * N, 256) * c;                        // tables
-  need += align_up(sizeof(fr) * (size_t)std::max(grid_max_plonk, grid_max_prod) * (npmax + 1), 256);
-  need += align_up(sizeof(fr) * eq_total, 256);
-  need += align_up(sizeof(ScState), 256);
-  need += align_up(psize, 256);
-  need += align_up(32 * (size_t)c, 256);
+  return P;
+}
+
+static size_t sc_partials_count(const ScPlan& P) {
+  return (size_t)(std::max(P.grid_plonk, P.grid_prod) + 1) * (P.npmax + 1);
+}
+
+// Carve the proof's buffers from an arena; false when it is too small.
+static bool sc_carve(Arena& ar, const ScPlan& P, uint64_t N, size_t psize, ScBuffers& B) {
+  for (int j = 0; j < P.c; j++) B.tab[j] = ar.take<fr>(N);
+  B.partials = ar.take<fr>(sc_partials_count(P));
+  B.E = ar.take<fr>(P.eq_total);
+  B.st = ar.take<ScState>(1);
+  B.roots = ar.take<uint8_t>(32 * (size_t)P.c);
+  B.proof = ar.take<uint8_t>(psize);
+  return B.tab[P.c - 1] && B.partials && B.E && B.st && B.roots && B.proof;
+}
+
+// Queue every kernel of one proof on st (B.roots must hold the column roots
+// by the time the queue runs).  ev: optional events; [2] and [3] bracket the
+// round-1 launch.
+static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const* src,
+                            const ScBuffers& B, const DevConst* dC, const fr* dtabs,
+                            const DevConst& hC, int skip_point, cudaStream_t st,
+                            uint32_t* launches, cudaEvent_t* ev) {
+  const uint32_t gate = p->gate, n = p->n, d = p->d;
+  const int c = P.c;
+  const uint64_t N = 1ull << n;
+  const bool plonk = gate == ZC_GATE_PLONK;
+  ScSetupArgs sa{};
+  sa.st = B.st;
+  sa.roots = B.roots;
+  transcript_init_words(sa.S0, ZC_FORM_SUMCHECK, gate, n, d, 0);
+  sa.c = c;
+  sa.n = (int)n;
+  sa.C = dC;
+  k_sc_setup<<<1, 32, 0, st>>>(sa);
+  ScEqArgs ea{};
+  ea.st = B.st;
+  ea.E = B.E;
+  for (uint32_t t = 0; t < 2 * n; t++) ea.task[t] = P.tasks[t];
+  ea.ntask = 2 * n;
+  ea.total = P.eq_total;
+  ea.n = (int)n;
+  ea.skip_point = skip_point;
+  ea.C = dC;
+  k_sc_eq<<<(std::max<uint32_t>(P.eq_total, n) + 255) / 256, 256, 0, st>>>(ea);
+  *launches += 2;
+  if (ev) cudaEventRecord(ev[2], st);
+
+  ScRoundArgs R{};
+  R.E = B.E;
+  for (uint32_t i = 0; i < n; i++) {
+    R.eq_hi[i] = P.eq_hi[i];
+    R.eq_lo[i] = P.eq_lo[i];
+    R.m_lo[i] = P.mlo[i];
+  }
+  R.n = (int)n;
+  R.c = c;
+  R.gate = gate;
+  R.d = d;
+  R.G = P.G;
+  R.st = B.st;
+  R.partials = B.partials;
+  R.proof = B.proof;
+  R.kcomp = hC.rnegpow[d - 2];
+  R.C = dC;
+  R.tabs = dtabs;
+  const uint64_t tail_pairs = plonk ? kTailPairsPlonk : kTailPairsProd;
+  const fr* cur[kMaxCols];
+  for (int j = 0; j < c; j++) cur[j] = src[j];
+  uint32_t i = 0;
+  for (; i < n; i++) {
+    const uint64_t h = N >> (i + 1);
+    if (h <= tail_pairs) break;
+    R.round = (int)i;
+    R.h = h;
+    for (int j = 0; j < c; j++) {
+      R.src[j] = cur[j];
+      R.dst[j] = B.tab[j];
+    }
+    if (plonk) {
+      R.nwork = (uint32_t)std::min<uint64_t>((h + 255) / 256, (uint64_t)P.grid_plonk);
+      if (i == 0) {
+        k_sc_plonk_round<true><<<R.nwork + 1, 256, 0, st>>>(R);
+        for (int j = 5; j < 8; j++) cur[j] = B.tab[j];
+      } else {
+        k_sc_plonk_round<false><<<R.nwork, 256, 0, st>>>(R);
+        for (int j = 0; j < 8; j++) cur[j] = B.tab[j];
+      }
+      *launches += 1;
+    } else {
+      if (i > 0) {
+        ScFoldArgs fa{};
+        for (int j = 0; j < c; j++) {
+          fa.src[j] = cur[j];
+          fa.dst[j] = B.tab[j];
+        }
+        fa.h = 2 * h;
+        fa.c = c;
+        fa.round = (int)i;
+        fa.st = B.st;
+        const uint64_t tot = 2 * h * (uint64_t)c;
+        k_sc_fold<<<(unsigned)std::min<uint64_t>((tot + 255) / 256, (uint64_t)P.grid_prod * 4), 256, 0,
+                    st>>>(fa);
+        for (int j = 0; j < c; j++) cur[j] = B.tab[j];
+        for (int j = 0; j < c; j++) R.src[j] = cur[j];
+        *launches += 1;
+      }
+      const uint64_t slots_per_blk = 256 / P.G;
+      R.nwork = (uint32_t)std::min<uint64_t>((h + slots_per_blk - 1) / slots_per_blk, (uint64_t)P.grid_prod);
+      k_sc_prod_round<<<R.nwork + (i == 0 ? 1 : 0), 256, 0, st>>>(R);
+      *launches += 1;
+    }
+    if (i == 0 && ev) cudaEventRecord(ev[3], st);
+  }
+  if (i == 0 && ev) cudaEventRecord(ev[3], st);
+  // the tail: remaining rounds, challenges and final values in one CTA
+  R.round = (int)i;
+  for (int j = 0; j < c; j++) {
+    R.src[j] = cur[j];
+    R.dst[j] = B.tab[j];
+  }
+  R.nwork = 1;
+  k_sc_tail<<<1, 256, 0, st>>>(R);
+  *launches += 1;
+  return cudaGetLastError() == cudaSuccess ? ZC_OK : ZC_ERR_CUDA;
+}
+
+zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, int on_dev,
+                         const uint8_t (*roots)[32], cudaStream_t st, uint8_t* proof,
+                         bool proof_on_dev) {
+  const uint32_t n = p->n, d = p->d;
+  const ScPlan P = sc_plan(p, ctx->sm_count);
+  const int c = P.c;
+  const uint64_t N = 1ull << n;
+  const size_t psize = 16 + 32 * ((size_t)n * (d + 2) + c);
+  size_t need = align_up(sizeof(fr) * N, 256) * c + align_up(sizeof(fr) * sc_partials_count(P), 256) +
+                align_up(sizeof(fr) * P.eq_total, 256) + align_up(sizeof(ScState), 256) +
+                align_up(psize, 256) + align_up(32 * (size_t)c, 256) + 4096;
   if (!roots) need += root_scratch_bytes(c, N);
-  need += 4096;
   zc_status s = ensure_arena(ctx, need);
   if (s != ZC_OK) return s;
   Arena& ar = ctx->arena;
   ar.reset();
-  fr* tab[kMaxCols];
-  for (int j = 0; j < c; j++) tab[j] = ar.take<fr>(N);
-  fr* partials = ar.take<fr>((size_t)std::max(grid_max_plonk, grid_max_prod) * (npmax + 1));
-  fr* E = ar.take<fr>(eq_total);
-  ScState* dst = ar.take<ScState>(1);
-  uint8_t* dproof = ar.take<uint8_t>(psize);
-  uint8_t* droots = ar.take<uint8_t>(32 * (size_t)c);
-  if (!dproof || !droots) {
+  ScBuffers B{};
+  if (!sc_carve(ar, P, N, psize, B)) {
     ctx->err = "scratch arena too small";
     return ZC_ERR_OOM;
   }
-
   const fr* src[kMaxCols];
   if (on_dev) {
     for (int j = 0; j < c; j++) src[j] = reinterpret_cast<const fr*>(cols[j]);
   } else {
     for (int j = 0; j < c; j++) {
-      ZC_CUDA_TRY(ctx, cudaMemcpyAsync(tab[j], cols[j], N * sizeof(fr), cudaMemcpyHostToDevice, st));
-      src[j] = tab[j];
+      ZC_CUDA_TRY(ctx, cudaMemcpyAsync(B.tab[j], cols[j], N * sizeof(fr), cudaMemcpyHostToDevice, st));
+      src[j] = B.tab[j];
     }
   }
   ctx->launches = 0;
@@ -676,145 +863,29 @@ zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* col
   ctx->dom_a = 2;
   ctx->dom_b = 3;
   // round-1 evaluation: per pair (d+1)(g+1)+1 mulmods, reads c*N*32 bytes
-  const double g_mul = plonk ? 5.0 : (double)(d - 1);
+  const double g_mul = p->gate == ZC_GATE_PLONK ? 5.0 : (double)(d - 1);
   ctx->dom_mulmods = (double)(N / 2) * ((d + 1) * (g_mul + 1) + 1);
   ctx->dom_bytes = 32.0 * (double)c * (double)N;
   ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[0], st));
   if (roots) {
     std::memcpy(ctx->pinned, roots, 32 * (size_t)c);
-    ZC_CUDA_TRY(ctx, cudaMemcpyAsync(droots, ctx->pinned, 32 * (size_t)c, cudaMemcpyHostToDevice, st));
+    ZC_CUDA_TRY(ctx, cudaMemcpyAsync(B.roots, ctx->pinned, 32 * (size_t)c, cudaMemcpyHostToDevice, st));
   } else {
-    s = launch_roots(ctx, src, c, N, droots, st);
+    s = launch_roots(ctx, src, c, N, B.roots, st);
     if (s != ZC_OK) return s;
   }
   ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[1], st));
-
-  ScSetupArgs sa{};
-  sa.st = dst;
-  sa.roots = droots;
-  transcript_init_words(sa.S0, ZC_FORM_SUMCHECK, gate, n, d, 0);
-  sa.c = c;
-  sa.n = (int)n;
-  sa.C = ctx->dconst;
-  k_sc_setup<<<1, 32, 0, st>>>(sa);
-  ctx->launches++;
-  ScEqArgs ea{};
-  ea.st = dst;
-  ea.E = E;
-  for (uint32_t t = 0; t < 2 * n; t++) ea.task[t] = tasks[t];
-  ea.ntask = 2 * n;
-  ea.total = eq_total;
-  ea.n = (int)n;
-  ea.skip_point = ctx->skip_point;
-  ea.C = ctx->dconst;
-  k_sc_eq<<<1 + (eq_total + 255) / 256, 256, 0, st>>>(ea);
-  ctx->launches++;
-  ZC_CUDA_TRY(ctx, cudaGetLastError());
-  ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[2], st));
-
-  const fr* cur[kMaxCols];
-  for (int j = 0; j < c; j++) cur[j] = src[j];
-  for (uint32_t i = 0; i < n; i++) {
-    const uint64_t h = N >> (i + 1);  // pairs this round
-    int nblk, np;
-    if (plonk) {
-      ScPlonkArgs pa{};
-      for (int j = 0; j < 8; j++) {
-        pa.src[j] = cur[j];
-        pa.dst[j] = tab[j];
-      }
-      pa.h = h;
-      pa.ehi = E + eq_off_hi[i];
-      pa.elo = E + eq_off_lo[i];
-      pa.m_lo = mlo_r[i];
-      pa.round = (int)i;
-      pa.st = dst;
-      pa.partials = partials;
-      pa.C = ctx->dconst;
-      uint64_t want = (h + 255) / 256;
-      nblk = (int)std::min<uint64_t>(want, (uint64_t)grid_max_plonk);
-      if (i == 0) {
-        np = 4;
-        k_sc_plonk_round<true><<<nblk, 256, 0, st>>>(pa);
-  ctx->launches++;
-        for (int j = 5; j < 8; j++) cur[j] = tab[j];  // wires now at level 1 in scratch
-      } else {
-        np = 3;
-        k_sc_plonk_round<false><<<nblk, 256, 0, st>>>(pa);
-  ctx->launches++;
-        for (int j = 0; j < 8; j++) cur[j] = tab[j];
-      }
-    } else {
-      if (i > 0) {
-        ScFoldArgs fa{};
-        for (int j = 0; j < c; j++) {
-          fa.src[j] = cur[j];
-          fa.dst[j] = tab[j];
-        }
-        fa.h = 2 * h;
-        fa.c = c;
-        fa.round = (int)i;
-        fa.st = dst;
-        uint64_t tot = 2 * h * (uint64_t)c;
-        int fb = (int)std::min<uint64_t>((tot + 255) / 256, (uint64_t)SMs * 8);
-        k_sc_fold<<<fb, 256, 0, st>>>(fa);
-  ctx->launches++;
-        for (int j = 0; j < c; j++) cur[j] = tab[j];
-      }
-      np = i == 0 ? (int)d + 1 : (int)d;
-      ScProdArgs pa{};
-      for (int j = 0; j < c; j++) pa.col[j] = cur[j];
-      pa.h = h;
-      pa.ehi = E + eq_off_hi[i];
-      pa.elo = E + eq_off_lo[i];
-      pa.m_lo = mlo_r[i];
-      pa.d = (int)d;
-      pa.np = np;
-      pa.G = G;
-      pa.round = (int)i;
-      pa.st = dst;
-      pa.partials = partials;
-      pa.kcomp = ctx->hconst.rnegpow[d - 2];
-      pa.C = ctx->dconst;
-      uint64_t slots_per_blk = 256 / G;
-      uint64_t want = (h + slots_per_blk - 1) / slots_per_blk;
-      nblk = (int)std::min<uint64_t>(want, (uint64_t)grid_max_prod);
-      k_sc_prod_eval<4><<<nblk, 256, 0, st>>>(pa);
-  ctx->launches++;
-    }
-    ScChalArgs ca{};
-    ca.partials = partials;
-    ca.nblk = nblk;
-    ca.np = np;
-    ca.d = (int)d;
-    ca.round = (int)i;
-    ca.n = (int)n;
-    ca.st = dst;
-    ca.proof = dproof;
-    ca.C = ctx->dconst;
-    ca.tabs = ctx->dtabs;
-    if (i == 0) ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[3], st));
-    k_sc_challenge<<<1, 256, 0, st>>>(ca);
-    ctx->launches++;
+  uint32_t launches = 0;
+  s = sc_enqueue(p, P, src, B, ctx->dconst, ctx->dtabs, ctx->hconst, ctx->skip_point, st, &launches,
+                 ctx->ev);
+  ctx->launches += launches;
+  if (s != ZC_OK) {
+    ctx->err = "kernel launch failed";
+    return s;
   }
   ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[4], st));
-  ScFinalArgs fa{};
-  for (int j = 0; j < c; j++) {
-    fa.src[j] = cur[j];
-    fa.level[j] = (plonk && j >= 5) ? 1u : 0u;
-  }
-  fa.c = c;
-  fa.n = (int)n;
-  fa.gate = gate;
-  fa.d = d;
-  fa.st = dst;
-  fa.proof = dproof;
-  k_sc_final<<<1, 128, 0, st>>>(fa);
-  ctx->launches++;
-  ZC_CUDA_TRY(ctx, cudaGetLastError());
-  ZC_CUDA_TRY(ctx, cudaMemcpyAsync(proof, dproof, psize,
-                                   proof_on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                   st));
+  ZC_CUDA_TRY(ctx, cudaMemcpyAsync(proof, B.proof, psize,
+                                   proof_on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[5], st));
   if (!proof_on_dev || !on_dev) {
     ZC_CUDA_TRY(ctx, cudaStreamSynchronize(st));
@@ -893,168 +964,37 @@ static zc_status static_setup(int dev, StaticDev** out) {
 static zc_status static_prove(const zc_params* p, const void* const* cols,
                               const uint8_t (*roots)[32], cudaStream_t st, uint8_t* proof,
                               StaticDev& S) {
-  const uint32_t gate = p->gate, n = p->n, d = p->d;
-  const int c = gate_ncols(gate, d);
-  const uint64_t N = 1ull << n;
-  const bool plonk = gate == ZC_GATE_PLONK;
+  const uint32_t n = p->n, d = p->d;
   int SMs = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&SMs, cudaDevAttrMultiProcessorCount, dev);
-  const int grid_max_plonk = 2 * SMs / 8 * 8 > 0 ? 2 * SMs / 8 * 8 : 8;
-  const int PP = 4;
-  int G = 1;
-  while (G * PP < (int)d + 1) G *= 2;
-  const int grid_max_prod = 2 * SMs;
-  const int npmax = (int)d + 1;
-  uint32_t eq_total = 0;
-  EqTask tasks[2 * kMaxN];
-  uint32_t eq_off_hi[kMaxN], eq_off_lo[kMaxN], mlo_r[kMaxN];
-  for (uint32_t i = 0; i < n; i++) {
-    uint32_t mlo, mhi;
-    eq_round_split((int)n, (int)i, &mlo, &mhi);
-    mlo_r[i] = mlo;
-    tasks[2 * i] = EqTask{eq_total, i + 1, mhi, plonk ? 1u : d};
-    eq_off_hi[i] = eq_total;
-    eq_total += 1u << mhi;
-    tasks[2 * i + 1] = EqTask{eq_total, n - mlo, mlo, 1u};
-    eq_off_lo[i] = eq_total;
-    eq_total += 1u << mlo;
-  }
+  const ScPlan P = sc_plan(p, SMs);
+  const int c = P.c;
+  const uint64_t N = 1ull << n;
+  const size_t psize = 16 + 32 * ((size_t)n * (d + 2) + c);
   // carve the static array; reject instances that do not fit
   Arena ar;
   ar.base = static_cast<char*>(S.scratch);
   ar.cap = kStaticScratchBytes;
-  fr* tab[kMaxCols];
-  for (int j = 0; j < c; j++) tab[j] = ar.take<fr>(N);
-  fr* partials = ar.take<fr>((size_t)std::max(grid_max_plonk, grid_max_prod) * (npmax + 1));
-  fr* E = ar.take<fr>(eq_total);
-  ScState* dst = ar.take<ScState>(1);
-  uint8_t* droots = ar.take<uint8_t>(32 * (size_t)c);
-  if (!tab[c - 1] || !partials || !E || !dst || !droots ||
-      (!roots && ar.used + root_scratch_bytes(c, N) > ar.cap))
+  ScBuffers B{};
+  if (!sc_carve(ar, P, N, psize, B) || (!roots && ar.used + root_scratch_bytes(c, N) > ar.cap))
     return ZC_ERR_UNSUPPORTED;  // instance larger than the static scratch
-
+  B.proof = proof;              // kernels write the caller's device buffer directly
   const fr* src[kMaxCols];
   for (int j = 0; j < c; j++) src[j] = reinterpret_cast<const fr*>(cols[j]);
   if (roots) {
-    if (cudaMemcpyAsync(droots, roots, 32 * (size_t)c, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    if (cudaMemcpyAsync(B.roots, roots, 32 * (size_t)c, cudaMemcpyHostToDevice, st) != cudaSuccess)
       return ZC_ERR_CUDA;
   } else {
     // the root kernels take their node scratch from the rest of the static array
     zc_ctx tmp;
     tmp.arena = ar;
-    zc_status rs = launch_roots(&tmp, src, c, N, droots, st);
+    const zc_status rs = launch_roots(&tmp, src, c, N, B.roots, st);
     tmp.arena.base = nullptr;
     if (rs != ZC_OK) return rs;
   }
-  ScSetupArgs sa{};
-  sa.st = dst;
-  sa.roots = droots;
-  transcript_init_words(sa.S0, ZC_FORM_SUMCHECK, gate, n, d, 0);
-  sa.c = c;
-  sa.n = (int)n;
-  sa.C = S.dconst;
-  k_sc_setup<<<1, 32, 0, st>>>(sa);  // also clears the error flag and the claim
-  ScEqArgs ea{};
-  ea.st = dst;
-  ea.E = E;
-  for (uint32_t t = 0; t < 2 * n; t++) ea.task[t] = tasks[t];
-  ea.ntask = 2 * n;
-  ea.total = eq_total;
-  ea.n = (int)n;
-  ea.skip_point = 0;
-  ea.C = S.dconst;
-  k_sc_eq<<<1 + (eq_total + 255) / 256, 256, 0, st>>>(ea);
-  const fr* cur[kMaxCols];
-  for (int j = 0; j < c; j++) cur[j] = src[j];
-  for (uint32_t i = 0; i < n; i++) {
-    const uint64_t h = N >> (i + 1);
-    int nblk, np;
-    if (plonk) {
-      ScPlonkArgs pa{};
-      for (int j = 0; j < 8; j++) {
-        pa.src[j] = cur[j];
-        pa.dst[j] = tab[j];
-      }
-      pa.h = h;
-      pa.ehi = E + eq_off_hi[i];
-      pa.elo = E + eq_off_lo[i];
-      pa.m_lo = mlo_r[i];
-      pa.round = (int)i;
-      pa.st = dst;
-      pa.partials = partials;
-      pa.C = S.dconst;
-      nblk = (int)std::min<uint64_t>((h + 255) / 256, (uint64_t)grid_max_plonk);
-      if (i == 0) {
-        np = 4;
-        k_sc_plonk_round<true><<<nblk, 256, 0, st>>>(pa);
-        for (int j = 5; j < 8; j++) cur[j] = tab[j];
-      } else {
-        np = 3;
-        k_sc_plonk_round<false><<<nblk, 256, 0, st>>>(pa);
-        for (int j = 0; j < 8; j++) cur[j] = tab[j];
-      }
-    } else {
-      if (i > 0) {
-        ScFoldArgs fa{};
-        for (int j = 0; j < c; j++) {
-          fa.src[j] = cur[j];
-          fa.dst[j] = tab[j];
-        }
-        fa.h = 2 * h;
-        fa.c = c;
-        fa.round = (int)i;
-        fa.st = dst;
-        uint64_t tot = 2 * h * (uint64_t)c;
-        int fb = (int)std::min<uint64_t>((tot + 255) / 256, (uint64_t)SMs * 8);
-        k_sc_fold<<<fb, 256, 0, st>>>(fa);
-        for (int j = 0; j < c; j++) cur[j] = tab[j];
-      }
-      np = i == 0 ? (int)d + 1 : (int)d;
-      ScProdArgs pa{};
-      for (int j = 0; j < c; j++) pa.col[j] = cur[j];
-      pa.h = h;
-      pa.ehi = E + eq_off_hi[i];
-      pa.elo = E + eq_off_lo[i];
-      pa.m_lo = mlo_r[i];
-      pa.d = (int)d;
-      pa.np = np;
-      pa.G = G;
-      pa.round = (int)i;
-      pa.st = dst;
-      pa.partials = partials;
-      pa.kcomp = S.hconst.rnegpow[d - 2];
-      pa.C = S.dconst;
-      uint64_t slots_per_blk = 256 / G;
-      nblk = (int)std::min<uint64_t>((h + slots_per_blk - 1) / slots_per_blk, (uint64_t)grid_max_prod);
-      k_sc_prod_eval<4><<<nblk, 256, 0, st>>>(pa);
-    }
-    ScChalArgs ca{};
-    ca.partials = partials;
-    ca.nblk = nblk;
-    ca.np = np;
-    ca.d = (int)d;
-    ca.round = (int)i;
-    ca.n = (int)n;
-    ca.st = dst;
-    ca.proof = proof;
-    ca.C = S.dconst;
-    ca.tabs = S.dtabs;
-    k_sc_challenge<<<1, 256, 0, st>>>(ca);
-  }
-  ScFinalArgs fa{};
-  for (int j = 0; j < c; j++) {
-    fa.src[j] = cur[j];
-    fa.level[j] = (plonk && j >= 5) ? 1u : 0u;
-  }
-  fa.c = c;
-  fa.n = (int)n;
-  fa.gate = gate;
-  fa.d = d;
-  fa.st = dst;
-  fa.proof = proof;
-  k_sc_final<<<1, 128, 0, st>>>(fa);
-  return cudaGetLastError() == cudaSuccess ? ZC_OK : ZC_ERR_CUDA;
+  uint32_t launches = 0;
+  return sc_enqueue(p, P, src, B, S.dconst, S.dtabs, S.hconst, 0, st, &launches, nullptr);
 }
 
 }  // namespace zc
