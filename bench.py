@@ -186,7 +186,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--n", type=int, default=None, help="override n (debugging)")
+    ap.add_argument("--n", type=int, default=None, help="override n (profiling smaller cases)")
+    ap.add_argument("--form", default="both", choices=["both", "sumcheck", "ntt"],
+                    help="restrict the step to one form (profiling); the bench line uses both")
     args = ap.parse_args()
     global N_LOG
     if args.n:
@@ -213,10 +215,16 @@ def main():
     q_dev = torch.zeros(M * 32, dtype=torch.uint8, device=dev)
     have_ntt = True
 
+    run_sc = args.form in ("both", "sumcheck")
+    if args.form == "sumcheck":
+        have_ntt = False
+
     def step():
         nonlocal have_ntt
-        ctx.prove_sumcheck(GATE, N_LOG, DEG, dcols, roots=roots, stream=stream, proof_out=p_sc)
-        st_sc = ctx.stats()
+        st_sc = None
+        if run_sc:
+            ctx.prove_sumcheck(GATE, N_LOG, DEG, dcols, roots=roots, stream=stream, proof_out=p_sc)
+            st_sc = ctx.stats()
         st_nt = None
         if have_ntt:
             try:
@@ -238,9 +246,11 @@ def main():
     for _ in range(3):
         with torch.cuda.stream(stream):
             e0.record(stream)
-            ctx.prove_sumcheck(GATE, N_LOG, DEG, dcols, roots=roots, stream=stream, proof_out=p_sc)
+            if run_sc:
+                ctx.prove_sumcheck(GATE, N_LOG, DEG, dcols, roots=roots, stream=stream, proof_out=p_sc)
             e1.record(stream)
-        st_sc = ctx.stats()
+        if run_sc:
+            st_sc = ctx.stats()
         if have_ntt:
             ctx.prove_ntt(GATE, N_LOG, DEG, dcols, roots=roots, stream=stream, proof_out=p_nt, q_out=q_dev)
             e2.record(stream)
@@ -263,7 +273,7 @@ def main():
     t0.record(stream)
     for _ in range(args.steps):
         a, b = step()
-        launches += int(a[9]) + (int(b[9]) if b else 0)
+        launches += (int(a[9]) if a else 0) + (int(b[9]) if b else 0)
     t1.record(stream)
     stream.synchronize()
     torch.cuda.synchronize()

@@ -408,7 +408,7 @@ ZC_D void zc_row_wide(const fr& a, uint32_t bi, uint32_t& t0, uint32_t& t1, uint
         "r"(v2), "r"(v3), "r"(v4), "r"(v5), "r"(v6), "r"(v7), "r"(v8));
 }
 
-ZC_D fr fr_mul(const fr& a, const fr& b) {
+ZC_D fr fr_mul_inl(const fr& a, const fr& b) {
   uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0, t7 = 0;
   zc_row_wide(a, b.v[0], t0, t1, t2, t3, t4, t5, t6, t7);
   zc_row_wide(a, b.v[1], t0, t1, t2, t3, t4, t5, t6, t7);
@@ -420,6 +420,12 @@ ZC_D fr fr_mul(const fr& a, const fr& b) {
   zc_row_wide(a, b.v[7], t0, t1, t2, t3, t4, t5, t6, t7);
   return fr_reduce_final(t0, t1, t2, t3, t4, t5, t6, t7);
 }
+
+// The multiplier is ~400 instructions; kernels call one out-of-line copy so
+// that their code fits the instruction cache (inlined at every call site, a
+// round body of ~30 products missed the cache on almost every instruction).
+static __device__ __noinline__ fr fr_mul_call(fr a, fr b) { return fr_mul_inl(a, b); }
+ZC_D fr fr_mul(const fr& a, const fr& b) { return fr_mul_call(a, b); }
 
 #else
 inline fr fr_add(const fr& a, const fr& b) { return fr_add_g(a, b); }
