@@ -600,6 +600,9 @@ zc_status zc_setup(const zc_setup_opts* opts, zc_ctx** out) {
   ctx->budget = opts->mem_budget_bytes;
   const char* sp = std::getenv("ZC_SUMCHECK_DERIVED_POINT");
   ctx->skip_point = (sp && sp[0] == '0') ? 1 : 0;
+  // tuning overrides (defaults come from the measured table in the design doc)
+  if (const char* t = std::getenv("ZC_TUNE_NTT_TILE")) ctx->ntt_tile_log = std::atoi(t);
+  if (const char* t = std::getenv("ZC_TUNE_NTT_MINB")) ctx->ntt_minb = std::atoi(t);
   if (cudaSetDevice(ctx->device) != cudaSuccess) {
     delete ctx;
     return ZC_ERR_CUDA;
@@ -630,6 +633,8 @@ void zc_destroy(zc_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   if (ctx->arena.base) cudaFree(ctx->arena.base);
+  for (auto& t : ctx->ntt_cache)
+    if (t.mem) cudaFree(t.mem);
   if (ctx->dconst) cudaFree(ctx->dconst);
   if (ctx->dtabs) cudaFree(ctx->dtabs);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);

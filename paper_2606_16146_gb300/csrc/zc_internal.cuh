@@ -98,6 +98,20 @@ struct zc_ctx {
   double dom_bytes = 0;
   int dom_a = 2, dom_b = 3;      // events bracketing that launch
   int skip_point = 0;            // 0: derive H(1) from the claim (default), 1: derive H(0)
+  int ntt_tile_log = 10;         // NTT pass tile (log2 elements), raised to the sub-DFT length
+  int ntt_minb = 2;              // NTT pass: minimum resident CTAs per SM for the 2048 tile
+  // per-size NTT tables (twiddles, coset factors, quotient scale), built on
+  // first use of a size; see zc_ntt.cu
+  struct NttSizeTables {
+    uint32_t n = 0, lb = 0;
+    void* mem = nullptr;
+    size_t bytes = 0;
+    uint64_t stamp = 0;
+    zc::fr *tw_fwd = nullptr, *tw_inv = nullptr, *coset = nullptr, *outer = nullptr, *fin = nullptr;
+  };
+  std::vector<NttSizeTables> ntt_cache;
+  uint64_t ntt_cache_clock = 0;
+  size_t ntt_cache_budget = 16ull << 30;
 };
 
 namespace zc {

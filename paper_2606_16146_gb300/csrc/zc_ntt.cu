@@ -46,6 +46,8 @@ struct NttTables {
   fr* wi_hi = nullptr;
   fr* s7_lo = nullptr;     // 7^-b (level 0)
   fr* s7_hi = nullptr;     // 7^-(a 2^15) (level 1)
+  fr* p7_lo = nullptr;     // 7^b (level 1)
+  fr* p7_hi = nullptr;     // 7^(a 2^15) (level 1)
   void* mem = nullptr;
 };
 
@@ -54,6 +56,7 @@ static std::mutex g_tabs_mu;
 
 struct NttTabArgs {
   fr* dft_fwd; fr* dft_inv; fr* wf_lo; fr* wf_hi; fr* wi_lo; fr* wi_hi; fr* s7_lo; fr* s7_hi;
+  fr* p7_lo; fr* p7_hi;
   fr w30;        // 2^30-th root (level 1)
   fr w30i;       // its inverse (level 1)
   fr seveninv;   // 7^-1 (level 1)
@@ -85,6 +88,8 @@ __global__ void k_ntt_tables(NttTabArgs A) {
     A.wi_hi[i] = fr_pow_dev(A.w30i, (uint64_t)i << kLoBits, C);
     A.s7_lo[i] = from_mont(fr_pow_dev(A.seveninv, i, C));          // level 0
     A.s7_hi[i] = fr_pow_dev(A.seveninv, (uint64_t)i << kLoBits, C);  // level 1
+    A.p7_lo[i] = fr_pow_dev(C->small[7], i, C);
+    A.p7_hi[i] = fr_pow_dev(C->small[7], (uint64_t)i << kLoBits, C);
   }
 }
 
@@ -95,8 +100,8 @@ __device__ __forceinline__ fr root_pow(const fr* lo, const fr* hi, uint32_t e) {
 
 // ---------------------------------------------------------------- passes --
 
-enum { PRE_NONE = 0, PRE_COSET = 1 };
-enum { POST_NONE = 0, POST_TW = 1, POST_OUTER = 2, POST_FINAL = 3 };
+enum { PRE_NONE = 0, PRE_COSET = 1, PRE_TAB = 2 };
+enum { POST_NONE = 0, POST_TW = 1, POST_OUTER = 2, POST_FINAL = 3, POST_TAB = 4 };
 
 struct NttPassArgs {
   const fr* in[kMaxCols];
@@ -120,6 +125,12 @@ struct NttPassArgs {
   uint32_t tw_shift;      // exponent in the 2^30 table: (e mod 2^(30-shift)) << shift
   uint32_t outer_lbdiv;   // POST_OUTER: e = (b >> lbdiv) * ((t << lbdiv) + (b mod 2^lbdiv))
   uint64_t fin_N;         // POST_FINAL: k = fin_N * t + b
+  // table modes: PRE_TAB factor = pre_tab[b * pre_kb + t * pre_kt];
+  // POST_TAB factor = post_tab[(b >> p_lbdiv) * p_hs + (b & (2^p_lbdiv - 1)) * p_ls + t * p_ts]
+  const fr* pre_tab;
+  const fr* post_tab;
+  uint32_t p_lbdiv;
+  uint64_t p_hs, p_ls, p_ts;
 };
 
 // radix-2/4/8 butterflies on x[0..R) in registers, X[k] = sum_r x[r] w_R^(rk)
@@ -213,8 +224,8 @@ __device__ __forceinline__ void stockham_stage(fr* sm, uint32_t logL, uint32_t l
   __syncthreads();
 }
 
-template <int TILE>
-__global__ void __launch_bounds__(TILE / 8, 1) k_ntt_pass(NttPassArgs A) {
+template <int TILE, int MINB>
+__global__ void __launch_bounds__(TILE / 8, MINB) k_ntt_pass(NttPassArgs A) {
   extern __shared__ __align__(16) fr sm[];
   const int item = blockIdx.y;
   const fr* __restrict__ in = A.in[item];
@@ -234,7 +245,9 @@ __global__ void __launch_bounds__(TILE / 8, 1) k_ntt_pass(NttPassArgs A) {
     const uint64_t b = b0 + w;
     const uint64_t a = (b >> A.in_lbdiv) * A.in_bs_hi + (b & in_bdiv_mask) * A.in_bs_lo + t * A.in_ts;
     fr x = ld_fr(in + a);
-    if (A.pre == PRE_COSET) {
+    if (A.pre == PRE_TAB) {
+      x = fr_mul(x, ld_fr(A.pre_tab + b * A.pre_kb + t * A.pre_kt));
+    } else if (A.pre == PRE_COSET) {
       const uint64_t k = b * A.pre_kb + t * A.pre_kt;
       // one slice per launch: every column uses the same tables
       fr f = fr_mul(ld_fr(A.pre_hi + (k >> A.pre_shift)),
@@ -261,7 +274,10 @@ __global__ void __launch_bounds__(TILE / 8, 1) k_ntt_pass(NttPassArgs A) {
     else { w = idx & (W - 1); t = idx >> logW; }
     const uint64_t b = b0 + w;
     fr y = sm[t * W + w];
-    if (A.post == POST_TW) {
+    if (A.post == POST_TAB) {
+      const uint64_t ti = (b >> A.p_lbdiv) * A.p_hs + (b & ((1ull << A.p_lbdiv) - 1)) * A.p_ls + t * A.p_ts;
+      y = fr_mul(y, ld_fr(A.post_tab + ti));
+    } else if (A.post == POST_TW) {
       const uint64_t e = (b & ((1ull << A.tw_lbmod) - 1)) * t;
       const uint32_t ex = (uint32_t)((e << A.tw_shift) & ((1ull << kLog30) - 1));
       if (ex) y = fr_mul(y, root_pow(A.tw_lo, A.tw_hi, ex));
@@ -278,6 +294,56 @@ __global__ void __launch_bounds__(TILE / 8, 1) k_ntt_pass(NttPassArgs A) {
     }
     const uint64_t a = (b >> A.out_lbdiv) * A.out_bs_hi + (b & out_bdiv_mask) * A.out_bs_lo + t * A.out_ts;
     st_fr(out + a, y);
+  }
+}
+
+// ----------------------------------------------------- per-size tables --
+// For one (n, log2 s): the four-step twiddles of size N in both directions,
+// the coset factors (7 w_M^j)^k / N of every slice (level 2, which also
+// converts canonical coefficients to Montgomery form), the outer twiddles of
+// the quotient INTT and its final scale 7^-k (level 0).  They depend only on
+// the sizes, so a context builds them on first use and reuses them.
+struct NttSizeArgs {
+  fr* tw_fwd;   // [b * L1 + t] = w_N^(b t), b < L2, t < L1
+  fr* tw_inv;   // [b * L2 + t] = w_N^-(b t), b < L1, t < L2
+  fr* coset;    // [j * N + k] = (7 w_M^j)^k / N   (level 2)
+  fr* outer;    // [j * N + k] = w_M^-(j k)
+  fr* fin;      // [k] = 7^-k                       (level 0)
+  uint32_t n, lb, l1, l2;
+  fr ninv_l2;
+  const NttTables* T;
+  const DevConst* C;
+};
+
+__global__ void k_ntt_size_tables(NttSizeArgs A, NttTables T) {
+  const uint64_t N = 1ull << A.n, M = N << A.lb;
+  const uint32_t logm = A.n + A.lb;
+  const uint64_t L1 = 1ull << A.l1, L2 = 1ull << A.l2;
+  const uint64_t total = 2 * N + 3 * M;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    if (e < N) {
+      const uint64_t b = e / L1, t = e % L1;
+      const uint32_t ex = (uint32_t)((((b * t) & (N - 1)) << (kLog30 - A.n)) & ((1ull << kLog30) - 1));
+      st_fr(A.tw_fwd + e, root_pow(T.wf_lo, T.wf_hi, ex));
+    } else if (e < 2 * N) {
+      const uint64_t i = e - N, b = i / L2, t = i % L2;
+      const uint32_t ex = (uint32_t)((((b * t) & (N - 1)) << (kLog30 - A.n)) & ((1ull << kLog30) - 1));
+      st_fr(A.tw_inv + i, root_pow(T.wi_lo, T.wi_hi, ex));
+    } else if (e < 2 * N + M) {
+      const uint64_t i = e - 2 * N, j = i >> A.n, k = i & (N - 1);
+      const uint32_t ex = (uint32_t)(((j * k) & (M - 1)) << (kLog30 - logm));
+      fr f = fr_mul(fr_mul(ld_fr(T.p7_hi + (k >> kLoBits)), ld_fr(T.p7_lo + (k & kLoMask))),
+                    root_pow(T.wf_lo, T.wf_hi, ex));
+      st_fr(A.coset + i, fr_mul(f, A.ninv_l2));
+    } else if (e < 2 * N + 2 * M) {
+      const uint64_t i = e - 2 * N - M, j = i >> A.n, k = i & (N - 1);
+      const uint32_t ex = (uint32_t)(((j * k) & (M - 1)) << (kLog30 - logm));
+      st_fr(A.outer + i, root_pow(T.wi_lo, T.wi_hi, ex));
+    } else {
+      const uint64_t k = e - 2 * N - 2 * M;
+      st_fr(A.fin + k, fr_mul(ld_fr(T.s7_hi + (k >> kLoBits)), ld_fr(T.s7_lo + (k & kLoMask))));
+    }
   }
 }
 
@@ -498,7 +564,7 @@ static zc_status ensure_tables(zc_ctx* ctx, cudaStream_t st, NttTables** out) {
   NttTables& T = g_tabs_by_dev[ctx->device];
   if (!T.ready) {
     const size_t n4 = 4096, n15 = 1u << kLoBits;
-    size_t bytes = sizeof(fr) * (2 * n4 + 6 * n15);
+    size_t bytes = sizeof(fr) * (2 * n4 + 8 * n15);
     if (cudaMalloc(&T.mem, bytes) != cudaSuccess) {
       cudaGetLastError();
       ctx->err = "cudaMalloc NTT tables";
@@ -513,6 +579,8 @@ static zc_status ensure_tables(zc_ctx* ctx, cudaStream_t st, NttTables** out) {
     T.wi_hi = p; p += n15;
     T.s7_lo = p; p += n15;
     T.s7_hi = p; p += n15;
+    T.p7_lo = p; p += n15;
+    T.p7_hi = p; p += n15;
     const DevConst& C = ctx->hconst;
     // w_2^32 = 7^((r-1)/2^32); w_2^30 = (w_2^32)^4
     uint32_t e[8];
@@ -531,6 +599,7 @@ static zc_status ensure_tables(zc_ctx* ctx, cudaStream_t st, NttTables** out) {
     a.dft_fwd = T.dft_fwd; a.dft_inv = T.dft_inv;
     a.wf_lo = T.wf_lo; a.wf_hi = T.wf_hi; a.wi_lo = T.wi_lo; a.wi_hi = T.wi_hi;
     a.s7_lo = T.s7_lo; a.s7_hi = T.s7_hi;
+    a.p7_lo = T.p7_lo; a.p7_hi = T.p7_hi;
     a.w30 = fr_mul_g(w30, C.r2);
     a.w30i = fr_mul_g(h_inv(w30, C), C.r2);
     a.seveninv = fr_mul_g(h_inv(seven, C), C.r2);
@@ -546,26 +615,103 @@ static zc_status ensure_tables(zc_ctx* ctx, cudaStream_t st, NttTables** out) {
   return ZC_OK;
 }
 
+// Pass kernel variants: tile of 2^logTile elements (TILE / 8 threads, each
+// owning 8 elements per stage) and a minimum number of resident CTAs per SM
+// (caps registers).  The context's tuning picks the tile and residency.
+template <int TILE, int MINB>
+static void launch_pass_variant(const NttPassArgs& a, dim3 grid, cudaStream_t st) {
+  k_ntt_pass<TILE, MINB><<<grid, TILE / 8, TILE * sizeof(fr), st>>>(a);
+}
+
+static void set_pass_attributes() {
+  cudaFuncSetAttribute(k_ntt_pass<1024, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 1024 * 32);
+  cudaFuncSetAttribute(k_ntt_pass<2048, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2048 * 32);
+  cudaFuncSetAttribute(k_ntt_pass<2048, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2048 * 32);
+  cudaFuncSetAttribute(k_ntt_pass<4096, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4096 * 32);
+}
+
 // launch one batched pass over `items` columns
 static zc_status run_pass(zc_ctx* ctx, cudaStream_t st, NttPassArgs& a, int items, uint64_t B) {
   const uint32_t logL = a.logL;
-  const uint32_t logTile = logL >= 11 ? 12 : 11;
+  uint32_t logTile = (uint32_t)ctx->ntt_tile_log;
+  if (logTile < logL) logTile = logL < 10 ? 10 : logL;
+  if (logTile > 12) logTile = 12;
+  if (logTile < 10) logTile = 10;
   a.logW = logTile - logL;
   while (a.logW > 0 && (1ull << a.logW) > B) a.logW--;
   const uint64_t W = 1ull << a.logW;
-  uint64_t blocks = (B + W - 1) / W;
+  const uint64_t blocks = (B + W - 1) / W;
   if (B % W) {
     ctx->err = "NTT pass: batch not a multiple of the tile";
     return ZC_ERR_ARG;
   }
   dim3 grid((unsigned)blocks, (unsigned)items);
-  if (logTile == 12) {
-    k_ntt_pass<4096><<<grid, 512, 4096 * sizeof(fr), st>>>(a);
-  } else {
-    k_ntt_pass<2048><<<grid, 256, 2048 * sizeof(fr), st>>>(a);
-  }
+  if (logTile == 12) launch_pass_variant<4096, 1>(a, grid, st);
+  else if (logTile == 11 && ctx->ntt_minb >= 2) launch_pass_variant<2048, 2>(a, grid, st);
+  else if (logTile == 11) launch_pass_variant<2048, 1>(a, grid, st);
+  else launch_pass_variant<1024, 4>(a, grid, st);
   ctx->launches++;
   return ZC_OK;
+}
+
+// The per-size tables of (n, lb), built on first use; nullptr when they
+// would exceed the context's table budget (the passes then form every factor
+// from the two-level power tables instead).
+static zc_ctx::NttSizeTables* size_tables(zc_ctx* ctx, const NttTables* T, uint32_t n, uint32_t lb,
+                                          uint32_t l1, uint32_t l2, cudaStream_t st) {
+  const uint64_t N = 1ull << n, M = N << lb;
+  for (auto& e : ctx->ntt_cache)
+    if (e.n == n && e.lb == lb) {
+      e.stamp = ++ctx->ntt_cache_clock;
+      return &e;
+    }
+  const size_t bytes = sizeof(fr) * (2 * N + 3 * M);
+  if (bytes > ctx->ntt_cache_budget) return nullptr;
+  size_t used = 0;
+  for (auto& e : ctx->ntt_cache) used += e.bytes;
+  while (!ctx->ntt_cache.empty() && used + bytes > ctx->ntt_cache_budget) {
+    size_t old = 0;
+    for (size_t i = 1; i < ctx->ntt_cache.size(); i++)
+      if (ctx->ntt_cache[i].stamp < ctx->ntt_cache[old].stamp) old = i;
+    cudaStreamSynchronize(st);
+    cudaFree(ctx->ntt_cache[old].mem);
+    used -= ctx->ntt_cache[old].bytes;
+    ctx->ntt_cache.erase(ctx->ntt_cache.begin() + old);
+  }
+  zc_ctx::NttSizeTables e;
+  if (cudaMalloc(&e.mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  e.n = n;
+  e.lb = lb;
+  e.bytes = bytes;
+  fr* q = static_cast<fr*>(e.mem);
+  e.tw_fwd = q; q += N;
+  e.tw_inv = q; q += N;
+  e.coset = q; q += M;
+  e.outer = q; q += M;
+  e.fin = q;
+  NttSizeArgs a{};
+  a.tw_fwd = e.tw_fwd;
+  a.tw_inv = e.tw_inv;
+  a.coset = e.coset;
+  a.outer = e.outer;
+  a.fin = e.fin;
+  a.n = n;
+  a.lb = lb;
+  a.l1 = l1;
+  a.l2 = l2;
+  const DevConst& C = ctx->hconst;
+  a.ninv_l2 = fr_mul_g(fr_mul_g(h_inv(h_from_u64(N), C), C.r2), C.r2);
+  a.C = ctx->dconst;
+  const uint64_t total = 2 * N + 3 * M;
+  k_ntt_size_tables<<<(unsigned)std::min<uint64_t>((total + 255) / 256, (uint64_t)ctx->sm_count * 16), 256, 0,
+                      st>>>(a, *T);
+  ctx->launches++;
+  e.stamp = ++ctx->ntt_cache_clock;
+  ctx->ntt_cache.push_back(e);
+  return &ctx->ntt_cache.back();
 }
 
 static void pass_defaults(NttPassArgs& a) {
@@ -594,8 +740,7 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
   const size_t psize = 20 + 32 + 32 * ((size_t)c + 1);
   static int attr_done[64] = {0};
   if (!attr_done[ctx->device]) {
-    cudaFuncSetAttribute(k_ntt_pass<4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4096 * 32);
-    cudaFuncSetAttribute(k_ntt_pass<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2048 * 32);
+    set_pass_attributes();
     attr_done[ctx->device] = 1;
   }
   NttTables* T = nullptr;
@@ -697,6 +842,7 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
   const uint32_t l2 = two ? n / 2 : 0;         // second digit
   const uint64_t L1 = 1ull << l1, L2 = 1ull << l2;
   zc_status rs;
+  zc_ctx::NttSizeTables* ST = size_tables(ctx, T, n, lb, l1, l2, st);
 
   // ---- N1: g_j = DFT^-1(e_j) (the factor 1/N is applied later), natural out
   if (two) {
@@ -712,6 +858,10 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
     a.dft = T->dft_inv;
     a.post = POST_TW; a.tw_lo = T->wi_lo; a.tw_hi = T->wi_hi;
     a.tw_lbmod = l1; a.tw_shift = kLog30 - n;
+    if (ST) {  // w_N^-(i1 k2) = tw_inv[i1 L2 + k2]
+      a.post = POST_TAB; a.post_tab = ST->tw_inv;
+      a.p_lbdiv = 63; a.p_ls = L2; a.p_ts = 1;
+    }
     if ((rs = run_pass(ctx, st, a, c, L1)) != ZC_OK) return rs;
     pass_defaults(a);
     for (int j = 0; j < c; j++) {
@@ -758,6 +908,11 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
       a.pre_kb = 1; a.pre_kt = L2;
       a.post = POST_TW; a.tw_lo = T->wf_lo; a.tw_hi = T->wf_hi;
       a.tw_lbmod = l2; a.tw_shift = kLog30 - n;
+      if (ST) {  // coset factor of k = k2 + L2 k1; twiddle w_N^(k2 i1) = tw_fwd[k2 L1 + i1]
+        a.pre = PRE_TAB; a.pre_tab = ST->coset + j * N;
+        a.post = POST_TAB; a.post_tab = ST->tw_fwd;
+        a.p_lbdiv = 63; a.p_ls = L1; a.p_ts = 1;
+      }
       if ((rs = run_pass(ctx, st, a, c, L2)) != ZC_OK) return rs;
       if (j == 0) ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[7], st));
       pass_defaults(a);
@@ -775,6 +930,9 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
       a.in_bs_lo = 0; a.in_ts = 1;
       a.out_bs_lo = 0; a.out_ts = 1;
       a.pre_kb = 0; a.pre_kt = 1;
+      if (ST) {
+        a.pre = PRE_TAB; a.pre_tab = ST->coset + j * N;
+      }
       if ((rs = run_pass(ctx, st, a, c, 1)) != ZC_OK) return rs;
       if (j == 0) ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[7], st));
     }
@@ -803,6 +961,10 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
       a.dft = T->dft_inv;
       a.post = POST_TW; a.tw_lo = T->wi_lo; a.tw_hi = T->wi_hi;
       a.tw_lbmod = l1; a.tw_shift = kLog30 - n;
+      if (ST) {  // w_N^-(i2 k3) = tw_inv[(b mod L1) L2 + k3]
+        a.post = POST_TAB; a.post_tab = ST->tw_inv;
+        a.p_lbdiv = l1; a.p_hs = 0; a.p_ls = L2; a.p_ts = 1;
+      }
       if ((rs = run_pass(ctx, st, a, 1, s * L1)) != ZC_OK) return rs;
       pass_defaults(a);
       a.in[0] = qhat; a.out[0] = qhat;
@@ -812,6 +974,10 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
       a.dft = T->dft_inv;
       a.post = POST_OUTER; a.tw_lo = T->wi_lo; a.tw_hi = T->wi_hi;
       a.outer_lbdiv = l2; a.tw_shift = kLog30 - logm;
+      if (ST) {  // w_M^-(j k'), k' = L2 k2 + k3: outer[j N + k']
+        a.post = POST_TAB; a.post_tab = ST->outer;
+        a.p_lbdiv = l2; a.p_hs = N; a.p_ls = 1; a.p_ts = L2;
+      }
       if ((rs = run_pass(ctx, st, a, 1, s * L2)) != ZC_OK) return rs;
     } else {
       pass_defaults(a);
@@ -822,6 +988,10 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
       a.dft = T->dft_inv;
       a.post = POST_OUTER; a.tw_lo = T->wi_lo; a.tw_hi = T->wi_hi;
       a.outer_lbdiv = 0; a.tw_shift = kLog30 - logm;
+      if (ST) {
+        a.post = POST_TAB; a.post_tab = ST->outer;
+        a.p_lbdiv = 63; a.p_ls = N; a.p_ts = 1;
+      }
       if ((rs = run_pass(ctx, st, a, 1, s)) != ZC_OK) return rs;
     }
     pass_defaults(a);
@@ -832,6 +1002,10 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
     a.dft = T->dft_inv;
     a.post = POST_FINAL; a.tw_lo = T->s7_lo; a.tw_hi = T->s7_hi;
     a.fin_N = N;
+    if (ST) {  // 7^-k, k = N t + b
+      a.post = POST_TAB; a.post_tab = ST->fin;
+      a.p_lbdiv = 63; a.p_ls = 1; a.p_ts = N;
+    }
     if ((rs = run_pass(ctx, st, a, 1, N)) != ZC_OK) return rs;
   }
   ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[4], st));
