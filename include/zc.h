@@ -151,6 +151,39 @@ zc_status zc_roots(zc_ctx* ctx, const zc_params* params, const void* const* cols
  * [9] number of kernels the call launched.  Waits for the call's events. */
 zc_status zc_stats(zc_ctx* ctx, double* phase_ms, uint32_t cap);
 
+/* ---- Batched proving (deployment mode; the paper proves one instance at a
+ * time).  A batch of `count` instances, each with its own form, params and
+ * DEVICE columns, DEVICE proof buffer (zc_proof_size bytes) and, for the NTT
+ * form, an optional DEVICE q buffer (NULL entries allowed).  The context
+ * runs the batch on up to 16 lanes (concurrent streams with their own
+ * scratch), longest instance first onto the least-loaded lane; every proof
+ * is byte-identical to the one zc_prove_sumcheck / zc_prove_ntt returns for
+ * the same instance.  Column roots are computed on the device. */
+
+/* Prove a batch now, asynchronously on cuda_stream (scratch is allocated
+ * before the kernels are queued, which may synchronise the device). */
+zc_status zc_prove_batch(zc_ctx* ctx, uint32_t count, const zc_form* forms, const zc_params* params,
+                         const void* const* const* cols, void* cuda_stream, uint8_t* const* proofs,
+                         void* const* q_outs);
+
+typedef struct zc_batch zc_batch;
+
+/* Allocate everything a batch needs, then capture its whole launch sequence
+ * into one CUDA graph.  The graph keeps the given pointers: relaunching it
+ * proves whatever the column buffers hold at launch time. */
+zc_status zc_batch_create(zc_ctx* ctx, uint32_t count, const zc_form* forms, const zc_params* params,
+                          const void* const* const* cols, uint8_t* const* proofs, void* const* q_outs,
+                          zc_batch** out);
+
+/* One graph launch proves every instance of the batch (asynchronous). */
+zc_status zc_batch_launch(zc_batch* batch, void* cuda_stream);
+
+/* Kernels the batch graph contains. */
+uint32_t zc_batch_kernels(const zc_batch* batch);
+
+/* Free the graph (the context keeps its lanes for later batches). */
+void zc_batch_destroy(zc_batch* batch);
+
 /* SumCheck-form proof without any device allocation (the paper has no
  * counterpart; this is a deployment variant of zc_prove_sumcheck).
  *
@@ -184,6 +217,37 @@ zc_status zc_stats(zc_ctx* ctx, double* phase_ms, uint32_t cap);
 zc_status zc_prove_sumcheck_static(const zc_params* params, const void* const* cols,
                                    const uint8_t (*col_roots)[32], void* cuda_stream,
                                    uint8_t* proof, size_t cap, size_t* len);
+
+/* ------------------------------------------------------------ tuning --
+ * Launch parameters of the kernels, per form and size.  The paper fixes the
+ * arithmetic, not the launch shape; every value gives byte-identical proofs
+ * and only changes speed.  A tuner (paper_2606_16146_gb300/tune.py) measures
+ * the candidates and stores the winners here.
+ *
+ *   ZC_TUNE_SC_GRID      SumCheck: most CTAs one round kernel is split over
+ *                        (the fold/evaluate split); 1..4096, default 2 per SM.
+ *   ZC_TUNE_SC_TAIL_LOG  SumCheck: the single-CTA tail takes over once a round
+ *                        has at most 2^value pairs; 0..24, default 8 (Plonk
+ *                        gate) or 6 (product gate).
+ *   ZC_TUNE_NTT_TILE_LOG NTT: elements per shared-memory pass tile, 2^value;
+ *                        10, 11 or 12, default 11.
+ *   ZC_TUNE_NTT_MINB     NTT: resident CTAs per SM the 2^11 tile is compiled
+ *                        for; 1 or 2, default 2.
+ *
+ * n = 0 sets the value for every size without its own entry; value = 0
+ * removes an entry.  Out-of-range keys, forms, sizes or values give
+ * ZC_ERR_ARG. */
+typedef enum {
+  ZC_TUNE_SC_GRID = 1,
+  ZC_TUNE_SC_TAIL_LOG = 2,
+  ZC_TUNE_NTT_TILE_LOG = 3,
+  ZC_TUNE_NTT_MINB = 4
+} zc_tune_key;
+
+zc_status zc_tune_set(zc_ctx* ctx, zc_form form, uint32_t n, zc_tune_key key, int32_t value);
+
+/* The value proofs of (form, n) use for key (the default when none is set). */
+zc_status zc_tune_get(zc_ctx* ctx, zc_form form, uint32_t n, zc_tune_key key, int32_t* value);
 
 /* Message describing the last failure on ctx ("" if none). */
 const char* zc_last_error(zc_ctx* ctx);

@@ -600,9 +600,6 @@ zc_status zc_setup(const zc_setup_opts* opts, zc_ctx** out) {
   ctx->budget = opts->mem_budget_bytes;
   const char* sp = std::getenv("ZC_SUMCHECK_DERIVED_POINT");
   ctx->skip_point = (sp && sp[0] == '0') ? 1 : 0;
-  // tuning overrides (defaults come from the measured table in the design doc)
-  if (const char* t = std::getenv("ZC_TUNE_NTT_TILE")) ctx->ntt_tile_log = std::atoi(t);
-  if (const char* t = std::getenv("ZC_TUNE_NTT_MINB")) ctx->ntt_minb = std::atoi(t);
   if (cudaSetDevice(ctx->device) != cudaSuccess) {
     delete ctx;
     return ZC_ERR_CUDA;
@@ -632,6 +629,7 @@ void zc_destroy(zc_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
+  destroy_lanes(ctx);
   if (ctx->arena.base) cudaFree(ctx->arena.base);
   for (auto& t : ctx->ntt_cache)
     if (t.mem) cudaFree(t.mem);
@@ -791,6 +789,38 @@ zc_status zc_stats(zc_ctx* ctx, double* phase_ms, uint32_t cap) {
   out[8] = ctx->dom_bytes;
   out[9] = ctx->launches;
   for (uint32_t i = 0; i < cap && i < 10; i++) phase_ms[i] = out[i];
+  return ZC_OK;
+}
+
+static bool tune_value_ok(zc_tune_key key, int32_t v) {
+  if (v == 0) return true;
+  switch (key) {
+    case ZC_TUNE_SC_GRID: return v >= 1 && v <= 4096;
+    case ZC_TUNE_SC_TAIL_LOG: return v >= 1 && v <= 24;
+    case ZC_TUNE_NTT_TILE_LOG: return v >= 10 && v <= 12;
+    case ZC_TUNE_NTT_MINB: return v == 1 || v == 2;
+  }
+  return false;
+}
+
+static bool tune_form_ok(zc_form form, zc_tune_key key) {
+  if (form == ZC_FORM_SUMCHECK) return key == ZC_TUNE_SC_GRID || key == ZC_TUNE_SC_TAIL_LOG;
+  if (form == ZC_FORM_NTT) return key == ZC_TUNE_NTT_TILE_LOG || key == ZC_TUNE_NTT_MINB;
+  return false;
+}
+
+zc_status zc_tune_set(zc_ctx* ctx, zc_form form, uint32_t n, zc_tune_key key, int32_t value) {
+  if (!ctx || n > (uint32_t)kMaxN || !tune_form_ok(form, key) || !tune_value_ok(key, value))
+    return ZC_ERR_ARG;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->tune[(int)form - 1][n][(int)key - 1] = value;
+  return ZC_OK;
+}
+
+zc_status zc_tune_get(zc_ctx* ctx, zc_form form, uint32_t n, zc_tune_key key, int32_t* value) {
+  if (!ctx || !value || n > (uint32_t)kMaxN || !tune_form_ok(form, key)) return ZC_ERR_ARG;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  *value = ctx->tuned(form, n, key);
   return ZC_OK;
 }
 

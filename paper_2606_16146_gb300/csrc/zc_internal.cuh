@@ -98,8 +98,16 @@ struct zc_ctx {
   double dom_bytes = 0;
   int dom_a = 2, dom_b = 3;      // events bracketing that launch
   int skip_point = 0;            // 0: derive H(1) from the claim (default), 1: derive H(0)
-  int ntt_tile_log = 10;         // NTT pass tile (log2 elements), raised to the sub-DFT length
-  int ntt_minb = 2;              // NTT pass: minimum resident CTAs per SM for the 2048 tile
+  uint32_t cur_n = 0;            // n of the proof being enqueued (selects tuned launch shapes)
+  // launch parameters set by zc_tune_set: [form - 1][n][key - 1], 0 = unset;
+  // n = 0 holds the value for sizes without their own entry
+  int32_t tune[2][zc::kMaxN + 1][4] = {};
+  int32_t tuned(zc_form form, uint32_t n, zc_tune_key key) const {
+    const int f = (int)form - 1, k = (int)key - 1;
+    if (f < 0 || f > 1 || k < 0 || k > 3) return 0;
+    if (n <= (uint32_t)zc::kMaxN && tune[f][n][k]) return tune[f][n][k];
+    return tune[f][0][k];
+  }
   // per-size NTT tables (twiddles, coset factors, quotient scale), built on
   // first use of a size; see zc_ntt.cu
   struct NttSizeTables {
@@ -112,6 +120,17 @@ struct zc_ctx {
   std::vector<NttSizeTables> ntt_cache;
   uint64_t ntt_cache_clock = 0;
   size_t ntt_cache_budget = 16ull << 30;
+  // While a prepared batch is being enqueued (possibly under graph capture)
+  // the cache neither allocates nor evicts; a missing size falls back to the
+  // two-level power tables.
+  bool ntt_cache_frozen = false;
+  zc_ctx* table_owner = nullptr;    // lanes use their parent's per-size tables
+  bool owns_const = true;           // lanes share the parent's constants
+  // batch lanes: child contexts with their own scratch arena and stream
+  std::vector<zc_ctx*> lanes;
+  std::vector<cudaStream_t> lane_streams;
+  std::vector<cudaEvent_t> lane_join;
+  cudaEvent_t fork_ev = nullptr;
 };
 
 namespace zc {
@@ -154,6 +173,12 @@ zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* col
 zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, int on_dev,
                     const uint8_t (*roots)[32], cudaStream_t st, uint8_t* proof,
                     bool proof_on_dev, void* q_out, int q_on_dev);
+// scratch bytes one proof needs (device columns, device roots computed)
+size_t sumcheck_scratch_bytes(const zc_ctx* ctx, const zc_params* p);
+size_t ntt_scratch_bytes(const zc_params* p, int sm_count, bool q_direct);
+// allocation-time set-up of the NTT form for one size (tables, attributes)
+zc_status ntt_prepare(zc_ctx* ctx, const zc_params* p, cudaStream_t st);
+void destroy_lanes(zc_ctx* ctx);
 
 // ------------------------------------------------------------ device helpers
 #if defined(__CUDACC__)

@@ -630,10 +630,20 @@ static void set_pass_attributes() {
   cudaFuncSetAttribute(k_ntt_pass<4096, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4096 * 32);
 }
 
+static int g_attr_done[64] = {0};
+static void ensure_pass_attributes(int dev) {
+  std::lock_guard<std::mutex> lk(g_tabs_mu);
+  if (!g_attr_done[dev]) {
+    set_pass_attributes();
+    g_attr_done[dev] = 1;
+  }
+}
+
 // launch one batched pass over `items` columns
 static zc_status run_pass(zc_ctx* ctx, cudaStream_t st, NttPassArgs& a, int items, uint64_t B) {
   const uint32_t logL = a.logL;
-  uint32_t logTile = (uint32_t)ctx->ntt_tile_log;
+  uint32_t logTile = (uint32_t)ctx->tuned(ZC_FORM_NTT, ctx->cur_n, ZC_TUNE_NTT_TILE_LOG);
+  const int minb = ctx->tuned(ZC_FORM_NTT, ctx->cur_n, ZC_TUNE_NTT_MINB);
   if (logTile < logL) logTile = logL < 10 ? 10 : logL;
   if (logTile > 12) logTile = 12;
   if (logTile < 10) logTile = 10;
@@ -647,7 +657,7 @@ static zc_status run_pass(zc_ctx* ctx, cudaStream_t st, NttPassArgs& a, int item
   }
   dim3 grid((unsigned)blocks, (unsigned)items);
   if (logTile == 12) launch_pass_variant<4096, 1>(a, grid, st);
-  else if (logTile == 11 && ctx->ntt_minb >= 2) launch_pass_variant<2048, 2>(a, grid, st);
+  else if (logTile == 11 && minb != 1) launch_pass_variant<2048, 2>(a, grid, st);
   else if (logTile == 11) launch_pass_variant<2048, 1>(a, grid, st);
   else launch_pass_variant<1024, 4>(a, grid, st);
   ctx->launches++;
@@ -657,8 +667,9 @@ static zc_status run_pass(zc_ctx* ctx, cudaStream_t st, NttPassArgs& a, int item
 // The per-size tables of (n, lb), built on first use; nullptr when they
 // would exceed the context's table budget (the passes then form every factor
 // from the two-level power tables instead).
-static zc_ctx::NttSizeTables* size_tables(zc_ctx* ctx, const NttTables* T, uint32_t n, uint32_t lb,
+static zc_ctx::NttSizeTables* size_tables(zc_ctx* user, const NttTables* T, uint32_t n, uint32_t lb,
                                           uint32_t l1, uint32_t l2, cudaStream_t st) {
+  zc_ctx* ctx = user->table_owner ? user->table_owner : user;
   const uint64_t N = 1ull << n, M = N << lb;
   for (auto& e : ctx->ntt_cache)
     if (e.n == n && e.lb == lb) {
@@ -666,7 +677,7 @@ static zc_ctx::NttSizeTables* size_tables(zc_ctx* ctx, const NttTables* T, uint3
       return &e;
     }
   const size_t bytes = sizeof(fr) * (2 * N + 3 * M);
-  if (bytes > ctx->ntt_cache_budget) return nullptr;
+  if (ctx->ntt_cache_frozen || bytes > ctx->ntt_cache_budget) return nullptr;
   size_t used = 0;
   for (auto& e : ctx->ntt_cache) used += e.bytes;
   while (!ctx->ntt_cache.empty() && used + bytes > ctx->ntt_cache_budget) {
@@ -720,10 +731,46 @@ static void pass_defaults(NttPassArgs& a) {
   a.out_lbdiv = 63;
 }
 
+static uint32_t ntt_log_blowup(const zc_params* p) {
+  uint32_t lb = p->log_blowup;
+  if (!lb)
+    while ((1u << lb) < p->d) lb++;
+  return lb;
+}
+
+size_t ntt_scratch_bytes(const zc_params* p, int sm_count, bool q_direct) {
+  const uint32_t n = p->n, lb = ntt_log_blowup(p);
+  const int c = gate_ncols(p->gate, p->d);
+  const uint64_t N = 1ull << n, M = N << lb, s = 1ull << lb;
+  const uint32_t hbits = (n + 1) / 2;
+  const uint32_t nlo = 1u << hbits, nhi = 1u << (n - hbits);
+  const uint32_t nblk_open = 2 * (uint32_t)sm_count;
+  const size_t psize = 20 + 32 + 32 * ((size_t)c + 1);
+  size_t need = 2 * align_up(sizeof(fr) * N, 256) * c + align_up(sizeof(fr) * M, 256);
+  if (!q_direct) need += align_up(sizeof(fr) * M, 256);
+  need += align_up(sizeof(fr) * s * (nlo + nhi), 256) + align_up(sizeof(fr) * s, 256);
+  need += align_up(sizeof(fr) * (c + 1) * nblk_open, 256) + align_up(sizeof(fr) * 32, 256);
+  need += align_up(sizeof(NttState), 256) + align_up(psize, 256) + align_up(32 * (size_t)(c + 1), 256);
+  need += root_scratch_bytes(c, N) + root_scratch_bytes(1, M) + 8192;
+  return need;
+}
+
+zc_status ntt_prepare(zc_ctx* ctx, const zc_params* p, cudaStream_t st) {
+  ensure_pass_attributes(ctx->device);
+  NttTables* T = nullptr;
+  zc_status s0 = ensure_tables(ctx, st, &T);
+  if (s0 != ZC_OK) return s0;
+  const uint32_t n = p->n, lb = ntt_log_blowup(p);
+  const bool two = n > 12;
+  size_tables(ctx, T, n, lb, two ? (n + 1) / 2 : n, two ? n / 2 : 0, st);
+  return cudaStreamSynchronize(st) == cudaSuccess ? ZC_OK : ZC_ERR_CUDA;
+}
+
 zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, int on_dev,
                     const uint8_t (*roots)[32], cudaStream_t st, uint8_t* proof,
                     bool proof_on_dev, void* q_out, int q_on_dev) {
   const uint32_t gate = p->gate, n = p->n, d = p->d;
+  ctx->cur_n = n;
   if (n > (uint32_t)kMaxNttN) {
     ctx->err = "NTT form supports n <= 24";
     return ZC_ERR_UNSUPPORTED;
@@ -738,11 +785,7 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
   const int c = gate_ncols(gate, d);
   const uint64_t N = 1ull << n, M = 1ull << logm, s = 1ull << lb;
   const size_t psize = 20 + 32 + 32 * ((size_t)c + 1);
-  static int attr_done[64] = {0};
-  if (!attr_done[ctx->device]) {
-    set_pass_attributes();
-    attr_done[ctx->device] = 1;
-  }
+  ensure_pass_attributes(ctx->device);
   NttTables* T = nullptr;
   zc_status s0 = ensure_tables(ctx, st, &T);
   if (s0 != ZC_OK) return s0;

@@ -674,19 +674,23 @@ struct ScBuffers {
 
 struct ScPlan {
   int c, G, grid_plonk, grid_prod, npmax;
+  uint64_t tail_pairs;
   uint32_t eq_total, eq_hi[kMaxN], eq_lo[kMaxN], mlo[kMaxN];
   EqTask tasks[2 * kMaxN];
 };
 
-static ScPlan sc_plan(const zc_params* p, int SMs) {
+// grid: most CTAs per round kernel (0: two per SM); tail_log: the tail takes
+// over at 2^tail_log pairs (0: the gate's default).
+static ScPlan sc_plan(const zc_params* p, int SMs, int grid = 0, int tail_log = 0) {
   ScPlan P{};
   const uint32_t n = p->n, d = p->d;
   const bool plonk = p->gate == ZC_GATE_PLONK;
   P.c = gate_ncols(p->gate, d);
   P.G = 1;
   while (P.G * kPP < (int)d + 1) P.G *= 2;
-  P.grid_plonk = std::max(8, 2 * SMs / 8 * 8);
-  P.grid_prod = 2 * SMs;
+  P.grid_plonk = grid > 0 ? grid : std::max(8, 2 * SMs / 8 * 8);
+  P.grid_prod = grid > 0 ? grid : 2 * SMs;
+  P.tail_pairs = tail_log > 0 ? 1ull << tail_log : (plonk ? kTailPairsPlonk : kTailPairsProd);
   P.npmax = (int)d + 1;
   for (uint32_t i = 0; i < n; i++) {
     uint32_t mlo, mhi;
@@ -767,7 +771,7 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
   R.kcomp = hC.rnegpow[d - 2];
   R.C = dC;
   R.tabs = dtabs;
-  const uint64_t tail_pairs = plonk ? kTailPairsPlonk : kTailPairsProd;
+  const uint64_t tail_pairs = P.tail_pairs;
   const fr* cur[kMaxCols];
   for (int j = 0; j < c; j++) cur[j] = src[j];
   uint32_t i = 0;
@@ -828,11 +832,22 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
   return cudaGetLastError() == cudaSuccess ? ZC_OK : ZC_ERR_CUDA;
 }
 
+size_t sumcheck_scratch_bytes(const zc_ctx* ctx, const zc_params* p) {
+  const ScPlan P = sc_plan(p, ctx->sm_count, ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_GRID),
+                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_TAIL_LOG));
+  const uint64_t N = 1ull << p->n;
+  const size_t psize = 16 + 32 * ((size_t)p->n * (p->d + 2) + P.c);
+  return align_up(sizeof(fr) * N, 256) * P.c + align_up(sizeof(fr) * sc_partials_count(P), 256) +
+         align_up(sizeof(fr) * P.eq_total, 256) + align_up(sizeof(ScState), 256) + align_up(psize, 256) +
+         align_up(32 * (size_t)P.c, 256) + 4096 + root_scratch_bytes(P.c, N);
+}
+
 zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, int on_dev,
                          const uint8_t (*roots)[32], cudaStream_t st, uint8_t* proof,
                          bool proof_on_dev) {
   const uint32_t n = p->n, d = p->d;
-  const ScPlan P = sc_plan(p, ctx->sm_count);
+  const ScPlan P = sc_plan(p, ctx->sm_count, ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_GRID),
+                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_TAIL_LOG));
   const int c = P.c;
   const uint64_t N = 1ull << n;
   const size_t psize = 16 + 32 * ((size_t)n * (d + 2) + c);

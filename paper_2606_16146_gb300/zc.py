@@ -21,6 +21,7 @@ STATUS = {0: "ZC_OK", 1: "ZC_ERR_ARG", 2: "ZC_ERR_OOM", 3: "ZC_ERR_CUDA", 4: "ZC
           5: "ZC_ERR_UNSUPPORTED", 6: "ZC_ERR_BUFFER_TOO_SMALL"}
 ZC_GATE_PLONK, ZC_GATE_PRODUCT = 1, 2
 ZC_FORM_SUMCHECK, ZC_FORM_NTT = 1, 2
+ZC_TUNE_SC_GRID, ZC_TUNE_SC_TAIL_LOG, ZC_TUNE_NTT_TILE_LOG, ZC_TUNE_NTT_MINB = 1, 2, 3, 4
 
 
 class ZCError(RuntimeError):
@@ -67,8 +68,22 @@ def lib(path: str | None = None):
         L.zc_verify.restype = ctypes.c_int
         L.zc_roots.argtypes = [vp, P(zc_params), vp, ctypes.c_int, vp, vp]
         L.zc_roots.restype = ctypes.c_int
+        L.zc_tune_set.argtypes = [vp, ctypes.c_int, ctypes.c_uint32, ctypes.c_int, ctypes.c_int32]
+        L.zc_tune_set.restype = ctypes.c_int
+        L.zc_tune_get.argtypes = [vp, ctypes.c_int, ctypes.c_uint32, ctypes.c_int, P(ctypes.c_int32)]
+        L.zc_tune_get.restype = ctypes.c_int
         L.zc_stats.argtypes = [vp, P(ctypes.c_double), ctypes.c_uint32]
         L.zc_stats.restype = ctypes.c_int
+        L.zc_prove_batch.argtypes = [vp, ctypes.c_uint32, vp, vp, vp, vp, vp, vp]
+        L.zc_prove_batch.restype = ctypes.c_int
+        L.zc_batch_create.argtypes = [vp, ctypes.c_uint32, vp, vp, vp, vp, vp, P(vp)]
+        L.zc_batch_create.restype = ctypes.c_int
+        L.zc_batch_launch.argtypes = [vp, vp]
+        L.zc_batch_launch.restype = ctypes.c_int
+        L.zc_batch_kernels.argtypes = [vp]
+        L.zc_batch_kernels.restype = ctypes.c_uint32
+        L.zc_batch_destroy.argtypes = [vp]
+        L.zc_batch_destroy.restype = None
         L.zc_prove_sumcheck_static.argtypes = [P(zc_params), vp, vp, vp, u8p, sz, P(sz)]
         L.zc_prove_sumcheck_static.restype = ctypes.c_int
         L.zc_last_error.argtypes = [vp]
@@ -203,10 +218,81 @@ class Context:
         self._check(st, "zc_roots")
         return [out[32 * j:32 * j + 32].tobytes() for j in range(c)]
 
+    def _batch_args(self, forms, params, cols, proofs, q_outs):
+        n = len(forms)
+        F = (ctypes.c_int * n)(*forms)
+        Pa = (zc_params * n)(*[zc_params(g, nn, d, lb) for (g, nn, d, lb) in params])
+        inner = [_Ptrs(c) for c in cols]
+        C = (ctypes.c_void_p * n)(*[ctypes.cast(x.arr, ctypes.c_void_p).value for x in inner])
+        Pr = (ctypes.c_void_p * n)(*[_addr(p) for p in proofs])
+        Q = None
+        if q_outs is not None:
+            Q = (ctypes.c_void_p * n)(*[(_addr(q) if q is not None else None) for q in q_outs])
+        keep = (F, Pa, inner, C, Pr, Q)
+        return keep, F, Pa, C, Pr, Q
+
+    def prove_batch(self, forms, params, cols, proofs, q_outs=None, stream=None):
+        """Prove a batch (device columns, proofs and q).  params: (gate, n, d, log_blowup)."""
+        keep, F, Pa, C, Pr, Q = self._batch_args(forms, params, cols, proofs, q_outs)
+        st = lib().zc_prove_batch(self.h, len(forms), ctypes.cast(F, ctypes.c_void_p),
+                                  ctypes.cast(Pa, ctypes.c_void_p), ctypes.cast(C, ctypes.c_void_p),
+                                  _stream_ptr(stream), ctypes.cast(Pr, ctypes.c_void_p),
+                                  ctypes.cast(Q, ctypes.c_void_p) if Q is not None else None)
+        self._check(st, "zc_prove_batch")
+
+    def batch_graph(self, forms, params, cols, proofs, q_outs=None):
+        """Capture the batch into one CUDA graph; returns a BatchGraph."""
+        keep, F, Pa, C, Pr, Q = self._batch_args(forms, params, cols, proofs, q_outs)
+        h = ctypes.c_void_p()
+        st = lib().zc_batch_create(self.h, len(forms), ctypes.cast(F, ctypes.c_void_p),
+                                   ctypes.cast(Pa, ctypes.c_void_p), ctypes.cast(C, ctypes.c_void_p),
+                                   ctypes.cast(Pr, ctypes.c_void_p),
+                                   ctypes.cast(Q, ctypes.c_void_p) if Q is not None else None,
+                                   ctypes.byref(h))
+        self._check(st, "zc_batch_create")
+        return BatchGraph(h, keep)
+
+    def tune_set(self, form: int, n: int, key: int, value: int) -> None:
+        """Launch parameter for proofs of (form, n); n = 0 for every size, value 0 clears."""
+        self._check(lib().zc_tune_set(self.h, form, n, key, value), "zc_tune_set")
+
+    def tune_get(self, form: int, n: int, key: int) -> int:
+        v = ctypes.c_int32()
+        self._check(lib().zc_tune_get(self.h, form, n, key, ctypes.byref(v)), "zc_tune_get")
+        return int(v.value)
+
     def stats(self) -> list[float]:
         a = (ctypes.c_double * 10)()
         self._check(lib().zc_stats(self.h, a, 10), "zc_stats")
         return list(a)
+
+
+class BatchGraph:
+    """A batch captured as one CUDA graph (zc_batch)."""
+
+    def __init__(self, h, keep):
+        self.h = h
+        self._keep = keep
+
+    def launch(self, stream=None):
+        st = lib().zc_batch_launch(self.h, _stream_ptr(stream))
+        if st != ZC_OK:
+            raise ZCError(st, "zc_batch_launch")
+
+    @property
+    def kernels(self) -> int:
+        return int(lib().zc_batch_kernels(self.h))
+
+    def close(self):
+        if self.h:
+            lib().zc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def verify(gate, n, d, form, cols, proof, q=None, roots=None, log_blowup=0) -> bool:
