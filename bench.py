@@ -37,6 +37,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2606_16146_gb300.costs import algorithmic_bytes, algorithmic_mulmods  # noqa: E402
+
 METRIC = "ZeroCheck prove ms (SumCheck vs NTT) by n, degree; served p50/p99 ms"
 GATE, N_LOG, DEG = 1, 22, 3
 SAMPLE_N = 18
@@ -44,27 +46,16 @@ SM_COUNT, IMAD_PER_CLK, SM_MAX_MHZ, IMAD_PER_MULMOD = 152, 64, 2070.0, 272
 ALU_PEAK_MULMOD = SM_COUNT * IMAD_PER_CLK * SM_MAX_MHZ * 1e6 / IMAD_PER_MULMOD
 
 
-def algorithmic_mulmods(form: str, n: int, d: int = 3, gate: int = 1) -> float:
-    """Per-proof modular multiplications (the counts fixed for the roofline)."""
-    N = 1 << n
-    c = 8 if gate == 1 else d + 1
-    g = 5 if gate == 1 else d - 1
-    s = 1 << max(0, (d - 1).bit_length())
-    M = s * N
-    if form == "sumcheck":
-        return (N - 1) * ((d + 1) * (g + 1) + 1 + c)
-    return (c * (N / 2) * n + c * s * (N + (N / 2) * n) + M * (g + 1)
-            + (M / 2) * math.log2(M) + M + c * N + (d - 1) * N)
+def _hbm_peak_bytes_s() -> float:
+    """Measured HBM copy bandwidth of this GPU model (bytes/s), else the fallback 6.8 TB/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]) * 1e9
+    except (OSError, KeyError, ValueError):
+        return 6.8e12
 
 
-def algorithmic_bytes(form: str, n: int, d: int = 3, gate: int = 1) -> float:
-    N = 1 << n
-    c = 8 if gate == 1 else d + 1
-    s = 1 << max(0, (d - 1).bit_length())
-    M = s * N
-    if form == "sumcheck":
-        return 128.0 * c * N
-    return 32.0 * (2 * c * N + c * M + M + 2 * M + c * N + M)
+HBM_PEAK = _hbm_peak_bytes_s()
 
 
 class ClockSampler:
@@ -179,6 +170,282 @@ def workload_config(world):
             "parallelism": f"replicas x{world}", "l2": "inputs (1 GiB) larger than L2; no flush"}
 
 
+def _median_event_ms(fn, stream, reps):
+    import torch
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts)), ts
+
+
+def _base_line(args, world, value, unit, hib, config):
+    return {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": hib, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32x8 (255-bit field, exact)", "data": "synthetic",
+            "config": config}
+
+
+def run_batched(args, world, rank, local):
+    """64 mixed instances (n 10..20 log-uniform, Plonk d=3 / product d=8), seeds
+    3000+i: one CUDA graph per batch against 64 sequential plain calls, for
+    all-SumCheck, all-NTT and cost-model-routed form assignments."""
+    import torch
+    from paper_2606_16146_gb300 import tune, witness, workloads, zc
+    from paper_2606_16146_gb300.router import CostModel
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = zc.Context(local, max_n=24, max_d=8)
+    inst = workloads.batched_instances()
+    cols = [witness.generate(s.gate, s.n, s.d, seed) for s, seed in inst]
+    dcols = [[torch.from_numpy(c).to(dev) for c in cc] for cc in cols]
+    stream = torch.cuda.Stream(dev)
+    model = CostModel()
+    model.calibrate(ctx, [(1, 3), (2, 8)], ns=[10, 12, 14, 16, 18, 20], reps=3)
+    variants = {
+        "sumcheck": [zc.ZC_FORM_SUMCHECK] * len(inst),
+        "ntt": [zc.ZC_FORM_NTT] * len(inst),
+        "routed": [model.route(s.gate, s.n, s.d) for s, _ in inst],
+    }
+    params = [(s.gate, s.n, s.d, 0) for s, _ in inst]
+    out = {}
+    K, W = args.steps, max(3, args.warmup)
+    for name, forms in variants.items():
+        seq_p = [torch.zeros(zc.proof_size(s.gate, s.n, s.d, f), dtype=torch.uint8, device=dev)
+                 for (s, _), f in zip(inst, forms)]
+        bat_p = [torch.zeros_like(x) for x in seq_p]
+
+        def sequential():
+            for (s, _), f, dc, pr in zip(inst, forms, dcols, seq_p):
+                if f == zc.ZC_FORM_SUMCHECK:
+                    ctx.prove_sumcheck(s.gate, s.n, s.d, dc, stream=stream, proof_out=pr)
+                else:
+                    ctx.prove_ntt(s.gate, s.n, s.d, dc, stream=stream, proof_out=pr, want_q=False)
+        for _ in range(W):
+            sequential()
+        seq_ms, _ = _median_event_ms(sequential, stream, K)
+        tuned = tune.tune_batch(ctx, forms, params, dcols, bat_p, None, reps=3)
+        g = ctx.batch_graph(forms, params, dcols, bat_p, None)
+        for _ in range(W):
+            g.launch(stream)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        time.sleep(0.3)
+        bat_ms, _ = _median_event_ms(lambda: g.launch(stream), stream, K)
+        clk = clocks.stop()
+        torch.cuda.synchronize()
+        exact = all(a.cpu().numpy().tobytes() == b.cpu().numpy().tobytes() for a, b in zip(seq_p, bat_p))
+        mm = sum(algorithmic_mulmods("sumcheck" if f == 1 else "ntt", s.n, s.d, s.gate)
+                 for (s, _), f in zip(inst, forms))
+        out[name] = {"sequential_ms": seq_ms, "batched_ms": bat_ms, "speedup": seq_ms / bat_ms,
+                     "proofs_per_s": len(inst) / (bat_ms * 1e-3),
+                     "sequential_proofs_per_s": len(inst) / (seq_ms * 1e-3),
+                     "exact_vs_sequential": exact, "graph_kernels": g.kernels,
+                     "forms": {"sumcheck": forms.count(1), "ntt": forms.count(2)},
+                     "tuned": {"settings": tuned["best"], "trials": len(tuned["trials"]),
+                               "untuned_ms": tuned["trials"][0][2]},
+                     "alu_frac": mm / (bat_ms * 1e-3) / ALU_PEAK_MULMOD, "clocks": clk}
+        last_graph = g
+    best = out["routed"]
+    # end to end: columns from pinned host memory, one graph launch, proofs back
+    hcols = [[torch.from_numpy(c).pin_memory() for c in cc] for cc in cols]
+    forms = variants["routed"]
+    proofs = [torch.zeros(zc.proof_size(s.gate, s.n, s.d, f), dtype=torch.uint8, device=dev)
+              for (s, _), f in zip(inst, forms)]
+    g = ctx.batch_graph(forms, params, dcols, proofs, None)
+    hp = [torch.empty(x.numel(), dtype=torch.uint8).pin_memory() for x in proofs]
+    e2e = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t_a = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for dc, hc in zip(dcols, hcols):
+                for d_, h_ in zip(dc, hc):
+                    d_.copy_(h_, non_blocking=True)
+            g.launch(stream)
+            for d_, h_ in zip(proofs, hp):
+                h_.copy_(d_, non_blocking=True)
+        stream.synchronize()
+        e2e.append((time.perf_counter() - t_a) * 1e3)
+    h2d = sum(c.nbytes for cc in cols for c in cc)
+    d2h = sum(x.numel() for x in proofs)
+    mm = sum(algorithmic_mulmods("sumcheck" if f == 1 else "ntt", s.n, s.d, s.gate)
+             for (s, _), f in zip(inst, forms))
+    achieved = mm / (best["batched_ms"] * 1e-3)
+    config = {"workload": "batched: 64 ZeroCheck instances, n log-uniform 10..20, Plonk d=3 / product "
+                          "d=8 with equal probability, seeds 3000+i, one CUDA graph per batch; baseline "
+                          "64 sequential plain calls on one stream",
+              "instances": len(inst), "n_range": [10, 20], "degrees": [3, 8],
+              "parallelism": f"replicas x{world}", "l2": "batch columns (~GBs) larger than L2; no flush"}
+    line = _base_line(args, world, best["batched_ms"], "ms", False, config)
+    line["ms_per_step"] = best["batched_ms"]
+    line["proofs_per_s"] = best["proofs_per_s"]
+    line["by_variant"] = out
+    line["e2e"] = {"value": float(np.median(e2e)), "unit": "ms", "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h}
+    line["gpu_launches"] = best["graph_kernels"] * args.steps
+    line["roofline"] = {"bound": "alu", "kernel": "whole batch graph (all instances)", "achieved": achieved,
+                        "peak": ALU_PEAK_MULMOD, "unit": "mulmod/s", "frac": achieved / ALU_PEAK_MULMOD,
+                        "traffic": None,
+                        "peak_note": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz / 272 IMAD per mulmod"}
+    line["clocks"] = best["clocks"]
+    line["cost_model_ms"] = [[*k, v] for k, v in sorted(model.table.items())]
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_sample_batched(inst, cols, forms)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    del last_graph, g
+    ctx.close()
+
+
+def cpu_sample_batched(inst, cols, forms):
+    """Oracle on the instances with n <= 14 of the batch, scaled to the whole batch by work."""
+    import oracle
+    t_s, mm_s, mm_all = 0.0, 0.0, 0.0
+    for (s, _), cc, f in zip(inst, cols, forms):
+        name = "sumcheck" if f == 1 else "ntt"
+        w = algorithmic_mulmods(name, s.n, s.d, s.gate)
+        mm_all += w
+        if s.n > 14:
+            continue
+        t0 = time.perf_counter()
+        if f == 1:
+            oracle.prove_sumcheck(s.gate, s.n, s.d, cc)
+        else:
+            oracle.prove_ntt(s.gate, s.n, s.d, cc)
+        t_s += time.perf_counter() - t0
+        mm_s += w
+    ms = t_s * 1e3 * mm_all / mm_s
+    return {"value": ms, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"the batch's instances with n <= 14 (routed forms), {t_s:.2f} s, scaled to "
+                      f"all 64 by algorithmic mulmods (x{mm_all / mm_s:.1f})"}
+
+
+SWEEP = [(1, 12, 3), (1, 20, 3), (1, 22, 3), (2, 22, 2), (2, 22, 4), (2, 22, 8), (2, 22, 16), (2, 22, 32)]
+
+
+def run_sweep(args, world, rank, local):
+    """Both forms, one proof at a time, over the plain and high-degree shapes:
+    Plonk n = 12, 20, 22 and the product gate at n = 22 for d = 2..32."""
+    import torch
+    from paper_2606_16146_gb300 import witness, zc
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = zc.Context(local, max_n=24, max_d=32)
+    stream = torch.cuda.Stream(dev)
+    rows = []
+    K, W = max(1, args.steps), max(3, args.warmup)
+    clocks = ClockSampler(local)
+    clocks.start()
+    for gate, n, d in SWEEP:
+        cols = witness.generate(gate, n, d, 1000 + n if gate == 1 else 2000 + 10 * d + n)
+        dcols = [torch.from_numpy(c).to(dev) for c in cols]
+        roots = ctx.roots(gate, n, d, dcols)
+        row = {"gate": "plonk" if gate == 1 else "product", "n": n, "d": d}
+        for form, name in ((zc.ZC_FORM_SUMCHECK, "sumcheck"), (zc.ZC_FORM_NTT, "ntt")):
+            proof = torch.zeros(zc.proof_size(gate, n, d, form), dtype=torch.uint8, device=dev)
+            if form == zc.ZC_FORM_SUMCHECK:
+                def fn():
+                    ctx.prove_sumcheck(gate, n, d, dcols, roots=roots, stream=stream, proof_out=proof)
+            else:
+                def fn():
+                    ctx.prove_ntt(gate, n, d, dcols, roots=roots, stream=stream, proof_out=proof,
+                                  want_q=False)
+            for _ in range(W):
+                fn()
+            ms, _ = _median_event_ms(fn, stream, K)
+            roof = 1e3 * max(algorithmic_mulmods(name, n, d, gate) / ALU_PEAK_MULMOD,
+                             algorithmic_bytes(name, n, d, gate) / HBM_PEAK)
+            row[name] = {"ms": ms, "roofline_ms": roof, "roofline_frac": roof / ms,
+                         "phases_ms": [round(x, 4) for x in ctx.stats()[:6]]}
+        rows.append(row)
+        del dcols
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    head = rows[2]
+    config = {"workload": "sweep: one proof of each form at a time; Plonk n=12, 20, 22 and product gate "
+                          "n=22, d in {2, 4, 8, 16, 32}; column roots given (untimed)",
+              "parallelism": f"replicas x{world}", "l2": "n >= 20 inputs larger than L2; no flush"}
+    line = _base_line(args, world, head["sumcheck"]["ms"] + head["ntt"]["ms"], "ms", False, config)
+    line["value_is"] = "Plonk n=22: SumCheck ms + NTT ms"
+    line["rows"] = rows
+    line["clocks"] = clk
+    line["e2e"] = None
+    line["e2e_note"] = "device-resident columns; the plain workload line carries the host-buffer run"
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_served(args, world, rank, local):
+    """Poisson request loop (n 12..24, d in {3, 8, 16}), admission by HBM
+    footprint against a 180 GB pool, cost-model routing; against the same
+    requests one at a time (one slot)."""
+    import torch
+    from paper_2606_16146_gb300 import serve, workloads, zc
+    from paper_2606_16146_gb300.router import CostModel
+    torch.cuda.set_device(local)
+    ctx = zc.Context(local, max_n=24, max_d=16)
+    model = CostModel()
+    model.calibrate(ctx, [(1, 3), (2, 8), (2, 16)], ns=[12, 14, 16, 18, 20], reps=3)
+    rates = [float(r) for r in args.rates.split(",")]
+    lists = {r: workloads.served_requests(r, args.requests) for r in rates}
+    budget = 180 * 10**9
+    srv = serve.Server(ctx, model=model, slots=8, hbm_budget_bytes=budget)
+    one = serve.Server(ctx, model=model, slots=1, hbm_budget_bytes=budget, in_order=True)
+    t_pool = time.perf_counter()
+    srv.load_pool([s for lst in lists.values() for _, s in lst])
+    t_pool = time.perf_counter() - t_pool
+    one.pool = srv.pool
+    # warm-up: every shape once through the loop (tables, lanes, pool allocation)
+    warm = [(0.0, s) for s in sorted(srv.pool, key=lambda s: (s.n, s.d))]
+    srv.run(srv.build(warm))
+    one.run(one.build(warm))
+    torch.cuda.synchronize()
+    rows = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches = 0
+    for r, lst in lists.items():
+        reqs = srv.build(lst)
+        res = srv.run(reqs)
+        launches += ctx.stats()[9]
+        rep = serve.report(reqs, res)
+        base_reqs = one.build(lst)
+        base = serve.report(base_reqs, one.run(base_reqs))
+        exact = all(a["proof"].cpu().numpy().tobytes() == b["proof"].cpu().numpy().tobytes()
+                    for a, b in zip(reqs, base_reqs))
+        rows[str(int(r))] = {"served": rep, "one_at_a_time": base, "exact_vs_one_at_a_time": exact}
+    clk = clocks.stop()
+    mid = rows[str(int(rates[len(rates) // 2]))]["served"]
+    config = {"workload": "served: Poisson arrivals, n uniform 12..24, d in {3 (Plonk), 8, 16 (product)}, "
+                          "witness pool per shape on the device, admission by scratch footprint against "
+                          "a 180 GB pool, 8 slots, cost-model routing; baseline: the same requests one "
+                          "at a time (1 slot)",
+              "rates_req_s": rates, "requests_per_rate": args.requests, "slots": 8,
+              "hbm_budget_bytes": budget, "parallelism": f"replicas x{world}",
+              "l2": "pool witnesses (tens of GB) larger than L2; no flush"}
+    line = _base_line(args, world, mid["p99_ms"], "ms", False, config)
+    line["value_is"] = f"p99 latency at {int(rates[len(rates) // 2])} req/s"
+    line["by_rate"] = rows
+    line["gpu_launches"] = int(launches)
+    line["clocks"] = clk
+    line["pool_setup_s"] = t_pool
+    line["cost_model_ms"] = [[*k, v] for k, v in sorted(model.table.items())]
+    line["e2e"] = None
+    line["e2e_note"] = ("latencies are host-observed from arrival to completion; request columns come "
+                        "from the device-resident witness pool, so there is no separate host-buffer run")
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -189,6 +456,11 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="override n (profiling smaller cases)")
     ap.add_argument("--form", default="both", choices=["both", "sumcheck", "ntt"],
                     help="restrict the step to one form (profiling); the bench line uses both")
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "served", "sweep"],
+                    help="plain: one Plonk n=22 proof per form (the headline line); batched: 64 "
+                         "mixed instances in one graph; served: Poisson request loop")
+    ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="served: arrival rates (req/s)")
+    ap.add_argument("--requests", type=int, default=200, help="served: requests per rate")
     args = ap.parse_args()
     global N_LOG
     if args.n:
@@ -196,6 +468,15 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload == "batched":
+        run_batched(args, world, rank, local)
+        return
+    if args.workload == "served":
+        run_served(args, world, rank, local)
+        return
+    if args.workload == "sweep":
+        run_sweep(args, world, rank, local)
         return
     import torch
     from paper_2606_16146_gb300 import witness, zc
@@ -314,13 +595,13 @@ def main():
             "peak_note": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz / 272 IMAD per mulmod"}
     by_form = {"sumcheck": {"ms": float(np.median(sc_ms)),
                             "roofline_ms": 1e3 * max(algorithmic_mulmods("sumcheck", N_LOG) / ALU_PEAK_MULMOD,
-                                                      algorithmic_bytes("sumcheck", N_LOG) / 6674.2e9),
+                                                      algorithmic_bytes("sumcheck", N_LOG) / HBM_PEAK),
                             "phases_ms": [round(x, 4) for x in st_sc[:5]]}}
     by_form["sumcheck"]["roofline_frac"] = by_form["sumcheck"]["roofline_ms"] / by_form["sumcheck"]["ms"]
     if have_ntt:
         by_form["ntt"] = {"ms": float(np.median(nt_ms)),
                           "roofline_ms": 1e3 * max(algorithmic_mulmods("ntt", N_LOG) / ALU_PEAK_MULMOD,
-                                                    algorithmic_bytes("ntt", N_LOG) / 6674.2e9),
+                                                    algorithmic_bytes("ntt", N_LOG) / HBM_PEAK),
                           "phases_ms": [round(x, 4) for x in st_nt[:6]]}
         by_form["ntt"]["roofline_frac"] = by_form["ntt"]["roofline_ms"] / by_form["ntt"]["ms"]
     else:

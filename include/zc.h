@@ -218,6 +218,55 @@ zc_status zc_prove_sumcheck_static(const zc_params* params, const void* const* c
                                    const uint8_t (*col_roots)[32], void* cuda_stream,
                                    uint8_t* proof, size_t cap, size_t* len);
 
+/* ----------------------------------------------------------- serving --
+ * A request loop over a list of timed requests (the paper proves one
+ * instance at a time; serving is a deployment mode of the same arithmetic).
+ * Requests become visible at their arrival time; each is admitted when a
+ * slot (a stream with its own child context) is free AND its scratch fits in
+ * a device pool of hbm_budget_bytes (first fit).  Admitted proofs run
+ * concurrently; their tables and transcripts live in the pool block until
+ * completion is observed, when the block and slot return for the next
+ * admission (continuous batching).  Every proof is byte-identical to the one
+ * zc_prove_sumcheck / zc_prove_ntt returns for the same request.
+ *
+ * Scratch bytes one proof takes (device columns, roots computed on the
+ * device; q_on_device: the NTT quotient goes to a caller buffer). */
+zc_status zc_scratch_bytes(zc_ctx* ctx, const zc_params* params, zc_form form, int q_on_device,
+                           size_t* bytes);
+
+typedef struct {
+  double arrival_s;           /* seconds after the run starts */
+  zc_params params;
+  zc_form form;               /* the form chosen for this request (a router's job) */
+  const void* const* cols;    /* DEVICE columns, canonical (read only; may be shared) */
+  uint8_t* proof;             /* DEVICE buffer of zc_proof_size bytes */
+  void* q_out;                /* NTT form: DEVICE buffer of M*32 bytes, or NULL */
+} zc_request;
+
+typedef struct {
+  double admit_s;             /* when it got its slot and scratch (run clock) */
+  double done_s;              /* when its completion was observed (run clock) */
+  uint64_t scratch_bytes;     /* the footprint it was admitted with */
+  uint32_t slot;
+  uint32_t waited_for_memory; /* 1 if a free slot waited for pool space for it */
+  zc_status status;
+} zc_result;
+
+typedef struct {
+  uint32_t slots;             /* proofs in flight at most, 1..64 */
+  uint64_t hbm_budget_bytes;  /* size of the scratch pool (allocated once, kept) */
+  uint32_t in_order;          /* 1: admit strictly by arrival; 0: a request that
+                                 does not fit yet lets later ones that fit pass */
+  double timeout_s;           /* ZC_ERR_TIMEOUT if the run lasts longer (0: none) */
+} zc_serve_opts;
+
+/* Run the loop until every request completed; results[i] for reqs[i].
+ * Blocks the calling thread (host clock: steady, seconds).  A request whose
+ * scratch exceeds the whole pool fails alone with ZC_ERR_OOM in its result.
+ * Returns the first failure status (results are filled in either case). */
+zc_status zc_serve(zc_ctx* ctx, const zc_request* reqs, uint32_t count, const zc_serve_opts* opts,
+                   zc_result* results);
+
 /* ------------------------------------------------------------ tuning --
  * Launch parameters of the kernels, per form and size.  The paper fixes the
  * arithmetic, not the launch shape; every value gives byte-identical proofs
@@ -229,6 +278,11 @@ zc_status zc_prove_sumcheck_static(const zc_params* params, const void* const* c
  *   ZC_TUNE_SC_TAIL_LOG  SumCheck: the single-CTA tail takes over once a round
  *                        has at most 2^value pairs; 0..24, default 8 (Plonk
  *                        gate) or 6 (product gate).
+ *   ZC_TUNE_SC_SMALL_LOG SumCheck, Plonk gate: rounds 2.. with at most 2^value
+ *                        pairs spread each pair over 16 threads; 1..24,
+ *                        default 12.
+ *   ZC_TUNE_SC_MINB      SumCheck, Plonk gate: resident CTAs per SM the large
+ *                        round kernels are compiled for; 1 or 2, default 1.
  *   ZC_TUNE_NTT_TILE_LOG NTT: elements per shared-memory pass tile, 2^value;
  *                        10, 11 or 12, default 11.
  *   ZC_TUNE_NTT_MINB     NTT: resident CTAs per SM the 2^11 tile is compiled
@@ -241,7 +295,9 @@ typedef enum {
   ZC_TUNE_SC_GRID = 1,
   ZC_TUNE_SC_TAIL_LOG = 2,
   ZC_TUNE_NTT_TILE_LOG = 3,
-  ZC_TUNE_NTT_MINB = 4
+  ZC_TUNE_NTT_MINB = 4,
+  ZC_TUNE_SC_SMALL_LOG = 5,
+  ZC_TUNE_SC_MINB = 6
 } zc_tune_key;
 
 zc_status zc_tune_set(zc_ctx* ctx, zc_form form, uint32_t n, zc_tune_key key, int32_t value);

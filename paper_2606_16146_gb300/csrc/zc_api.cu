@@ -51,6 +51,10 @@ zc_status check_params(zc_ctx* ctx, const zc_params* p, zc_form form) {
 
 zc_status ensure_arena(zc_ctx* ctx, size_t bytes) {
   if (ctx->arena.cap >= bytes) return ZC_OK;
+  if (ctx->arena_borrowed) {
+    ctx->err = "scratch block smaller than the proof needs";
+    return ZC_ERR_OOM;
+  }
   if (ctx->budget && bytes > ctx->budget) {
     ctx->err = "scratch need exceeds the memory budget";
     return ZC_ERR_OOM;
@@ -630,6 +634,7 @@ void zc_destroy(zc_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   destroy_lanes(ctx);
+  destroy_serve_pool(ctx);
   if (ctx->arena.base) cudaFree(ctx->arena.base);
   for (auto& t : ctx->ntt_cache)
     if (t.mem) cudaFree(t.mem);
@@ -799,12 +804,16 @@ static bool tune_value_ok(zc_tune_key key, int32_t v) {
     case ZC_TUNE_SC_TAIL_LOG: return v >= 1 && v <= 24;
     case ZC_TUNE_NTT_TILE_LOG: return v >= 10 && v <= 12;
     case ZC_TUNE_NTT_MINB: return v == 1 || v == 2;
+    case ZC_TUNE_SC_SMALL_LOG: return v >= 1 && v <= 24;
+    case ZC_TUNE_SC_MINB: return v == 1 || v == 2;
   }
   return false;
 }
 
 static bool tune_form_ok(zc_form form, zc_tune_key key) {
-  if (form == ZC_FORM_SUMCHECK) return key == ZC_TUNE_SC_GRID || key == ZC_TUNE_SC_TAIL_LOG;
+  if (form == ZC_FORM_SUMCHECK)
+    return key == ZC_TUNE_SC_GRID || key == ZC_TUNE_SC_TAIL_LOG || key == ZC_TUNE_SC_SMALL_LOG ||
+           key == ZC_TUNE_SC_MINB;
   if (form == ZC_FORM_NTT) return key == ZC_TUNE_NTT_TILE_LOG || key == ZC_TUNE_NTT_MINB;
   return false;
 }

@@ -34,7 +34,7 @@ static double instance_cost(const zc_params& p, zc_form f) {
   return c * N / 2 * p.n + c * s * (N + N / 2 * p.n) + M * (p.n + lb) / 2 + M * p.d;
 }
 
-static zc_status make_lanes(zc_ctx* ctx, int K) {
+zc_status make_lanes(zc_ctx* ctx, int K) {
   while ((int)ctx->lanes.size() < K) {
     zc_ctx* L = new zc_ctx();
     L->device = ctx->device;
@@ -168,7 +168,7 @@ zc_status batch_enqueue(zc_ctx* ctx, uint32_t count, const zc_form* forms, const
 void destroy_lanes(zc_ctx* ctx) {
   for (size_t k = 0; k < ctx->lanes.size(); k++) {
     zc_ctx* L = ctx->lanes[k];
-    if (L->arena.base) cudaFree(L->arena.base);
+    if (L->arena.base && !L->arena_borrowed) cudaFree(L->arena.base);
     if (L->pinned) cudaFreeHost(L->pinned);
     for (int i = 0; i < 8; i++)
       if (L->ev[i]) cudaEventDestroy(L->ev[i]);

@@ -89,6 +89,7 @@ struct zc_ctx {
   zc::fr* dtabs = nullptr;        // per-degree tables (device)
   std::vector<zc::fr> htabs;      // host copy
   zc::Arena arena;               // per-call scratch
+  bool arena_borrowed = false;   // arena is a block of the serving pool (not freed here)
   void* pinned = nullptr;        // small pinned staging buffer
   size_t pinned_cap = 0;
   cudaEvent_t ev[8] = {};
@@ -101,10 +102,10 @@ struct zc_ctx {
   uint32_t cur_n = 0;            // n of the proof being enqueued (selects tuned launch shapes)
   // launch parameters set by zc_tune_set: [form - 1][n][key - 1], 0 = unset;
   // n = 0 holds the value for sizes without their own entry
-  int32_t tune[2][zc::kMaxN + 1][4] = {};
+  int32_t tune[2][zc::kMaxN + 1][6] = {};
   int32_t tuned(zc_form form, uint32_t n, zc_tune_key key) const {
     const int f = (int)form - 1, k = (int)key - 1;
-    if (f < 0 || f > 1 || k < 0 || k > 3) return 0;
+    if (f < 0 || f > 1 || k < 0 || k > 5) return 0;
     if (n <= (uint32_t)zc::kMaxN && tune[f][n][k]) return tune[f][n][k];
     return tune[f][0][k];
   }
@@ -131,6 +132,9 @@ struct zc_ctx {
   std::vector<cudaStream_t> lane_streams;
   std::vector<cudaEvent_t> lane_join;
   cudaEvent_t fork_ev = nullptr;
+  // serving: one device pool that in-flight proofs take their scratch from
+  void* serve_pool = nullptr;
+  size_t serve_pool_cap = 0;
 };
 
 namespace zc {
@@ -178,7 +182,10 @@ size_t sumcheck_scratch_bytes(const zc_ctx* ctx, const zc_params* p);
 size_t ntt_scratch_bytes(const zc_params* p, int sm_count, bool q_direct);
 // allocation-time set-up of the NTT form for one size (tables, attributes)
 zc_status ntt_prepare(zc_ctx* ctx, const zc_params* p, cudaStream_t st);
+// batch/serving lanes: child contexts with their own stream and scratch
+zc_status make_lanes(zc_ctx* ctx, int K);
 void destroy_lanes(zc_ctx* ctx);
+void destroy_serve_pool(zc_ctx* ctx);
 
 // ------------------------------------------------------------ device helpers
 #if defined(__CUDACC__)

@@ -746,8 +746,9 @@ size_t ntt_scratch_bytes(const zc_params* p, int sm_count, bool q_direct) {
   const uint32_t nlo = 1u << hbits, nhi = 1u << (n - hbits);
   const uint32_t nblk_open = 2 * (uint32_t)sm_count;
   const size_t psize = 20 + 32 + 32 * ((size_t)c + 1);
-  size_t need = 2 * align_up(sizeof(fr) * N, 256) * c + align_up(sizeof(fr) * M, 256);
-  if (!q_direct) need += align_up(sizeof(fr) * M, 256);
+  size_t need = 2 * align_up(sizeof(fr) * N, 256) * c;  // coefficients + slice buffer
+  need += align_up(sizeof(fr) * M, 256);                  // qhat
+  if (!q_direct) need += align_up(sizeof(fr) * M, 256);   // q
   need += align_up(sizeof(fr) * s * (nlo + nhi), 256) + align_up(sizeof(fr) * s, 256);
   need += align_up(sizeof(fr) * (c + 1) * nblk_open, 256) + align_up(sizeof(fr) * 32, 256);
   need += align_up(sizeof(NttState), 256) + align_up(psize, 256) + align_up(32 * (size_t)(c + 1), 256);
@@ -794,15 +795,7 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
   const uint32_t nlo = 1u << hbits, nhi = 1u << (n - hbits);
   const uint32_t nblk_open = 2 * (uint32_t)ctx->sm_count;
   const bool q_direct = q_out && q_on_dev;
-  size_t need = 0;
-  need += 2 * align_up(sizeof(fr) * N, 256) * c;    // coefficients + slice buffer
-  need += align_up(sizeof(fr) * M, 256);            // qhat
-  if (!q_direct) need += align_up(sizeof(fr) * M, 256);
-  need += align_up(sizeof(fr) * s * (nlo + nhi), 256) + align_up(sizeof(fr) * s, 256);
-  need += align_up(sizeof(fr) * (c + 1) * nblk_open, 256) + align_up(sizeof(fr) * 32, 256);
-  need += align_up(sizeof(NttState), 256) + align_up(psize, 256) + align_up(32 * (size_t)(c + 1), 256);
-  need += root_scratch_bytes(c, N) + root_scratch_bytes(1, M) + 8192;
-  zc_status s1 = ensure_arena(ctx, need);
+  zc_status s1 = ensure_arena(ctx, ntt_scratch_bytes(p, ctx->sm_count, q_direct));
   if (s1 != ZC_OK) return s1;
   Arena& ar = ctx->arena;
   ar.reset();

@@ -39,9 +39,13 @@
 
 namespace zc {
 
-constexpr uint64_t kTailPairsPlonk = 256;
+constexpr uint64_t kTailPairsPlonk = 32;
 constexpr uint64_t kTailPairsProd = 64;
+constexpr uint64_t kSmallPairsPlonk = 4096;  // Plonk rounds with at most this many pairs: k_sc_plonk_small
 constexpr int kPP = 4;  // product gate: points per thread
+constexpr int kSmallPB = 16;  // pairs per chunk of k_sc_plonk_small (256 threads)
+constexpr int kTailPB = 32;   // pairs per chunk in the tail (512 threads)
+constexpr int kTailThreads = 16 * kTailPB;
 
 // ------------------------------------------------------------------ args --
 
@@ -82,7 +86,9 @@ struct ScRoundArgs {
   int n, c;
   uint32_t gate, d;
   int G;               // product gate: threads per pair
-  uint32_t nwork;      // CTAs that evaluate pairs (round 1 adds one for the inverses)
+  uint32_t nwork;      // CTAs that evaluate pairs (round 1 may add one for the inverses)
+  uint32_t full;       // evaluate H at all of 0..d-1 (no point derived from the claim)
+  uint32_t next_derives;  // the next round derives a point: keep the claim
   ScState* st;
   fr* partials;
   uint8_t* proof;
@@ -161,66 +167,71 @@ struct ChalSmem {
   fr H[kMaxPts + 1];   // H(0..d+1)
   fr Hinf;
   fr tmp[2][kMaxPts];
+  fr cl[kMaxPts];      // c_i l_i(t)
   fr alpha;
   uint32_t msg[8 + 8 * kMaxPts];
 };
 
-// Finish round `i` from the sums Hc (shared memory, np values): derive the
-// missing point, extrapolate, G_i(t) = c_i l_i(t) H_i(t) into the proof,
-// absorb, squeeze alpha_i, next claim H_i(alpha_i).  All threads of the CTA.
+// Finish round `i` from the sums Hc (shared memory, np values): either all
+// of H(0..d-1) and H(inf) (np = d + 1) or H(p0), H(2..d-1), H(inf) (np = d,
+// the other of H(0), H(1) derived from the claim); extrapolate, G_i(t) =
+// c_i l_i(t) H_i(t) into the proof, absorb, squeeze alpha_i, update c_i and,
+// when the next round derives a point, the claim H_i(alpha_i).  All threads
+// of the CTA (at least 128).  Independent steps run on different warps so the
+// serial chain is eight multiplications and the hash.
 __device__ void sc_challenge(ChalSmem& S, int np, int d, int i, ScState* st, uint8_t* proof,
-                             const DevConst* C, const fr* tabs) {
-  const bool first = i == 0;
+                             const DevConst* C, const fr* tabs, bool need_claim) {
+  const bool full = np == d + 1;
   const fr r = st->r[i];
-  if (threadIdx.x == 0) {
+  const fr two_r_m1 = fr_sub(fr_add(r, r), C->one);
+  const fr one_m_r = fr_sub(C->one, r);
+  const int t = threadIdx.x;
+  const int hs = (d + 2 + 31) / 32 * 32;  // first thread of the warp after the c_i l_i(t) threads
+  if (t < d + 2) {  // c_i l_i(t)
+    S.cl[t] = fr_mul(st->ci, fr_add(one_m_r, fr_mul(C->small[t], two_r_m1)));
+  } else if (t == hs) {  // another warp: H(0..d-1), H(inf)
     S.Hinf = S.Hc[np - 1];
-    if (first) {
-      for (int t = 0; t < d; t++) S.H[t] = S.Hc[t];
+    if (full) {
+      for (int q = 0; q < d; q++) S.H[q] = S.Hc[q];
     } else {
       const uint32_t p0 = st->p0[i];
-      for (int t = 2; t < d; t++) S.H[t] = S.Hc[t - 1];
+      for (int q = 2; q < d; q++) S.H[q] = S.Hc[q - 1];
       const fr claim = st->claim;  // level 0
       if (p0 == 0) {
         S.H[0] = S.Hc[0];
-        S.H[1] = fr_mul(fr_sub(claim, fr_mul(fr_sub(C->one, r), S.H[0])), st->rinv[i]);
+        S.H[1] = fr_mul(fr_sub(claim, fr_mul(one_m_r, S.H[0])), st->rinv[i]);
       } else {
         S.H[1] = S.Hc[0];
         S.H[0] = fr_mul(fr_sub(claim, fr_mul(r, S.H[1])), st->r1inv[i]);
       }
     }
   }
+  if (t < 8) S.msg[t] = st->S[t];
   __syncthreads();
   // extrapolate H(d), H(d+1) from H(0..d-1) and the leading coefficient
   const fr* ext = tabs + C->ext_base[d];
-  if (threadIdx.x < (unsigned)d) {
-    const int s = threadIdx.x;
-    S.tmp[0][s] = fr_mul(S.H[s], ext[2 + s]);
-    S.tmp[1][s] = fr_mul(S.H[s], ext[2 + d + s]);
+  if (t < 2 * d) {
+    const int which = t / d, q = t % d;
+    S.tmp[which][q] = fr_mul(S.H[q], ext[2 + which * d + q]);
   }
   __syncthreads();
-  if (threadIdx.x < 2) {
-    const int t = threadIdx.x;
-    fr s = fr_mul(S.Hinf, ext[t]);
-    for (int q = 0; q < d; q++) s = fr_add(s, S.tmp[t][q]);
-    S.H[d + t] = s;
+  if (t < 2) {
+    fr v = fr_mul(S.Hinf, ext[t]);
+    for (int q = 0; q < d; q++) v = fr_add(v, S.tmp[t][q]);
+    S.H[d + t] = v;
   }
   __syncthreads();
   // G(t) = c_i l_i(t) H(t), level 0 = canonical
-  const fr two_r_m1 = fr_sub(fr_add(r, r), C->one);
-  const fr one_m_r = fr_sub(C->one, r);
-  if (threadIdx.x < (unsigned)(d + 2)) {
-    const int t = threadIdx.x;
-    const fr l = fr_add(one_m_r, fr_mul(C->small[t], two_r_m1));
-    const fr g = fr_mul(S.H[t], fr_mul(st->ci, l));
+  if (t < d + 2) {
+    const fr g = fr_mul(S.H[t], S.cl[t]);
     uint8_t* pout = proof + 16 + 32 * ((size_t)i * (d + 2) + t);
     for (int q = 0; q < 8; q++) {
       S.msg[8 + 8 * t + q] = sha_bswap(g.v[q]);
       for (int b = 0; b < 4; b++) pout[4 * q + b] = (uint8_t)(g.v[q] >> (8 * b));
     }
   }
-  if (threadIdx.x < 8) S.msg[threadIdx.x] = st->S[threadIdx.x];
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (t == 0) {
     uint32_t Sn[8];
     sha256_words(S.msg, 8 + 8 * (d + 2), Sn);
     const fr a = fr_mul(tr_squeeze(Sn), C->r2);
@@ -229,23 +240,23 @@ __device__ void sc_challenge(ChalSmem& S, int np, int d, int i, ScState* st, uin
     S.alpha = a;
   }
   __syncthreads();
-  // next claim H_i(alpha) by Lagrange over the nodes 0..d
   const fr a = S.alpha;
-  const fr* dinv = tabs + C->lag_base[d];
-  if (threadIdx.x <= (unsigned)d) {
-    const int s = threadIdx.x;
-    fr num = C->one;
-    for (int q = 0; q <= d; q++)
-      if (q != s) num = fr_mul(num, fr_sub(a, C->small[q]));
-    S.tmp[0][s] = fr_mul(fr_mul(S.H[s], num), dinv[s]);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    fr s = fr_zero();
-    for (int q = 0; q <= d; q++) s = fr_add(s, S.tmp[0][q]);
-    st->claim = s;
-    const fr l = fr_add(one_m_r, fr_mul(a, two_r_m1));
-    st->ci = fr_mul(st->ci, l);
+  if (t == hs) st->ci = fr_mul(st->ci, fr_add(one_m_r, fr_mul(a, two_r_m1)));
+  if (need_claim) {
+    // next claim H_i(alpha) by Lagrange over the nodes 0..d
+    const fr* dinv = tabs + C->lag_base[d];
+    if (t <= d) {
+      fr num = C->one;
+      for (int q = 0; q <= d; q++)
+        if (q != t) num = fr_mul(num, fr_sub(a, C->small[q]));
+      S.tmp[0][t] = fr_mul(fr_mul(S.H[t], num), dinv[t]);
+    }
+    __syncthreads();
+    if (t == 0) {
+      fr v = fr_zero();
+      for (int q = 0; q <= d; q++) v = fr_add(v, S.tmp[0][q]);
+      st->claim = v;
+    }
   }
   __syncthreads();
 }
@@ -270,7 +281,7 @@ __device__ void sc_finish_round(const ScRoundArgs& A, int np) {
     if (lane == 0) S.Hc[p] = s;
   }
   __syncthreads();
-  sc_challenge(S, np, (int)A.d, A.round, A.st, A.proof, A.C, A.tabs);
+  sc_challenge(S, np, (int)A.d, A.round, A.st, A.proof, A.C, A.tabs, A.next_derives != 0);
 }
 
 // ------------------------------------------------------- per-pair work --
@@ -344,9 +355,9 @@ __device__ __forceinline__ void plonk_pair(const fr* const* src, fr* const* dst,
 
 // point index -> evaluation point (kInf for infinity)
 constexpr uint32_t kInf = 0xffffffffu;
-__device__ __forceinline__ uint32_t prod_point(int p, int np, bool first, uint32_t p0) {
+__device__ __forceinline__ uint32_t prod_point(int p, int np, bool full, uint32_t p0) {
   if (p == np - 1) return kInf;
-  if (first) return (uint32_t)p;         // 0, 1, ..., d-1
+  if (full) return (uint32_t)p;          // 0, 1, ..., d-1
   return p == 0 ? p0 : (uint32_t)p + 1;  // p0, 2, ..., d-1
 }
 
@@ -387,6 +398,101 @@ __device__ __forceinline__ void prod_pair(const ScRoundArgs& A, const fr* const*
 #pragma unroll
   for (int p = 0; p < kPP; p++)
     if (p < pcnt) acc[p] = fr_add(acc[p], fr_mul(prod[p], w));
+}
+
+// Plonk round i >= 2 on a chunk of PB pairs, the work of each pair spread
+// over 16 threads (blockDim.x == 16 PB) so that a round is four
+// multiplications deep:
+//   1. thread (column, half, pair): fold by alpha_{i-1}, store, keep in smem;
+//   2. thread (pair, item): qM b, qR b, qO c at each finite point, the slope
+//      product dqM db, and the eq weight E_hi E_lo;
+//   3. thread (pair, point): s = a (qL + qM b) + qR b + qO c + qC at a finite
+//      point, dqM db da at infinity, times the eq weight.
+// FULL: points 0, 1, 2, inf; otherwise p0, 2, inf.  Threads t < NPT PB add
+// their value for (pair t / NPT, point t % NPT) into acc.
+template <int PB>
+struct PlonkChunkSmem {
+  fr V[8][2][PB];  // folded lo / hi per column
+  fr U[PB][12];    // products and the eq weight
+};
+
+// column j of pair p at point pt: 0 -> lo, 1 -> hi, 2 -> 2 hi - lo, 3 -> slope
+template <int PB>
+__device__ __forceinline__ fr plonk_at(const PlonkChunkSmem<PB>& S, int j, int p, int pt) {
+  const fr lo = S.V[j][0][p], hi = S.V[j][1][p];
+  if (pt == 0) return lo;
+  if (pt == 1) return hi;
+  const fr dl = fr_sub(hi, lo);
+  return pt == 2 ? fr_add(hi, dl) : dl;
+}
+
+template <int PB, bool FULL, bool COHERENT>
+__device__ __forceinline__ void plonk_chunk(PlonkChunkSmem<PB>& S, const fr* const* src, fr* const* dst,
+                                            uint64_t h, uint64_t kbase, const fr& alpha, uint32_t p0,
+                                            const fr* ehi, const fr* elo, uint32_t mlo, fr& acc) {
+  constexpr int NPT = FULL ? 4 : 3, NF = NPT - 1, NITEM = 3 * NF + 2;
+  const int t = threadIdx.x;
+  auto point = [&](int f) { return FULL ? f : (f == 0 ? (int)p0 : 2); };  // finite point f
+  {
+    const int p = t % PB, half = (t / PB) & 1, j = t / (2 * PB);
+    const uint64_t e = kbase + p + (half ? h : 0);
+    if (kbase + p < h) {
+      const fr x0 = ldx<COHERENT>(src[j] + e), x1 = ldx<COHERENT>(src[j] + e + 2 * h);
+      const fr v = fr_add(x0, fr_mul(alpha, fr_sub(x1, x0)));
+      st_fr(dst[j] + e, v);
+      S.V[j][half][p] = v;
+    }
+  }
+  __syncthreads();
+  if (t < 16 * PB) {
+    const int p = t >> 4, q = t & 15;
+    const uint64_t k = kbase + p;
+    if (k < h && q < NITEM) {
+      fr u;
+      if (q == NITEM - 1) {
+        u = fr_mul(ldx<COHERENT>(ehi + (k >> mlo)), ldx<COHERENT>(elo + (k & ((1ull << mlo) - 1))));
+      } else if (q == NITEM - 2) {
+        u = fr_mul(plonk_at(S, 2, p, 3), plonk_at(S, 6, p, 3));  // dqM db
+      } else {
+        const int pt = point(q / 3), term = q % 3;
+        const int ja = term == 0 ? 2 : (term == 1 ? 1 : 3);  // qM, qR, qO
+        const int jb = term == 2 ? 7 : 6;                    // b, b, c
+        u = fr_mul(plonk_at(S, ja, p, pt), plonk_at(S, jb, p, pt));
+      }
+      S.U[p][q] = u;
+    }
+  }
+  __syncthreads();
+  if (t < NPT * PB) {
+    const int p = t / NPT, f = t % NPT;
+    if (kbase + p < h) {
+      fr v;
+      if (f < NF) {
+        const int pt = point(f);
+        v = fr_mul(plonk_at(S, 5, p, pt), fr_add(plonk_at(S, 0, p, pt), S.U[p][3 * f]));
+        v = fr_add(v, fr_add(fr_add(S.U[p][3 * f + 1], S.U[p][3 * f + 2]), plonk_at(S, 4, p, pt)));
+      } else {
+        v = fr_mul(S.U[p][NITEM - 2], plonk_at(S, 5, p, 3));
+      }
+      acc = fr_add(acc, fr_mul(v, S.U[p][NITEM - 1]));
+    }
+  }
+  __syncthreads();
+}
+
+// Sum the per-thread values of plonk_chunk over pairs: out[q] for q < NPT.
+template <int PB, int NPT>
+__device__ __forceinline__ void plonk_chunk_reduce(const fr& acc, fr* out) {
+  __shared__ fr R[NPT * PB];
+  const int t = threadIdx.x;
+  if (t < NPT * PB) R[t] = acc;
+  __syncthreads();
+  if (t < NPT) {
+    fr s = fr_zero();
+    for (int p = 0; p < PB; p++) s = fr_add(s, R[NPT * p + t]);
+    out[t] = s;
+  }
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------- kernels --
@@ -446,8 +552,8 @@ __device__ void sc_inverses(ScState* st, int n, const DevConst* C) {
 // converts a, b, c, evaluates t = 0, 1, 2, inf; the extra last CTA computes
 // the inverses used from round 2 on).  Otherwise: folds by alpha_{i-1} and
 // evaluates t = p0, 2, inf.  The last CTA to finish runs the challenge.
-template <bool FIRST>
-__global__ void __launch_bounds__(256, 1) k_sc_plonk_round(ScRoundArgs A) {
+template <bool FIRST, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_sc_plonk_round(ScRoundArgs A) {
   constexpr int NP = FIRST ? 4 : 3;
   if (FIRST && blockIdx.x == A.nwork) {
     sc_inverses(A.st, A.n, A.C);
@@ -477,6 +583,25 @@ __global__ void __launch_bounds__(256, 1) k_sc_plonk_round(ScRoundArgs A) {
   sc_finish_round(A, NP);
 }
 
+// One small Plonk round (i >= 2, few pairs): chunks of kSmallPB pairs, each
+// pair's work spread over 16 threads (plonk_chunk), all of H(0), H(1), H(2),
+// H(inf) evaluated (no inverse needed).  The last CTA to finish runs the
+// challenge.
+__global__ void __launch_bounds__(16 * kSmallPB) k_sc_plonk_small(ScRoundArgs A) {
+  __shared__ PlonkChunkSmem<kSmallPB> S;
+  __shared__ fr part[4];
+  const int i = A.round;
+  const fr alpha = A.st->alpha[i - 1];
+  fr acc = fr_zero();
+  for (uint64_t kb = (uint64_t)blockIdx.x * kSmallPB; kb < A.h; kb += (uint64_t)A.nwork * kSmallPB)
+    plonk_chunk<kSmallPB, true, false>(S, A.src, A.dst, A.h, kb, alpha, 0u, A.E + A.eq_hi[i],
+                                       A.E + A.eq_lo[i], A.m_lo[i], acc);
+  plonk_chunk_reduce<kSmallPB, 4>(acc, part);
+  if (threadIdx.x < 4) st_fr(A.partials + (size_t)blockIdx.x * 4 + threadIdx.x, part[threadIdx.x]);
+  __syncthreads();
+  sc_finish_round(A, 4);
+}
+
 // MLE update by alpha_{round-1}: dst[j][k] = src[j][k] + alpha (src[j][k+h] - src[j][k])
 __global__ void __launch_bounds__(256) k_sc_fold(ScFoldArgs A) {
   const fr alpha = A.st->alpha[A.round - 1];
@@ -490,8 +615,34 @@ __global__ void __launch_bounds__(256) k_sc_fold(ScFoldArgs A) {
   }
 }
 
-// Product-gate evaluation of one large round (columns already folded): G
-// threads share a pair, each evaluating kPP consecutive points.
+// Product gate f = q w1 .. w_{d-1} - o at point t (kInf: leading
+// coefficient) for pair k, times the eq weight w.  Tables at level 0; the
+// product of d factors lands on level 1 - d, o is brought there by kcomp,
+// and the eq weight (level d) returns the sum to level 0.
+template <bool COHERENT>
+__device__ __forceinline__ fr prod_point_value(const ScRoundArgs& A, const fr* const* col, uint64_t k,
+                                               uint64_t h, uint32_t t, bool first, const fr& w,
+                                               uint32_t& bad) {
+  const int d = (int)A.d;
+  fr prod;
+  for (int j = 0; j < d; j++) {
+    const fr lo = ldx<COHERENT>(col[j] + k), hi = ldx<COHERENT>(col[j] + k + h);
+    if (first) bad |= (!fr_is_canonical(lo)) | (!fr_is_canonical(hi));
+    const fr dl = fr_sub(hi, lo);
+    const fr x = t == kInf ? dl : (t == 0 ? lo : (t == 1 ? hi : fr_add(lo, fr_mul_small(dl, t))));
+    prod = j == 0 ? x : fr_mul(prod, x);
+  }
+  if (t != kInf) {  // o enters at level 0; infinity has no o term
+    const fr lo = ldx<COHERENT>(col[d] + k), hi = ldx<COHERENT>(col[d] + k + h);
+    if (first) bad |= (!fr_is_canonical(lo)) | (!fr_is_canonical(hi));
+    const fr x = t == 0 ? lo : (t == 1 ? hi : fr_add(lo, fr_mul_small(fr_sub(hi, lo), t)));
+    prod = fr_sub(prod, fr_mul(x, A.kcomp));
+  }
+  return fr_mul(prod, w);
+}
+
+// Product-gate evaluation of one large round (columns already folded): one
+// thread per (pair, point), floor(256 / np) pairs per CTA in flight.
 __global__ void __launch_bounds__(256) k_sc_prod_round(ScRoundArgs A) {
   const int i = A.round;
   const bool first = i == 0;
@@ -499,65 +650,48 @@ __global__ void __launch_bounds__(256) k_sc_prod_round(ScRoundArgs A) {
     sc_inverses(A.st, A.n, A.C);
     return;
   }
-  const int G = A.G, d = (int)A.d;
-  const int np = first ? d + 1 : d;
-  const uint32_t p0 = first ? 0u : A.st->p0[i];
-  const int g = threadIdx.x % G;
-  const uint64_t slot = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-  const uint64_t nslots = (uint64_t)A.nwork * blockDim.x / G;
-  const int pbeg = g * kPP;
-  const int pcnt = max(0, min(kPP, np - pbeg));
+  const int d = (int)A.d;
+  const bool full = first || A.full;
+  const int np = full ? d + 1 : d;
+  const uint32_t p0 = full ? 0u : A.st->p0[i];
+  const int spb = (int)blockDim.x / np;
+  const int slot = (int)threadIdx.x / np, pi = (int)threadIdx.x % np;
   const uint32_t mlo = A.m_lo[i];
   const fr* ehi = A.E + A.eq_hi[i];
   const fr* elo = A.E + A.eq_lo[i];
   uint32_t bad = 0;
-  fr acc[kPP];
-  uint32_t tpt[kPP];
-#pragma unroll
-  for (int p = 0; p < kPP; p++) {
-    acc[p] = fr_zero();
-    tpt[p] = p < pcnt ? prod_point(pbeg + p, np, first, p0) : 0u;
-  }
-  for (uint64_t k = slot; k < A.h && pcnt > 0; k += nslots) {
-    const fr w = fr_mul(ld_fr(ehi + (k >> mlo)), ld_fr(elo + (k & ((1ull << mlo) - 1))));
-    prod_pair<false>(A, A.src, k, A.h, pcnt, tpt, first, w, acc, bad);
+  fr acc = fr_zero();
+  if (slot < spb) {
+    const uint32_t t = prod_point(pi, np, full, p0);
+    for (uint64_t k = (uint64_t)blockIdx.x * spb + slot; k < A.h; k += (uint64_t)A.nwork * spb) {
+      const fr w = fr_mul(ld_fr(ehi + (k >> mlo)), ld_fr(elo + (k & ((1ull << mlo) - 1))));
+      acc = fr_add(acc, prod_point_value<false>(A, A.src, k, A.h, t, first && pi == 0, w, bad));
+    }
   }
   if (bad) atomicOr(&A.st->err, 1u);
-  // reduce over the threads of the CTA that share g
-  __shared__ fr red[256 / 32][32][kPP];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int p = 0; p < kPP; p++) {
-    fr s = acc[p];
-    for (int off = 16; off >= G; off >>= 1) s = fr_add(s, shfl_down_fr(s, off));
-    if (lane < G) red[warp][lane][p] = s;
-  }
+  __shared__ fr red[256];
+  red[threadIdx.x] = acc;
   __syncthreads();
-  for (int q = threadIdx.x; q < G * kPP; q += blockDim.x) {
-    const int gg = q / kPP, p = q % kPP, pg = gg * kPP + p;
-    if (pg >= np) continue;
+  if ((int)threadIdx.x < np) {
     fr s = fr_zero();
-    for (int w2 = 0; w2 < nw; w2++) s = fr_add(s, red[w2][gg][p]);
-    st_fr(A.partials + (size_t)blockIdx.x * np + pg, s);
+    for (int q = 0; q < spb; q++) s = fr_add(s, red[q * np + threadIdx.x]);
+    st_fr(A.partials + (size_t)blockIdx.x * np + threadIdx.x, s);
   }
   __syncthreads();
   sc_finish_round(A, np);
 }
 
 // All rounds from A.round on, their challenges and the final values, in one
-// CTA of 256 threads.  Tables are read with coherent loads: they are
-// rewritten between rounds inside this launch.
-__global__ void __launch_bounds__(256, 1) k_sc_tail(ScRoundArgs A) {
+// CTA of kTailThreads threads.  Tables are read with coherent loads: they
+// are rewritten between rounds inside this launch.
+template <bool PLONK>
+__global__ void __launch_bounds__(PLONK ? kTailThreads : 256, 1) k_sc_tail(ScRoundArgs A) {
   __shared__ ChalSmem S;
   __shared__ fr pg[kMaxPts];
   const DevConst* C = A.C;
   const int n = A.n, c = A.c, d = (int)A.d;
-  const bool plonk = A.gate == ZC_GATE_PLONK;
+  constexpr bool plonk = PLONK;
   const uint64_t N = 1ull << n;
-  if (A.round == 0) {
-    sc_inverses(A.st, n, C);
-    __syncthreads();
-  }
   uint32_t bad = 0;
   // source of round i's pairs: the input for round 0, then the folded tables
   const fr* cur[kMaxCols];
@@ -568,7 +702,7 @@ __global__ void __launch_bounds__(256, 1) k_sc_tail(ScRoundArgs A) {
     const fr* ehi = A.E + A.eq_hi[i];
     const fr* elo = A.E + A.eq_lo[i];
     int np;
-    if (plonk) {
+    if constexpr (PLONK) {
       if (i == 0) {
         np = 4;
         fr acc[4] = {fr_zero(), fr_zero(), fr_zero(), fr_zero()};
@@ -578,15 +712,13 @@ __global__ void __launch_bounds__(256, 1) k_sc_tail(ScRoundArgs A) {
               fr_mul(ld_fr_cg(ehi + (k >> mlo)), ld_fr_cg(elo + (k & ((1ull << mlo) - 1)))), acc, bad);
         block_sum<4>(acc, pg);
       } else {
-        np = 3;
-        fr acc[3] = {fr_zero(), fr_zero(), fr_zero()};
+        np = 4;
+        fr acc = fr_zero();
         const fr alpha = A.st->alpha[i - 1];
-        const uint32_t p0 = A.st->p0[i];
-        for (uint64_t k = threadIdx.x; k < h; k += blockDim.x)
-          plonk_pair<false, true>(
-              cur, A.dst, C, k, h, alpha, p0,
-              fr_mul(ld_fr_cg(ehi + (k >> mlo)), ld_fr_cg(elo + (k & ((1ull << mlo) - 1)))), acc, bad);
-        block_sum<3>(acc, pg);
+        __shared__ PlonkChunkSmem<kTailPB> PS;
+        for (uint64_t kb = 0; kb < h; kb += kTailPB)
+          plonk_chunk<kTailPB, true, true>(PS, cur, A.dst, h, kb, alpha, 0u, ehi, elo, mlo, acc);
+        plonk_chunk_reduce<kTailPB, 4>(acc, pg);
       }
       // the converted wires live in dst after round 1, everything after round 2
       for (int j = (i == 0 ? 5 : 0); j < c; j++) cur[j] = A.dst[j];
@@ -602,9 +734,9 @@ __global__ void __launch_bounds__(256, 1) k_sc_tail(ScRoundArgs A) {
         __syncthreads();
         for (int j = 0; j < c; j++) cur[j] = A.dst[j];
       }
+      // every tail round evaluates all of 0..d-1 and infinity (no derived point)
       const bool first = i == 0;
-      np = first ? d + 1 : d;
-      const uint32_t p0 = first ? 0u : A.st->p0[i];
+      np = d + 1;
       const int G = A.G;
       const int g = threadIdx.x % G;
       const uint64_t nslots = blockDim.x / G;
@@ -614,7 +746,7 @@ __global__ void __launch_bounds__(256, 1) k_sc_tail(ScRoundArgs A) {
 #pragma unroll
       for (int p = 0; p < kPP; p++) {
         acc[p] = fr_zero();
-        tpt[p] = p < pcnt ? prod_point(pbeg + p, np, first, p0) : 0u;
+        tpt[p] = p < pcnt ? prod_point(pbeg + p, np, true, 0u) : 0u;
       }
       for (uint64_t k = threadIdx.x / G; k < h && pcnt > 0; k += nslots) {
         const fr w = fr_mul(ld_fr_cg(ehi + (k >> mlo)), ld_fr_cg(elo + (k & ((1ull << mlo) - 1))));
@@ -628,7 +760,7 @@ __global__ void __launch_bounds__(256, 1) k_sc_tail(ScRoundArgs A) {
     }
     for (int p = threadIdx.x; p < np; p += blockDim.x) S.Hc[p] = pg[p];
     __syncthreads();
-    sc_challenge(S, np, d, i, A.st, A.proof, C, A.tabs);
+    sc_challenge(S, np, d, i, A.st, A.proof, C, A.tabs, false);
   }
   if (bad) atomicOr(&A.st->err, 1u);
   __syncthreads();
@@ -674,14 +806,16 @@ struct ScBuffers {
 
 struct ScPlan {
   int c, G, grid_plonk, grid_prod, npmax;
-  uint64_t tail_pairs;
+  uint64_t tail_pairs, small_pairs;
+  int minb;  // Plonk round kernels: resident CTAs per SM they are compiled for
   uint32_t eq_total, eq_hi[kMaxN], eq_lo[kMaxN], mlo[kMaxN];
   EqTask tasks[2 * kMaxN];
 };
 
 // grid: most CTAs per round kernel (0: two per SM); tail_log: the tail takes
 // over at 2^tail_log pairs (0: the gate's default).
-static ScPlan sc_plan(const zc_params* p, int SMs, int grid = 0, int tail_log = 0) {
+static ScPlan sc_plan(const zc_params* p, int SMs, int grid = 0, int tail_log = 0, int small_log = 0,
+                      int minb = 0) {
   ScPlan P{};
   const uint32_t n = p->n, d = p->d;
   const bool plonk = p->gate == ZC_GATE_PLONK;
@@ -691,6 +825,8 @@ static ScPlan sc_plan(const zc_params* p, int SMs, int grid = 0, int tail_log = 
   P.grid_plonk = grid > 0 ? grid : std::max(8, 2 * SMs / 8 * 8);
   P.grid_prod = grid > 0 ? grid : 2 * SMs;
   P.tail_pairs = tail_log > 0 ? 1ull << tail_log : (plonk ? kTailPairsPlonk : kTailPairsProd);
+  P.small_pairs = small_log > 0 ? 1ull << small_log : kSmallPairsPlonk;
+  P.minb = minb == 2 ? 2 : 1;
   P.npmax = (int)d + 1;
   for (uint32_t i = 0; i < n; i++) {
     uint32_t mlo, mhi;
@@ -775,22 +911,36 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
   const fr* cur[kMaxCols];
   for (int j = 0; j < c; j++) cur[j] = src[j];
   uint32_t i = 0;
+  // Rounds i >= 2 with more than small_pairs pairs take one of H(0), H(1)
+  // from the claim, which needs 1/r_i and 1/(1 - r_i): an extra CTA of round
+  // 1 computes them, only when such a round exists.
+  const bool need_inv = (N >> 2) > std::max(P.small_pairs, tail_pairs);
+  const uint32_t inv_cta = need_inv ? 1u : 0u;
   for (; i < n; i++) {
     const uint64_t h = N >> (i + 1);
     if (h <= tail_pairs) break;
     R.round = (int)i;
     R.h = h;
+    R.full = (i == 0 || h <= P.small_pairs) ? 1u : 0u;
+    R.next_derives = (h / 2 > P.small_pairs && h / 2 > tail_pairs) ? 1u : 0u;
     for (int j = 0; j < c; j++) {
       R.src[j] = cur[j];
       R.dst[j] = B.tab[j];
     }
-    if (plonk) {
+    if (plonk && i > 0 && h <= P.small_pairs) {
+      R.nwork = (uint32_t)std::min<uint64_t>((h + kSmallPB - 1) / kSmallPB, (uint64_t)P.grid_plonk);
+      k_sc_plonk_small<<<R.nwork, 16 * kSmallPB, 0, st>>>(R);
+      for (int j = 0; j < 8; j++) cur[j] = B.tab[j];
+      *launches += 1;
+    } else if (plonk) {
       R.nwork = (uint32_t)std::min<uint64_t>((h + 255) / 256, (uint64_t)P.grid_plonk);
       if (i == 0) {
-        k_sc_plonk_round<true><<<R.nwork + 1, 256, 0, st>>>(R);
+        if (P.minb == 2) k_sc_plonk_round<true, 2><<<R.nwork + inv_cta, 256, 0, st>>>(R);
+        else k_sc_plonk_round<true, 1><<<R.nwork + inv_cta, 256, 0, st>>>(R);
         for (int j = 5; j < 8; j++) cur[j] = B.tab[j];
       } else {
-        k_sc_plonk_round<false><<<R.nwork, 256, 0, st>>>(R);
+        if (P.minb == 2) k_sc_plonk_round<false, 2><<<R.nwork, 256, 0, st>>>(R);
+        else k_sc_plonk_round<false, 1><<<R.nwork, 256, 0, st>>>(R);
         for (int j = 0; j < 8; j++) cur[j] = B.tab[j];
       }
       *launches += 1;
@@ -812,9 +962,9 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
         for (int j = 0; j < c; j++) R.src[j] = cur[j];
         *launches += 1;
       }
-      const uint64_t slots_per_blk = 256 / P.G;
+      const uint64_t slots_per_blk = 256 / (R.full ? d + 1 : d);
       R.nwork = (uint32_t)std::min<uint64_t>((h + slots_per_blk - 1) / slots_per_blk, (uint64_t)P.grid_prod);
-      k_sc_prod_round<<<R.nwork + (i == 0 ? 1 : 0), 256, 0, st>>>(R);
+      k_sc_prod_round<<<R.nwork + (i == 0 ? inv_cta : 0u), 256, 0, st>>>(R);
       *launches += 1;
     }
     if (i == 0 && ev) cudaEventRecord(ev[3], st);
@@ -827,14 +977,19 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
     R.dst[j] = B.tab[j];
   }
   R.nwork = 1;
-  k_sc_tail<<<1, 256, 0, st>>>(R);
+  if (plonk)
+    k_sc_tail<true><<<1, kTailThreads, 0, st>>>(R);
+  else
+    k_sc_tail<false><<<1, 256, 0, st>>>(R);
   *launches += 1;
   return cudaGetLastError() == cudaSuccess ? ZC_OK : ZC_ERR_CUDA;
 }
 
 size_t sumcheck_scratch_bytes(const zc_ctx* ctx, const zc_params* p) {
   const ScPlan P = sc_plan(p, ctx->sm_count, ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_GRID),
-                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_TAIL_LOG));
+                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_TAIL_LOG),
+                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_SMALL_LOG),
+                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_MINB));
   const uint64_t N = 1ull << p->n;
   const size_t psize = 16 + 32 * ((size_t)p->n * (p->d + 2) + P.c);
   return align_up(sizeof(fr) * N, 256) * P.c + align_up(sizeof(fr) * sc_partials_count(P), 256) +
@@ -847,15 +1002,13 @@ zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* col
                          bool proof_on_dev) {
   const uint32_t n = p->n, d = p->d;
   const ScPlan P = sc_plan(p, ctx->sm_count, ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_GRID),
-                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_TAIL_LOG));
+                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_TAIL_LOG),
+                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_SMALL_LOG),
+                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_MINB));
   const int c = P.c;
   const uint64_t N = 1ull << n;
   const size_t psize = 16 + 32 * ((size_t)n * (d + 2) + c);
-  size_t need = align_up(sizeof(fr) * N, 256) * c + align_up(sizeof(fr) * sc_partials_count(P), 256) +
-                align_up(sizeof(fr) * P.eq_total, 256) + align_up(sizeof(ScState), 256) +
-                align_up(psize, 256) + align_up(32 * (size_t)c, 256) + 4096;
-  if (!roots) need += root_scratch_bytes(c, N);
-  zc_status s = ensure_arena(ctx, need);
+  zc_status s = ensure_arena(ctx, sumcheck_scratch_bytes(ctx, p));
   if (s != ZC_OK) return s;
   Arena& ar = ctx->arena;
   ar.reset();

@@ -19,9 +19,12 @@ from . import build as _build
 ZC_OK = 0
 STATUS = {0: "ZC_OK", 1: "ZC_ERR_ARG", 2: "ZC_ERR_OOM", 3: "ZC_ERR_CUDA", 4: "ZC_ERR_TIMEOUT",
           5: "ZC_ERR_UNSUPPORTED", 6: "ZC_ERR_BUFFER_TOO_SMALL"}
+(ZC_ERR_ARG, ZC_ERR_OOM, ZC_ERR_CUDA, ZC_ERR_TIMEOUT, ZC_ERR_UNSUPPORTED,
+ ZC_ERR_BUFFER_TOO_SMALL) = 1, 2, 3, 4, 5, 6
 ZC_GATE_PLONK, ZC_GATE_PRODUCT = 1, 2
 ZC_FORM_SUMCHECK, ZC_FORM_NTT = 1, 2
 ZC_TUNE_SC_GRID, ZC_TUNE_SC_TAIL_LOG, ZC_TUNE_NTT_TILE_LOG, ZC_TUNE_NTT_MINB = 1, 2, 3, 4
+ZC_TUNE_SC_SMALL_LOG, ZC_TUNE_SC_MINB = 5, 6
 
 
 class ZCError(RuntimeError):
@@ -38,6 +41,22 @@ class zc_params(ctypes.Structure):
 class zc_setup_opts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("max_n", ctypes.c_uint32), ("max_d", ctypes.c_uint32),
                 ("mem_budget_bytes", ctypes.c_uint64)]
+
+
+class zc_request(ctypes.Structure):
+    _fields_ = [("arrival_s", ctypes.c_double), ("params", zc_params), ("form", ctypes.c_int),
+                ("cols", ctypes.c_void_p), ("proof", ctypes.c_void_p), ("q_out", ctypes.c_void_p)]
+
+
+class zc_result(ctypes.Structure):
+    _fields_ = [("admit_s", ctypes.c_double), ("done_s", ctypes.c_double),
+                ("scratch_bytes", ctypes.c_uint64), ("slot", ctypes.c_uint32),
+                ("waited_for_memory", ctypes.c_uint32), ("status", ctypes.c_int)]
+
+
+class zc_serve_opts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_uint32), ("hbm_budget_bytes", ctypes.c_uint64),
+                ("in_order", ctypes.c_uint32), ("timeout_s", ctypes.c_double)]
 
 
 _lib = None
@@ -68,6 +87,10 @@ def lib(path: str | None = None):
         L.zc_verify.restype = ctypes.c_int
         L.zc_roots.argtypes = [vp, P(zc_params), vp, ctypes.c_int, vp, vp]
         L.zc_roots.restype = ctypes.c_int
+        L.zc_scratch_bytes.argtypes = [vp, P(zc_params), ctypes.c_int, ctypes.c_int, P(sz)]
+        L.zc_scratch_bytes.restype = ctypes.c_int
+        L.zc_serve.argtypes = [vp, P(zc_request), ctypes.c_uint32, P(zc_serve_opts), P(zc_result)]
+        L.zc_serve.restype = ctypes.c_int
         L.zc_tune_set.argtypes = [vp, ctypes.c_int, ctypes.c_uint32, ctypes.c_int, ctypes.c_int32]
         L.zc_tune_set.restype = ctypes.c_int
         L.zc_tune_get.argtypes = [vp, ctypes.c_int, ctypes.c_uint32, ctypes.c_int, P(ctypes.c_int32)]
@@ -191,9 +214,10 @@ class Context:
         return out
 
     def prove_ntt(self, gate, n, d, cols, roots=None, stream=None, proof_out=None, q_out=None,
-                  log_blowup=0):
+                  log_blowup=0, want_q=True):
         """NTT-form proof.  Returns (proof, q); q_out may be a device tensor of
-        M*32 bytes, or None for a host array."""
+        M*32 bytes, or None for a host array; want_q=False keeps q on the
+        device only (returns (proof, None))."""
         p = zc_params(gate, n, d, log_blowup)
         P, on_dev = self._cols(cols)
         rb, rp = _roots_arg(roots)
@@ -201,11 +225,12 @@ class Context:
         lb = log_blowup or (d - 1).bit_length()
         M = 1 << (n + lb)
         out = proof_out if proof_out is not None else np.zeros(cap, np.uint8)
-        q = q_out if q_out is not None else np.zeros(M * 32, np.uint8)
-        q_dev = 1 if (_is_torch(q) and q.is_cuda) else 0
+        q = q_out if q_out is not None else (np.zeros(M * 32, np.uint8) if want_q else None)
+        q_dev = 1 if (q is None or (_is_torch(q) and q.is_cuda)) else 0
         ln = ctypes.c_size_t()
         st = lib().zc_prove_ntt(self.h, ctypes.byref(p), P.p, on_dev, rp, _stream_ptr(stream),
-                                _addr(out), cap, ctypes.byref(ln), _addr(q), q_dev)
+                                _addr(out), cap, ctypes.byref(ln), _addr(q) if q is not None else None,
+                                q_dev)
         self._check(st, "zc_prove_ntt")
         return out, q
 
@@ -251,6 +276,44 @@ class Context:
                                    ctypes.byref(h))
         self._check(st, "zc_batch_create")
         return BatchGraph(h, keep)
+
+    def scratch_bytes(self, gate, n, d, form, q_on_device=False, log_blowup=0) -> int:
+        """Device scratch one proof of this shape takes (its admission footprint)."""
+        out = ctypes.c_size_t()
+        p = zc_params(gate, n, d, log_blowup)
+        self._check(lib().zc_scratch_bytes(self.h, ctypes.byref(p), form, 1 if q_on_device else 0,
+                                           ctypes.byref(out)), "zc_scratch_bytes")
+        return int(out.value)
+
+    def serve(self, requests, slots=8, hbm_budget_bytes=180 << 30, in_order=False, timeout_s=0.0):
+        """Run the request loop.  requests: dicts with arrival_s, gate, n, d, form, cols
+        (device tensors), proof (device tensor) and optional q (device tensor).  Returns one
+        dict per request: admit_s, done_s, scratch_bytes, slot, waited_for_memory, status."""
+        cnt = len(requests)
+        R = (zc_request * max(1, cnt))()
+        keep = []
+        for i, r in enumerate(requests):
+            cp = _Ptrs(r["cols"])
+            keep.append(cp)
+            R[i].arrival_s = float(r["arrival_s"])
+            R[i].params = zc_params(r["gate"], r["n"], r["d"], r.get("log_blowup", 0))
+            R[i].form = int(r["form"])
+            R[i].cols = ctypes.cast(cp.arr, ctypes.c_void_p).value
+            R[i].proof = _addr(r["proof"])
+            R[i].q_out = _addr(r["q"]) if r.get("q") is not None else None
+        out = (zc_result * max(1, cnt))()
+        o = zc_serve_opts(slots, hbm_budget_bytes, 1 if in_order else 0, timeout_s)
+        st = lib().zc_serve(self.h, R, cnt, ctypes.byref(o), out)
+        res = [{"admit_s": out[i].admit_s, "done_s": out[i].done_s,
+                "scratch_bytes": int(out[i].scratch_bytes), "slot": int(out[i].slot),
+                "waited_for_memory": bool(out[i].waited_for_memory), "status": int(out[i].status)}
+               for i in range(cnt)]
+        if st != ZC_OK:
+            msg = lib().zc_last_error(self.h)
+            err = ZCError(st, f"zc_serve: {msg.decode() if msg else ''}")
+            err.results = res
+            raise err
+        return res
 
     def tune_set(self, form: int, n: int, key: int, value: int) -> None:
         """Launch parameter for proofs of (form, n); n = 0 for every size, value 0 clears."""
