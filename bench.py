@@ -37,7 +37,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2606_16146_gb300.costs import algorithmic_bytes, algorithmic_mulmods  # noqa: E402
+from paper_2606_16146_gb300.costs import algorithmic_bytes, algorithmic_mulmods, blowup, ncols  # noqa: E402
 
 METRIC = "ZeroCheck prove ms (SumCheck vs NTT) by n, degree; served p50/p99 ms"
 GATE, N_LOG, DEG = 1, 22, 3
@@ -454,6 +454,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="override n (profiling smaller cases)")
+    ap.add_argument("--d", type=int, default=None,
+                    help="override the degree (profiling; d != 3 or --gate 2 uses the product gate)")
+    ap.add_argument("--gate", type=int, default=1, choices=[1, 2])
     ap.add_argument("--form", default="both", choices=["both", "sumcheck", "ntt"],
                     help="restrict the step to one form (profiling); the bench line uses both")
     ap.add_argument("--workload", default="plain", choices=["plain", "batched", "served", "sweep"],
@@ -462,9 +465,11 @@ def main():
     ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="served: arrival rates (req/s)")
     ap.add_argument("--requests", type=int, default=200, help="served: requests per rate")
     args = ap.parse_args()
-    global N_LOG
+    global N_LOG, GATE, DEG
     if args.n:
         N_LOG = args.n
+    if args.d:
+        GATE, DEG = (1, 3) if args.d == 3 and args.gate != 2 else (2, args.d)
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -488,7 +493,8 @@ def main():
     roots = ctx.roots(GATE, N_LOG, DEG, dcols)
     stream = torch.cuda.Stream(dev)
     N = 1 << N_LOG
-    M = 4 * N
+    M = blowup(DEG) * N
+    C = ncols(GATE, DEG)
     ps_sc = zc.proof_size(GATE, N_LOG, DEG, zc.ZC_FORM_SUMCHECK)
     ps_nt = zc.proof_size(GATE, N_LOG, DEG, zc.ZC_FORM_NTT)
     p_sc = torch.zeros(ps_sc, dtype=torch.uint8, device=dev)
@@ -580,11 +586,11 @@ def main():
             ctx.prove_ntt(GATE, N_LOG, DEG, hcols, roots=roots, stream=stream, q_out=hq)
         stream.synchronize()
         e2e_ms.append((time.perf_counter() - t_a) * 1e3)
-    h2d = 2 * 8 * N * 32 if have_ntt else 8 * N * 32
+    h2d = 2 * C * N * 32 if have_ntt else C * N * 32
     d2h = ps_sc + ((ps_nt + M * 32) if have_ntt else 0)
 
     # ---- dominant kernel roofline (the longest single launch of the step)
-    dom = st_nt if (st_nt and st_nt[6] > st_sc[6]) else st_sc
+    dom = st_nt if (st_nt and (st_sc is None or st_nt[6] > st_sc[6])) else st_sc
     dom_name = ("ntt slice-LDE pass" if dom is st_nt else "sumcheck round-1 evaluate kernel")
     dom_ms = dom[6]
     achieved = dom[7] / (dom_ms * 1e-3) if dom_ms > 0 else 0.0
@@ -593,15 +599,16 @@ def main():
             "algorithmic_mulmods_per_launch": dom[7], "algorithmic_bytes_per_launch": dom[8],
             "hbm_gbs_at_algorithmic_bytes": dom[8] / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None,
             "peak_note": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz / 272 IMAD per mulmod"}
-    by_form = {"sumcheck": {"ms": float(np.median(sc_ms)),
-                            "roofline_ms": 1e3 * max(algorithmic_mulmods("sumcheck", N_LOG) / ALU_PEAK_MULMOD,
-                                                      algorithmic_bytes("sumcheck", N_LOG) / HBM_PEAK),
-                            "phases_ms": [round(x, 4) for x in st_sc[:5]]}}
-    by_form["sumcheck"]["roofline_frac"] = by_form["sumcheck"]["roofline_ms"] / by_form["sumcheck"]["ms"]
+    by_form = {"sumcheck": {"ms": float(np.median(sc_ms)) if run_sc else None,
+                            "roofline_ms": 1e3 * max(algorithmic_mulmods("sumcheck", N_LOG, DEG, GATE) / ALU_PEAK_MULMOD,
+                                                      algorithmic_bytes("sumcheck", N_LOG, DEG, GATE) / HBM_PEAK),
+                            "phases_ms": [round(x, 4) for x in st_sc[:5]] if st_sc else None}}
+    if run_sc:
+        by_form["sumcheck"]["roofline_frac"] = by_form["sumcheck"]["roofline_ms"] / by_form["sumcheck"]["ms"]
     if have_ntt:
         by_form["ntt"] = {"ms": float(np.median(nt_ms)),
-                          "roofline_ms": 1e3 * max(algorithmic_mulmods("ntt", N_LOG) / ALU_PEAK_MULMOD,
-                                                    algorithmic_bytes("ntt", N_LOG) / HBM_PEAK),
+                          "roofline_ms": 1e3 * max(algorithmic_mulmods("ntt", N_LOG, DEG, GATE) / ALU_PEAK_MULMOD,
+                                                    algorithmic_bytes("ntt", N_LOG, DEG, GATE) / HBM_PEAK),
                           "phases_ms": [round(x, 4) for x in st_nt[:6]]}
         by_form["ntt"]["roofline_frac"] = by_form["ntt"]["roofline_ms"] / by_form["ntt"]["ms"]
     else:

@@ -274,15 +274,21 @@ zc_status zc_serve(zc_ctx* ctx, const zc_request* reqs, uint32_t count, const zc
  * the candidates and stores the winners here.
  *
  *   ZC_TUNE_SC_GRID      SumCheck: most CTAs one round kernel is split over
- *                        (the fold/evaluate split); 1..4096, default 2 per SM.
+ *                        (the fold/evaluate split); 1..4096, default one wave
+ *                        of resident CTAs (Plonk) or two (product gate).
  *   ZC_TUNE_SC_TAIL_LOG  SumCheck: the single-CTA tail takes over once a round
  *                        has at most 2^value pairs; 0..24, default 8 (Plonk
  *                        gate) or 6 (product gate).
- *   ZC_TUNE_SC_SMALL_LOG SumCheck, Plonk gate: rounds 2.. with at most 2^value
+ *   ZC_TUNE_SC_SMALL_LOG SumCheck: rounds 2.. with at most 2^value pairs
+ *                        evaluate both H(0) and H(1) instead of deriving one
+ *                        from the claim; 1..24, default 14.
+ *   ZC_TUNE_SC_CHUNK_LOG SumCheck, Plonk gate: rounds 2.. with at most 2^value
  *                        pairs spread each pair over 16 threads; 1..24,
- *                        default 12.
+ *                        default 16.
  *   ZC_TUNE_SC_MINB      SumCheck, Plonk gate: resident CTAs per SM the large
- *                        round kernels are compiled for; 1 or 2, default 1.
+ *                        round kernels are compiled for; 1 or 2, default 2.
+ *   ZC_TUNE_SC_PROD_PPT  SumCheck, product gate: evaluation points per thread
+ *                        in the large rounds; 1 or 3, default 3.
  *   ZC_TUNE_NTT_TILE_LOG NTT: elements per shared-memory pass tile, 2^value;
  *                        10, 11 or 12, default 11.
  *   ZC_TUNE_NTT_MINB     NTT: resident CTAs per SM the 2^11 tile is compiled
@@ -297,7 +303,9 @@ typedef enum {
   ZC_TUNE_NTT_TILE_LOG = 3,
   ZC_TUNE_NTT_MINB = 4,
   ZC_TUNE_SC_SMALL_LOG = 5,
-  ZC_TUNE_SC_MINB = 6
+  ZC_TUNE_SC_MINB = 6,
+  ZC_TUNE_SC_PROD_PPT = 7,
+  ZC_TUNE_SC_CHUNK_LOG = 8
 } zc_tune_key;
 
 zc_status zc_tune_set(zc_ctx* ctx, zc_form form, uint32_t n, zc_tune_key key, int32_t value);

@@ -806,6 +806,8 @@ static bool tune_value_ok(zc_tune_key key, int32_t v) {
     case ZC_TUNE_NTT_MINB: return v == 1 || v == 2;
     case ZC_TUNE_SC_SMALL_LOG: return v >= 1 && v <= 24;
     case ZC_TUNE_SC_MINB: return v == 1 || v == 2;
+    case ZC_TUNE_SC_PROD_PPT: return v == 1 || v == 3;
+    case ZC_TUNE_SC_CHUNK_LOG: return v >= 1 && v <= 24;
   }
   return false;
 }
@@ -813,7 +815,7 @@ static bool tune_value_ok(zc_tune_key key, int32_t v) {
 static bool tune_form_ok(zc_form form, zc_tune_key key) {
   if (form == ZC_FORM_SUMCHECK)
     return key == ZC_TUNE_SC_GRID || key == ZC_TUNE_SC_TAIL_LOG || key == ZC_TUNE_SC_SMALL_LOG ||
-           key == ZC_TUNE_SC_MINB;
+           key == ZC_TUNE_SC_MINB || key == ZC_TUNE_SC_PROD_PPT || key == ZC_TUNE_SC_CHUNK_LOG;
   if (form == ZC_FORM_NTT) return key == ZC_TUNE_NTT_TILE_LOG || key == ZC_TUNE_NTT_MINB;
   return false;
 }

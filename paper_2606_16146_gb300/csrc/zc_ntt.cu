@@ -106,6 +106,7 @@ enum { POST_NONE = 0, POST_TW = 1, POST_OUTER = 2, POST_FINAL = 3, POST_TAB = 4 
 struct NttPassArgs {
   const fr* in[kMaxCols];
   fr* out[kMaxCols];
+  uint32_t items;         // columns in this launch
   uint32_t logL;          // sub-DFT length
   uint32_t logW;          // sub-DFTs per CTA
   // element (b, t) address: ((b >> lbdiv) * bs_hi) + (b & (bdiv-1)) * bs_lo + t * ts
@@ -162,11 +163,34 @@ __device__ __forceinline__ void dft8(fr (&x)[8], const fr* tab) {
   x[7] = fr_sub(e3, o3);
 }
 
+// The CTA tile in shared memory: element i's two 16-byte halves live in two
+// planes, and the 16-byte index is XOR-swizzled (i ^ ((i >> 3) & 7)) so
+// that unit-stride and radix-strided (8, 64) warp accesses spread over all
+// banks.
+struct SmTile {
+  uint4* p;     // plane 0: p[0, T), plane 1: p[T, 2T)
+  uint32_t T;
+  __device__ __forceinline__ uint32_t sw(uint32_t i) const { return i ^ ((i >> 3) & 7); }
+  __device__ __forceinline__ fr get(uint32_t i) const {
+    const uint32_t s = sw(i);
+    const uint4 a = p[s], b = p[T + s];
+    fr x;
+    x.v[0] = a.x; x.v[1] = a.y; x.v[2] = a.z; x.v[3] = a.w;
+    x.v[4] = b.x; x.v[5] = b.y; x.v[6] = b.z; x.v[7] = b.w;
+    return x;
+  }
+  __device__ __forceinline__ void put(uint32_t i, const fr& x) const {
+    const uint32_t s = sw(i);
+    p[s] = make_uint4(x.v[0], x.v[1], x.v[2], x.v[3]);
+    p[T + s] = make_uint4(x.v[4], x.v[5], x.v[6], x.v[7]);
+  }
+};
+
 // One Stockham stage of radix R = 2^lr on the CTA tile sm[t * W + w]; each
 // thread owns 8 elements (8 / R independent groups).
 template <int LR>
-__device__ __forceinline__ void stockham_stage(fr* sm, uint32_t logL, uint32_t logW, uint32_t logNs,
-                                               const fr* tab) {
+__device__ __forceinline__ void stockham_stage(const SmTile& sm, uint32_t logL, uint32_t logW,
+                                               uint32_t logNs, const fr* tab) {
   constexpr int R = 1 << LR;
   constexpr int GROUPS = 8 / R;
   const uint32_t L = 1u << logL, W = 1u << logW;
@@ -182,7 +206,7 @@ __device__ __forceinline__ void stockham_stage(fr* sm, uint32_t logL, uint32_t l
     ww[g] = w;
     if (j_all < ngroups) {
 #pragma unroll
-      for (int r = 0; r < R; r++) x[g * R + r] = sm[(j + r * qL) * W + w];
+      for (int r = 0; r < R; r++) x[g * R + r] = sm.get((j + r * qL) * W + w);
     }
   }
   __syncthreads();
@@ -219,20 +243,25 @@ __device__ __forceinline__ void stockham_stage(fr* sm, uint32_t logL, uint32_t l
     const uint32_t k = j & ((1u << logNs) - 1);
     const uint32_t idxD = ((j >> logNs) << (logNs + LR)) + k;
 #pragma unroll
-    for (int r = 0; r < R; r++) sm[(idxD + (r << logNs)) * W + w] = x[g * R + r];
+    for (int r = 0; r < R; r++) sm.put((idxD + (r << logNs)) * W + w, x[g * R + r]);
   }
   __syncthreads();
 }
 
 template <int TILE, int MINB>
 __global__ void __launch_bounds__(TILE / 8, MINB) k_ntt_pass(NttPassArgs A) {
-  extern __shared__ __align__(16) fr sm[];
-  const int item = blockIdx.y;
+  extern __shared__ __align__(16) uint4 sm_planes[];
+  const SmTile sm{sm_planes, (uint32_t)TILE};
+  // items (columns) vary fastest across consecutive CTAs, so the per-element
+  // factor tables, shared by every column, are reused from L2
+  const uint32_t items = A.items;
+  const int item = (int)(blockIdx.x % items);
+  const uint64_t blk = blockIdx.x / items;
   const fr* __restrict__ in = A.in[item];
   fr* out = A.out[item];
   const uint32_t logL = A.logL, logW = A.logW;
   const uint32_t L = 1u << logL, W = 1u << logW;
-  const uint64_t b0 = (uint64_t)blockIdx.x << logW;
+  const uint64_t b0 = blk << logW;
   const uint32_t n_el = L << logW;  // <= TILE (smaller only for tiny transforms)
   const bool in_t_fast = A.in_ts == 1, out_t_fast = A.out_ts == 1;
   const uint64_t in_bdiv_mask = (1ull << A.in_lbdiv) - 1, out_bdiv_mask = (1ull << A.out_lbdiv) - 1;
@@ -254,7 +283,7 @@ __global__ void __launch_bounds__(TILE / 8, MINB) k_ntt_pass(NttPassArgs A) {
                     ld_fr(A.pre_lo + (k & ((1ull << A.pre_shift) - 1))));
       x = fr_mul(x, f);
     }
-    sm[t * W + w] = x;
+    sm.put(t * W + w, x);
   }
   __syncthreads();
 
@@ -273,7 +302,7 @@ __global__ void __launch_bounds__(TILE / 8, MINB) k_ntt_pass(NttPassArgs A) {
     if (out_t_fast) { t = idx & (L - 1); w = idx >> logL; }
     else { w = idx & (W - 1); t = idx >> logW; }
     const uint64_t b = b0 + w;
-    fr y = sm[t * W + w];
+    fr y = sm.get(t * W + w);
     if (A.post == POST_TAB) {
       const uint64_t ti = (b >> A.p_lbdiv) * A.p_hs + (b & ((1ull << A.p_lbdiv) - 1)) * A.p_ls + t * A.p_ts;
       y = fr_mul(y, ld_fr(A.post_tab + ti));
@@ -655,7 +684,8 @@ static zc_status run_pass(zc_ctx* ctx, cudaStream_t st, NttPassArgs& a, int item
     ctx->err = "NTT pass: batch not a multiple of the tile";
     return ZC_ERR_ARG;
   }
-  dim3 grid((unsigned)blocks, (unsigned)items);
+  a.items = (uint32_t)items;
+  dim3 grid((unsigned)(blocks * (uint64_t)items));
   if (logTile == 12) launch_pass_variant<4096, 1>(a, grid, st);
   else if (logTile == 11 && minb != 1) launch_pass_variant<2048, 2>(a, grid, st);
   else if (logTile == 11) launch_pass_variant<2048, 1>(a, grid, st);

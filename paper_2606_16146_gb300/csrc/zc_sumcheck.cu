@@ -33,6 +33,8 @@
 // weight (stored at level d) and a per-degree constant for o bring back to 0.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "zc_internal.cuh"
 #include "zc_transcript.cuh"
@@ -41,9 +43,10 @@ namespace zc {
 
 constexpr uint64_t kTailPairsPlonk = 32;
 constexpr uint64_t kTailPairsProd = 64;
-constexpr uint64_t kSmallPairsPlonk = 4096;  // Plonk rounds with at most this many pairs: k_sc_plonk_small
-constexpr int kPP = 4;  // product gate: points per thread
-constexpr int kSmallPB = 16;  // pairs per chunk of k_sc_plonk_small (256 threads)
+constexpr uint64_t kSmallPairsPlonk = 1ull << 14;  // rounds with at most this many pairs evaluate H(0) and H(1)
+constexpr uint64_t kChunkPairsPlonk = 1ull << 16;  // Plonk rounds 2.. with at most this many: k_sc_plonk_chunk
+constexpr int kPP = 3;  // product gate: points per thread
+constexpr int kSmallPB = 16;  // pairs per chunk of k_sc_plonk_chunk (256 threads)
 constexpr int kTailPB = 32;   // pairs per chunk in the tail (512 threads)
 constexpr int kTailThreads = 16 * kTailPB;
 
@@ -362,12 +365,12 @@ __device__ __forceinline__ uint32_t prod_point(int p, int np, bool full, uint32_
 }
 
 // Product gate f = q w1 .. w_{d-1} - o, pair k: this thread's kPP points.
-template <bool COHERENT>
+template <int PP, bool COHERENT>
 __device__ __forceinline__ void prod_pair(const ScRoundArgs& A, const fr* const* col, uint64_t k,
-                                          uint64_t h, int pcnt, const uint32_t (&tpt)[kPP],
-                                          bool first, const fr& w, fr (&acc)[kPP], uint32_t& bad) {
+                                          uint64_t h, int pcnt, const uint32_t (&tpt)[PP],
+                                          bool first, const fr& w, fr (&acc)[PP], uint32_t& bad) {
   const int d = (int)A.d;
-  fr prod[kPP];
+  fr prod[PP];
   for (int j = 0; j <= d; j++) {
     const fr lo = ldx<COHERENT>(col[j] + k), hi = ldx<COHERENT>(col[j] + k + h);
     if (first) bad |= (!fr_is_canonical(lo)) | (!fr_is_canonical(hi));
@@ -375,7 +378,7 @@ __device__ __forceinline__ void prod_pair(const ScRoundArgs& A, const fr* const*
     fr e = lo;
     uint32_t tcur = 0;
 #pragma unroll
-    for (int p = 0; p < kPP; p++) {
+    for (int p = 0; p < PP; p++) {
       if (p >= pcnt) break;
       fr x;
       if (tpt[p] == kInf) {
@@ -396,7 +399,7 @@ __device__ __forceinline__ void prod_pair(const ScRoundArgs& A, const fr* const*
     }
   }
 #pragma unroll
-  for (int p = 0; p < kPP; p++)
+  for (int p = 0; p < PP; p++)
     if (p < pcnt) acc[p] = fr_add(acc[p], fr_mul(prod[p], w));
 }
 
@@ -583,23 +586,26 @@ __global__ void __launch_bounds__(256, MINB) k_sc_plonk_round(ScRoundArgs A) {
   sc_finish_round(A, NP);
 }
 
-// One small Plonk round (i >= 2, few pairs): chunks of kSmallPB pairs, each
-// pair's work spread over 16 threads (plonk_chunk), all of H(0), H(1), H(2),
-// H(inf) evaluated (no inverse needed).  The last CTA to finish runs the
-// challenge.
-__global__ void __launch_bounds__(16 * kSmallPB) k_sc_plonk_small(ScRoundArgs A) {
+// One Plonk round i >= 2 in chunks of kSmallPB pairs, each pair's work
+// spread over 16 threads (plonk_chunk).  FULL: all of H(0), H(1), H(2),
+// H(inf) (small rounds: no inverse needed); otherwise H(p0), H(2), H(inf).
+// The last CTA to finish runs the challenge.
+template <bool FULL>
+__global__ void __launch_bounds__(16 * kSmallPB) k_sc_plonk_chunk(ScRoundArgs A) {
+  constexpr int NPT = FULL ? 4 : 3;
   __shared__ PlonkChunkSmem<kSmallPB> S;
-  __shared__ fr part[4];
+  __shared__ fr part[NPT];
   const int i = A.round;
   const fr alpha = A.st->alpha[i - 1];
+  const uint32_t p0 = FULL ? 0u : A.st->p0[i];
   fr acc = fr_zero();
   for (uint64_t kb = (uint64_t)blockIdx.x * kSmallPB; kb < A.h; kb += (uint64_t)A.nwork * kSmallPB)
-    plonk_chunk<kSmallPB, true, false>(S, A.src, A.dst, A.h, kb, alpha, 0u, A.E + A.eq_hi[i],
+    plonk_chunk<kSmallPB, FULL, false>(S, A.src, A.dst, A.h, kb, alpha, p0, A.E + A.eq_hi[i],
                                        A.E + A.eq_lo[i], A.m_lo[i], acc);
-  plonk_chunk_reduce<kSmallPB, 4>(acc, part);
-  if (threadIdx.x < 4) st_fr(A.partials + (size_t)blockIdx.x * 4 + threadIdx.x, part[threadIdx.x]);
+  plonk_chunk_reduce<kSmallPB, NPT>(acc, part);
+  if (threadIdx.x < NPT) st_fr(A.partials + (size_t)blockIdx.x * NPT + threadIdx.x, part[threadIdx.x]);
   __syncthreads();
-  sc_finish_round(A, 4);
+  sc_finish_round(A, NPT);
 }
 
 // MLE update by alpha_{round-1}: dst[j][k] = src[j][k] + alpha (src[j][k+h] - src[j][k])
@@ -615,35 +621,12 @@ __global__ void __launch_bounds__(256) k_sc_fold(ScFoldArgs A) {
   }
 }
 
-// Product gate f = q w1 .. w_{d-1} - o at point t (kInf: leading
-// coefficient) for pair k, times the eq weight w.  Tables at level 0; the
-// product of d factors lands on level 1 - d, o is brought there by kcomp,
-// and the eq weight (level d) returns the sum to level 0.
-template <bool COHERENT>
-__device__ __forceinline__ fr prod_point_value(const ScRoundArgs& A, const fr* const* col, uint64_t k,
-                                               uint64_t h, uint32_t t, bool first, const fr& w,
-                                               uint32_t& bad) {
-  const int d = (int)A.d;
-  fr prod;
-  for (int j = 0; j < d; j++) {
-    const fr lo = ldx<COHERENT>(col[j] + k), hi = ldx<COHERENT>(col[j] + k + h);
-    if (first) bad |= (!fr_is_canonical(lo)) | (!fr_is_canonical(hi));
-    const fr dl = fr_sub(hi, lo);
-    const fr x = t == kInf ? dl : (t == 0 ? lo : (t == 1 ? hi : fr_add(lo, fr_mul_small(dl, t))));
-    prod = j == 0 ? x : fr_mul(prod, x);
-  }
-  if (t != kInf) {  // o enters at level 0; infinity has no o term
-    const fr lo = ldx<COHERENT>(col[d] + k), hi = ldx<COHERENT>(col[d] + k + h);
-    if (first) bad |= (!fr_is_canonical(lo)) | (!fr_is_canonical(hi));
-    const fr x = t == 0 ? lo : (t == 1 ? hi : fr_add(lo, fr_mul_small(fr_sub(hi, lo), t)));
-    prod = fr_sub(prod, fr_mul(x, A.kcomp));
-  }
-  return fr_mul(prod, w);
-}
-
-// Product-gate evaluation of one large round (columns already folded): one
-// thread per (pair, point), floor(256 / np) pairs per CTA in flight.
-__global__ void __launch_bounds__(256) k_sc_prod_round(ScRoundArgs A) {
+// Product-gate evaluation of one large round (columns already folded): G =
+// ceil(np / PP) threads per pair, each evaluating up to PP consecutive
+// points (the extensions lo + t (hi - lo) advance by one addition per
+// point), floor(256 / G) pairs per CTA in flight.
+template <int PP>
+__global__ void __launch_bounds__(256, PP == 1 ? 3 : 2) k_sc_prod_round(ScRoundArgs A) {
   const int i = A.round;
   const bool first = i == 0;
   if (first && blockIdx.x == A.nwork) {
@@ -654,28 +637,37 @@ __global__ void __launch_bounds__(256) k_sc_prod_round(ScRoundArgs A) {
   const bool full = first || A.full;
   const int np = full ? d + 1 : d;
   const uint32_t p0 = full ? 0u : A.st->p0[i];
-  const int spb = (int)blockDim.x / np;
-  const int slot = (int)threadIdx.x / np, pi = (int)threadIdx.x % np;
+  const int G = (np + PP - 1) / PP;
+  const int spb = (int)blockDim.x / G;
+  const int slot = (int)threadIdx.x / G, g = (int)threadIdx.x % G;
+  const int pbeg = g * PP, pcnt = max(0, min(PP, np - pbeg));
   const uint32_t mlo = A.m_lo[i];
   const fr* ehi = A.E + A.eq_hi[i];
   const fr* elo = A.E + A.eq_lo[i];
   uint32_t bad = 0;
-  fr acc = fr_zero();
+  fr acc[PP];
+  uint32_t tpt[PP];
+#pragma unroll
+  for (int p = 0; p < PP; p++) {
+    acc[p] = fr_zero();
+    tpt[p] = p < pcnt ? prod_point(pbeg + p, np, full, p0) : 0u;
+  }
   if (slot < spb) {
-    const uint32_t t = prod_point(pi, np, full, p0);
     for (uint64_t k = (uint64_t)blockIdx.x * spb + slot; k < A.h; k += (uint64_t)A.nwork * spb) {
       const fr w = fr_mul(ld_fr(ehi + (k >> mlo)), ld_fr(elo + (k & ((1ull << mlo) - 1))));
-      acc = fr_add(acc, prod_point_value<false>(A, A.src, k, A.h, t, first && pi == 0, w, bad));
+      prod_pair<PP, false>(A, A.src, k, A.h, pcnt, tpt, first && g == 0, w, acc, bad);
     }
   }
   if (bad) atomicOr(&A.st->err, 1u);
-  __shared__ fr red[256];
-  red[threadIdx.x] = acc;
+  __shared__ fr red[256][PP];
+#pragma unroll
+  for (int p = 0; p < PP; p++) red[threadIdx.x][p] = acc[p];
   __syncthreads();
   if ((int)threadIdx.x < np) {
-    fr s = fr_zero();
-    for (int q = 0; q < spb; q++) s = fr_add(s, red[q * np + threadIdx.x]);
-    st_fr(A.partials + (size_t)blockIdx.x * np + threadIdx.x, s);
+    const int q = threadIdx.x, gq = q / PP, pq = q % PP;
+    fr v = fr_zero();
+    for (int sl = 0; sl < spb; sl++) v = fr_add(v, red[sl * G + gq][pq]);
+    st_fr(A.partials + (size_t)blockIdx.x * np + q, v);
   }
   __syncthreads();
   sc_finish_round(A, np);
@@ -750,7 +742,7 @@ __global__ void __launch_bounds__(PLONK ? kTailThreads : 256, 1) k_sc_tail(ScRou
       }
       for (uint64_t k = threadIdx.x / G; k < h && pcnt > 0; k += nslots) {
         const fr w = fr_mul(ld_fr_cg(ehi + (k >> mlo)), ld_fr_cg(elo + (k & ((1ull << mlo) - 1))));
-        prod_pair<true>(A, cur, k, h, pcnt, tpt, first, w, acc, bad);
+        prod_pair<kPP, true>(A, cur, k, h, pcnt, tpt, first, w, acc, bad);
       }
       // sum each point over all threads (threads outside its group add zero)
       for (int p = 0; p < np; p++) {
@@ -806,27 +798,59 @@ struct ScBuffers {
 
 struct ScPlan {
   int c, G, grid_plonk, grid_prod, npmax;
-  uint64_t tail_pairs, small_pairs;
+  uint64_t tail_pairs, small_pairs, chunk_pairs;
+  int grid_chunk;
   int minb;  // Plonk round kernels: resident CTAs per SM they are compiled for
+  int ppt;   // product round kernel: points per thread (1 or kPP)
   uint32_t eq_total, eq_hi[kMaxN], eq_lo[kMaxN], mlo[kMaxN];
   EqTask tasks[2 * kMaxN];
 };
 
 // grid: most CTAs per round kernel (0: two per SM); tail_log: the tail takes
 // over at 2^tail_log pairs (0: the gate's default).
+// Resident 256-thread CTAs per SM of a kernel on the current device (cached).
+static int resident_ctas(const void* fn) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<int, const void*>, int>> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto& e : cache)
+    if (e.first.first == dev && e.first.second == fn) return e.second;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, 0) != cudaSuccess || nb < 1) {
+    cudaGetLastError();
+    nb = 1;
+  }
+  cache.push_back({{dev, fn}, nb});
+  return nb;
+}
+
+static const void* plonk_round_fn(int minb) {
+  return minb == 2 ? reinterpret_cast<const void*>(k_sc_plonk_round<false, 2>)
+                   : reinterpret_cast<const void*>(k_sc_plonk_round<false, 1>);
+}
+
 static ScPlan sc_plan(const zc_params* p, int SMs, int grid = 0, int tail_log = 0, int small_log = 0,
-                      int minb = 0) {
+                      int minb = 0, int ppt = 0, int chunk_log = 0) {
   ScPlan P{};
   const uint32_t n = p->n, d = p->d;
   const bool plonk = p->gate == ZC_GATE_PLONK;
   P.c = gate_ncols(p->gate, d);
   P.G = 1;
   while (P.G * kPP < (int)d + 1) P.G *= 2;
-  P.grid_plonk = grid > 0 ? grid : std::max(8, 2 * SMs / 8 * 8);
-  P.grid_prod = grid > 0 ? grid : 2 * SMs;
+  // default: one wave of resident CTAs for the Plonk kernels (register bound,
+  // one CTA per SM), two waves for the product kernel
+  P.grid_plonk = grid > 0 ? grid : SMs * resident_ctas(plonk_round_fn(minb == 1 ? 1 : 2));
+  P.ppt = ppt == 1 ? 1 : 3;
+  P.grid_prod = grid > 0 ? grid
+                         : 2 * SMs * resident_ctas(P.ppt == 1 ? reinterpret_cast<const void*>(k_sc_prod_round<1>)
+                                                              : reinterpret_cast<const void*>(k_sc_prod_round<3>));
   P.tail_pairs = tail_log > 0 ? 1ull << tail_log : (plonk ? kTailPairsPlonk : kTailPairsProd);
   P.small_pairs = small_log > 0 ? 1ull << small_log : kSmallPairsPlonk;
-  P.minb = minb == 2 ? 2 : 1;
+  P.chunk_pairs = chunk_log > 0 ? 1ull << chunk_log : kChunkPairsPlonk;
+  P.grid_chunk = SMs * resident_ctas(reinterpret_cast<const void*>(k_sc_plonk_chunk<false>));
+  P.minb = minb == 1 ? 1 : 2;
   P.npmax = (int)d + 1;
   for (uint32_t i = 0; i < n; i++) {
     uint32_t mlo, mhi;
@@ -843,7 +867,7 @@ static ScPlan sc_plan(const zc_params* p, int SMs, int grid = 0, int tail_log = 
 }
 
 static size_t sc_partials_count(const ScPlan& P) {
-  return (size_t)(std::max(P.grid_plonk, P.grid_prod) + 1) * (P.npmax + 1);
+  return (size_t)(std::max(std::max(P.grid_plonk, P.grid_prod), P.grid_chunk) + 1) * (P.npmax + 1);
 }
 
 // Carve the proof's buffers from an arena; false when it is too small.
@@ -927,9 +951,10 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
       R.src[j] = cur[j];
       R.dst[j] = B.tab[j];
     }
-    if (plonk && i > 0 && h <= P.small_pairs) {
-      R.nwork = (uint32_t)std::min<uint64_t>((h + kSmallPB - 1) / kSmallPB, (uint64_t)P.grid_plonk);
-      k_sc_plonk_small<<<R.nwork, 16 * kSmallPB, 0, st>>>(R);
+    if (plonk && i > 0 && h <= P.chunk_pairs) {
+      R.nwork = (uint32_t)std::min<uint64_t>((h + kSmallPB - 1) / kSmallPB, (uint64_t)P.grid_chunk);
+      if (R.full) k_sc_plonk_chunk<true><<<R.nwork, 16 * kSmallPB, 0, st>>>(R);
+      else k_sc_plonk_chunk<false><<<R.nwork, 16 * kSmallPB, 0, st>>>(R);
       for (int j = 0; j < 8; j++) cur[j] = B.tab[j];
       *launches += 1;
     } else if (plonk) {
@@ -962,9 +987,11 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
         for (int j = 0; j < c; j++) R.src[j] = cur[j];
         *launches += 1;
       }
-      const uint64_t slots_per_blk = 256 / (R.full ? d + 1 : d);
+      const uint64_t slots_per_blk = 256 / (((R.full ? d + 1 : d) + P.ppt - 1) / P.ppt);
       R.nwork = (uint32_t)std::min<uint64_t>((h + slots_per_blk - 1) / slots_per_blk, (uint64_t)P.grid_prod);
-      k_sc_prod_round<<<R.nwork + (i == 0 ? inv_cta : 0u), 256, 0, st>>>(R);
+      const uint32_t ctas = R.nwork + (i == 0 ? inv_cta : 0u);
+      if (P.ppt == 1) k_sc_prod_round<1><<<ctas, 256, 0, st>>>(R);
+      else k_sc_prod_round<3><<<ctas, 256, 0, st>>>(R);
       *launches += 1;
     }
     if (i == 0 && ev) cudaEventRecord(ev[3], st);
@@ -989,7 +1016,9 @@ size_t sumcheck_scratch_bytes(const zc_ctx* ctx, const zc_params* p) {
   const ScPlan P = sc_plan(p, ctx->sm_count, ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_GRID),
                            ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_TAIL_LOG),
                            ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_SMALL_LOG),
-                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_MINB));
+                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_MINB),
+                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_PROD_PPT),
+                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_CHUNK_LOG));
   const uint64_t N = 1ull << p->n;
   const size_t psize = 16 + 32 * ((size_t)p->n * (p->d + 2) + P.c);
   return align_up(sizeof(fr) * N, 256) * P.c + align_up(sizeof(fr) * sc_partials_count(P), 256) +
@@ -1004,7 +1033,9 @@ zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* col
   const ScPlan P = sc_plan(p, ctx->sm_count, ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_GRID),
                            ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_TAIL_LOG),
                            ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_SMALL_LOG),
-                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_MINB));
+                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_MINB),
+                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_PROD_PPT),
+                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_CHUNK_LOG));
   const int c = P.c;
   const uint64_t N = 1ull << n;
   const size_t psize = 16 + 32 * ((size_t)n * (d + 2) + c);

@@ -17,9 +17,11 @@ from __future__ import annotations
 from . import zc
 
 SC_SPACE = {
-    zc.ZC_TUNE_SC_GRID: (76, 152, 304, 608),
+    zc.ZC_TUNE_SC_GRID: (152, 304, 456, 608, 912),
     zc.ZC_TUNE_SC_MINB: (1, 2),
-    zc.ZC_TUNE_SC_SMALL_LOG: (10, 12, 14),
+    zc.ZC_TUNE_SC_PROD_PPT: (1, 3),
+    zc.ZC_TUNE_SC_CHUNK_LOG: (12, 14, 16, 18, 20),
+    zc.ZC_TUNE_SC_SMALL_LOG: (10, 12, 13, 14, 16),
     zc.ZC_TUNE_SC_TAIL_LOG: (4, 5, 6, 7),
 }
 NTT_SPACE = {
@@ -104,6 +106,11 @@ def tune_batch(ctx, forms, params, cols, proofs, q_outs=None, reps: int = 3) -> 
             state["g"] = ctx.batch_graph(forms, params, cols, proofs, q_outs)
         state["g"].launch(stream)
 
+    def reset():
+        if state["g"] is not None:
+            state["g"].close()
+            state["g"] = None
+
     # a new graph per setting: the launch shapes are fixed at capture
     trials, settings = [], {}
     best_ms = _time(run, stream, reps)
@@ -117,8 +124,7 @@ def tune_batch(ctx, forms, params, cols, proofs, q_outs=None, reps: int = 3) -> 
                 continue
             for n in ns:
                 ctx.tune_set(form, n, key, v)
-            state["g"].close()
-            state["g"] = None
+            reset()
             ms = _time(run, stream, reps)
             trials.append(((form, key), v, ms))
             if ms < best_ms:
@@ -126,8 +132,6 @@ def tune_batch(ctx, forms, params, cols, proofs, q_outs=None, reps: int = 3) -> 
         for n in ns:
             ctx.tune_set(form, n, key, best_v)
         settings[(form, key)] = best_v
-        state["g"].close()
-        state["g"] = None
-    if state["g"] is not None:
-        state["g"].close()
+        reset()
+    reset()
     return {"ms": best_ms, "best": {f"{f}:{k}": v for (f, k), v in settings.items()}, "trials": trials}

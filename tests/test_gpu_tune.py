@@ -26,7 +26,9 @@ def test_sumcheck_candidates_same_bytes(ctx, gate, n, d):
     cands += [{zc.ZC_TUNE_SC_GRID: 1, zc.ZC_TUNE_SC_TAIL_LOG: 1, zc.ZC_TUNE_SC_SMALL_LOG: 1},
               {zc.ZC_TUNE_SC_GRID: 3, zc.ZC_TUNE_SC_TAIL_LOG: 24},
               {zc.ZC_TUNE_SC_GRID: 5, zc.ZC_TUNE_SC_SMALL_LOG: 24, zc.ZC_TUNE_SC_TAIL_LOG: 3,
-               zc.ZC_TUNE_SC_MINB: 2}]
+               zc.ZC_TUNE_SC_MINB: 2},
+              {zc.ZC_TUNE_SC_SMALL_LOG: 1, zc.ZC_TUNE_SC_CHUNK_LOG: 24, zc.ZC_TUNE_SC_TAIL_LOG: 2},
+              {zc.ZC_TUNE_SC_SMALL_LOG: 1, zc.ZC_TUNE_SC_CHUNK_LOG: 1, zc.ZC_TUNE_SC_PROD_PPT: 1}]
     for cand in cands:
         for k in tune.SC_SPACE:
             ctx.tune_set(zc.ZC_FORM_SUMCHECK, n, k, cand.get(k, 0))
@@ -79,3 +81,27 @@ def test_autotuner_picks_fastest(ctx):
             assert ctx.tune_get(form, n, k) == v
         for k in tune.space(form):
             ctx.tune_set(form, n, k, 0)
+
+
+def test_batch_tuner_keeps_bytes(ctx):
+    import torch
+    mix = [(1, 1, 9, 3), (2, 2, 8, 8), (1, 2, 10, 8), (2, 1, 11, 3)]
+    forms, params, cols, dcols, proofs = [], [], [], [], []
+    for i, (form, gate, n, d) in enumerate(mix):
+        c = witness.generate(gate, n, d, 8400 + i)
+        forms.append(form)
+        params.append((gate, n, d, 0))
+        cols.append(c)
+        dcols.append(to_device(c))
+        proofs.append(torch.zeros(zc.proof_size(gate, n, d, form), dtype=torch.uint8, device="cuda"))
+    r = tune.tune_batch(ctx, forms, params, dcols, proofs, None, reps=1)
+    assert r["ms"] > 0 and len(r["trials"]) > 1
+    ctx.prove_batch(forms, params, dcols, proofs, None)
+    torch.cuda.synchronize()
+    for (form, gate, n, d), c, p in zip(mix, cols, proofs):
+        want = (oracle.prove_sumcheck(gate, n, d, c) if form == 1 else oracle.prove_ntt(gate, n, d, c)[0])
+        assert proof_bytes(p) == want
+    for form in (zc.ZC_FORM_SUMCHECK, zc.ZC_FORM_NTT):
+        for n in range(8, 12):
+            for k in tune.space(form):
+                ctx.tune_set(form, n, k, 0)
