@@ -57,6 +57,31 @@ def _hbm_peak_bytes_s() -> float:
 
 HBM_PEAK = _hbm_peak_bytes_s()
 
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "ntt_pass_plonk_n22_traffic.md")
+
+
+def recorded_traffic(path: str = TRAFFIC_RECORD):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu record,
+    or None when the kernel sources changed since the counters were taken."""
+    import hashlib
+    try:
+        fields = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "sources",
+                                                              "source_sha256")):
+                    k, v = line.split(":", 1)
+                    fields[k.strip()] = v.strip().strip("`")
+        h = hashlib.sha256()
+        for rel in fields["sources"].split(","):
+            with open(os.path.join(ROOT, rel.strip()), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != fields["source_sha256"]:
+            return None
+        return float(fields["traffic_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
 
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
@@ -594,8 +619,10 @@ def main():
     dom_name = ("ntt slice-LDE pass" if dom is st_nt else "sumcheck round-1 evaluate kernel")
     dom_ms = dom[6]
     achieved = dom[7] / (dom_ms * 1e-3) if dom_ms > 0 else 0.0
+    traffic = recorded_traffic() if (dom is st_nt and N_LOG == 22 and GATE == 1) else None
     roof = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": ALU_PEAK_MULMOD,
-            "unit": "mulmod/s", "frac": achieved / ALU_PEAK_MULMOD, "traffic": None,
+            "unit": "mulmod/s", "frac": achieved / ALU_PEAK_MULMOD, "traffic": traffic,
+            "traffic_source": "profiles/ntt_pass_plonk_n22_traffic.md" if traffic else None,
             "algorithmic_mulmods_per_launch": dom[7], "algorithmic_bytes_per_launch": dom[8],
             "hbm_gbs_at_algorithmic_bytes": dom[8] / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None,
             "peak_note": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz / 272 IMAD per mulmod"}

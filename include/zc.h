@@ -284,7 +284,7 @@ zc_status zc_serve(zc_ctx* ctx, const zc_request* reqs, uint32_t count, const zc
  *                        from the claim; 1..24, default 14.
  *   ZC_TUNE_SC_CHUNK_LOG SumCheck, Plonk gate: rounds 2.. with at most 2^value
  *                        pairs spread each pair over 16 threads; 1..24,
- *                        default 16.
+ *                        default 13.
  *   ZC_TUNE_SC_MINB      SumCheck, Plonk gate: resident CTAs per SM the large
  *                        round kernels are compiled for; 1 or 2, default 2.
  *   ZC_TUNE_SC_PROD_PPT  SumCheck, product gate: evaluation points per thread

@@ -44,7 +44,7 @@ namespace zc {
 constexpr uint64_t kTailPairsPlonk = 32;
 constexpr uint64_t kTailPairsProd = 64;
 constexpr uint64_t kSmallPairsPlonk = 1ull << 14;  // rounds with at most this many pairs evaluate H(0) and H(1)
-constexpr uint64_t kChunkPairsPlonk = 1ull << 16;  // Plonk rounds 2.. with at most this many: k_sc_plonk_chunk
+constexpr uint64_t kChunkPairsPlonk = 1ull << 13;  // Plonk rounds 2.. with at most this many: k_sc_plonk_chunk
 constexpr int kPP = 3;  // product gate: points per thread
 constexpr int kSmallPB = 16;  // pairs per chunk of k_sc_plonk_chunk (256 threads)
 constexpr int kTailPB = 32;   // pairs per chunk in the tail (512 threads)
@@ -938,15 +938,24 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
   // Rounds i >= 2 with more than small_pairs pairs take one of H(0), H(1)
   // from the claim, which needs 1/r_i and 1/(1 - r_i): an extra CTA of round
   // 1 computes them, only when such a round exists.
-  const bool need_inv = (N >> 2) > std::max(P.small_pairs, tail_pairs);
+  // Whether round i (h pairs, not in the tail) evaluates all points: round 1
+  // always; later rounds when small, and for the Plonk gate only in the
+  // chunk kernel (the pair kernel always derives a point).
+  auto round_full = [&](uint32_t r, uint64_t hh) {
+    if (r == 0) return true;
+    if (hh > P.small_pairs) return false;
+    return !plonk || hh <= P.chunk_pairs;
+  };
+  bool need_inv = false;
+  for (uint32_t r = 1; r < n && (N >> (r + 1)) > tail_pairs; r++) need_inv |= !round_full(r, N >> (r + 1));
   const uint32_t inv_cta = need_inv ? 1u : 0u;
   for (; i < n; i++) {
     const uint64_t h = N >> (i + 1);
     if (h <= tail_pairs) break;
     R.round = (int)i;
     R.h = h;
-    R.full = (i == 0 || h <= P.small_pairs) ? 1u : 0u;
-    R.next_derives = (h / 2 > P.small_pairs && h / 2 > tail_pairs) ? 1u : 0u;
+    R.full = round_full(i, h) ? 1u : 0u;
+    R.next_derives = (h / 2 > tail_pairs && !round_full(i + 1, h / 2)) ? 1u : 0u;
     for (int j = 0; j < c; j++) {
       R.src[j] = cur[j];
       R.dst[j] = B.tab[j];

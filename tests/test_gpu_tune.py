@@ -105,3 +105,19 @@ def test_batch_tuner_keeps_bytes(ctx):
         for n in range(8, 12):
             for k in tune.space(form):
                 ctx.tune_set(form, n, k, 0)
+
+
+@pytest.mark.parametrize("small,chunk", [(14, 10), (10, 14), (16, 16), (1, 1)])
+def test_full_and_derived_rounds_mix(ctx, small, chunk):
+    """Rounds that derive a point and rounds that evaluate all points, in
+    either kernel, interleave correctly (claims kept exactly when needed)."""
+    gate, n, d = 1, 17, 3
+    cols = witness.generate(gate, n, d, 8500)
+    want = oracle.prove_sumcheck(gate, n, d, cols)
+    ctx.tune_set(zc.ZC_FORM_SUMCHECK, n, zc.ZC_TUNE_SC_SMALL_LOG, small)
+    ctx.tune_set(zc.ZC_FORM_SUMCHECK, n, zc.ZC_TUNE_SC_CHUNK_LOG, chunk)
+    try:
+        assert proof_bytes(ctx.prove_sumcheck(gate, n, d, to_device(cols))) == want
+    finally:
+        ctx.tune_set(zc.ZC_FORM_SUMCHECK, n, zc.ZC_TUNE_SC_SMALL_LOG, 0)
+        ctx.tune_set(zc.ZC_FORM_SUMCHECK, n, zc.ZC_TUNE_SC_CHUNK_LOG, 0)
