@@ -134,29 +134,31 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_sample(steps: int = 1) -> dict:
-    """Time the CPU oracle on the n = SAMPLE_N witness; scale to n = N_LOG."""
+def cpu_sample(steps: int = 1, warmup: int = 0) -> dict:
+    """Time the CPU oracle on the n = SAMPLE_N witness; scale to n = N_LOG.
+    warmup untimed samples first; the value is the median of `steps` samples."""
     import oracle
     from paper_2606_16146_gb300 import witness
     cols = witness.generate(GATE, SAMPLE_N, DEG, 1000 + SAMPLE_N)
     roots = [oracle.root(c) for c in cols]
     ts, tn = [], []
-    for _ in range(steps):
+    for it in range(warmup + steps):
         t0 = time.perf_counter()
         oracle.prove_sumcheck(GATE, SAMPLE_N, DEG, cols, roots=roots)
         t1 = time.perf_counter()
         oracle.prove_ntt(GATE, SAMPLE_N, DEG, cols, roots=roots)
         t2 = time.perf_counter()
-        ts.append(t1 - t0)
-        tn.append(t2 - t1)
+        if it >= warmup:
+            ts.append(t1 - t0)
+            tn.append(t2 - t1)
     ks = algorithmic_mulmods("sumcheck", N_LOG) / algorithmic_mulmods("sumcheck", SAMPLE_N)
     kn = algorithmic_mulmods("ntt", N_LOG) / algorithmic_mulmods("ntt", SAMPLE_N)
     sc_ms = float(np.median(ts)) * 1e3 * ks
     nt_ms = float(np.median(tn)) * 1e3 * kn
     return {"value": sc_ms + nt_ms, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": (f"one SumCheck and one NTT proof of the Plonk witness at n={SAMPLE_N}, "
-                       f"scaled to n={N_LOG} by the algorithmic mulmod ratio "
-                       f"(x{ks:.1f} SumCheck, x{kn:.1f} NTT)"),
+            "sample": (f"one SumCheck and one NTT proof of the Plonk witness at n={SAMPLE_N} (median of "
+                       f"{steps} after {warmup} warm-up), scaled to n={N_LOG} by the algorithmic mulmod "
+                       f"ratio (x{ks:.1f} SumCheck, x{kn:.1f} NTT)"),
             "sumcheck_ms": sc_ms, "ntt_ms": nt_ms, "raw_s": [float(np.median(ts)), float(np.median(tn))]}
 
 
@@ -170,14 +172,28 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The largest value over all ranks (replicas: the slowest rank's time)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int) -> None:
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    for _ in range(args.warmup):
-        pass
-    samples = [cpu_sample(1)["value"] for _ in range(args.steps)]
-    base = cpu_sample(1)
-    ms = float(np.median(samples))
+    base = cpu_sample(steps=args.steps, warmup=args.warmup)
+    ms = base["value"]
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32x8 (255-bit field, exact)",
@@ -573,9 +589,7 @@ def main():
             nt_ms.append(e1.elapsed_time(e2))
 
     # ---- timed region
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    barrier(world)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
@@ -591,11 +605,7 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     elapsed = t0.elapsed_time(t1)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
+    elapsed = max_over_ranks(elapsed, world, dev)
     ms_per_step = elapsed / args.steps
     value = elapsed / (args.steps * world)
 

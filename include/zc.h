@@ -289,6 +289,8 @@ zc_status zc_serve(zc_ctx* ctx, const zc_request* reqs, uint32_t count, const zc
  *                        round kernels are compiled for; 1 or 2, default 2.
  *   ZC_TUNE_SC_PROD_PPT  SumCheck, product gate: evaluation points per thread
  *                        in the large rounds; 1 or 3, default 3.
+ *   ZC_TUNE_BATCH_LANES  batches: concurrent lanes (streams); set with n = 0
+ *                        under either form; 1..64, default 16.
  *   ZC_TUNE_NTT_TILE_LOG NTT: elements per shared-memory pass tile, 2^value;
  *                        10, 11 or 12, default 11.
  *   ZC_TUNE_NTT_MINB     NTT: resident CTAs per SM the 2^11 tile is compiled
@@ -305,7 +307,8 @@ typedef enum {
   ZC_TUNE_SC_SMALL_LOG = 5,
   ZC_TUNE_SC_MINB = 6,
   ZC_TUNE_SC_PROD_PPT = 7,
-  ZC_TUNE_SC_CHUNK_LOG = 8
+  ZC_TUNE_SC_CHUNK_LOG = 8,
+  ZC_TUNE_BATCH_LANES = 9
 } zc_tune_key;
 
 zc_status zc_tune_set(zc_ctx* ctx, zc_form form, uint32_t n, zc_tune_key key, int32_t value);

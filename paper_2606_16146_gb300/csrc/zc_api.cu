@@ -808,11 +808,13 @@ static bool tune_value_ok(zc_tune_key key, int32_t v) {
     case ZC_TUNE_SC_MINB: return v == 1 || v == 2;
     case ZC_TUNE_SC_PROD_PPT: return v == 1 || v == 3;
     case ZC_TUNE_SC_CHUNK_LOG: return v >= 1 && v <= 24;
+    case ZC_TUNE_BATCH_LANES: return v >= 1 && v <= 64;
   }
   return false;
 }
 
 static bool tune_form_ok(zc_form form, zc_tune_key key) {
+  if (key == ZC_TUNE_BATCH_LANES) return form == ZC_FORM_SUMCHECK || form == ZC_FORM_NTT;
   if (form == ZC_FORM_SUMCHECK)
     return key == ZC_TUNE_SC_GRID || key == ZC_TUNE_SC_TAIL_LOG || key == ZC_TUNE_SC_SMALL_LOG ||
            key == ZC_TUNE_SC_MINB || key == ZC_TUNE_SC_PROD_PPT || key == ZC_TUNE_SC_CHUNK_LOG;
@@ -823,7 +825,12 @@ static bool tune_form_ok(zc_form form, zc_tune_key key) {
 zc_status zc_tune_set(zc_ctx* ctx, zc_form form, uint32_t n, zc_tune_key key, int32_t value) {
   if (!ctx || n > (uint32_t)kMaxN || !tune_form_ok(form, key) || !tune_value_ok(key, value))
     return ZC_ERR_ARG;
+  if (key == ZC_TUNE_BATCH_LANES && n != 0) return ZC_ERR_ARG;
   std::lock_guard<std::mutex> lk(ctx->mu);
+  if (key == ZC_TUNE_BATCH_LANES) {  // one value for the context, kept under the SumCheck form
+    ctx->tune[0][0][(int)key - 1] = value;
+    return ZC_OK;
+  }
   ctx->tune[(int)form - 1][n][(int)key - 1] = value;
   return ZC_OK;
 }
@@ -831,7 +838,7 @@ zc_status zc_tune_set(zc_ctx* ctx, zc_form form, uint32_t n, zc_tune_key key, in
 zc_status zc_tune_get(zc_ctx* ctx, zc_form form, uint32_t n, zc_tune_key key, int32_t* value) {
   if (!ctx || !value || n > (uint32_t)kMaxN || !tune_form_ok(form, key)) return ZC_ERR_ARG;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  *value = ctx->tuned(form, n, key);
+  *value = key == ZC_TUNE_BATCH_LANES ? ctx->tuned(ZC_FORM_SUMCHECK, 0, key) : ctx->tuned(form, n, key);
   return ZC_OK;
 }
 

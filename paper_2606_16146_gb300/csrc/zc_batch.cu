@@ -18,7 +18,8 @@
 
 namespace zc {
 
-constexpr int kMaxLanes = 16;
+constexpr int kDefaultLanes = 16;
+constexpr int kMaxLanes = 64;
 
 static double instance_cost(const zc_params& p, zc_form f) {
   const double N = std::ldexp(1.0, (int)p.n);
@@ -88,7 +89,11 @@ static std::vector<int> assign_lanes(uint32_t count, const zc_form* forms, const
   return lane;
 }
 
-static int lanes_for(uint32_t count) { return (int)std::min<uint32_t>(count, kMaxLanes); }
+static int lanes_for(const zc_ctx* ctx, uint32_t count) {
+  const int32_t t = ctx->tuned(ZC_FORM_SUMCHECK, 0, ZC_TUNE_BATCH_LANES);
+  const int want = t > 0 ? std::min<int>(t, kMaxLanes) : kDefaultLanes;
+  return (int)std::min<uint32_t>(count, (uint32_t)want);
+}
 
 zc_status batch_prepare(zc_ctx* ctx, uint32_t count, const zc_form* forms, const zc_params* params,
                         const bool* q_direct, cudaStream_t st) {
@@ -96,7 +101,7 @@ zc_status batch_prepare(zc_ctx* ctx, uint32_t count, const zc_form* forms, const
     zc_status s = check_params(ctx, &params[i], forms[i]);
     if (s != ZC_OK) return s;
   }
-  const int K = lanes_for(count);
+  const int K = lanes_for(ctx, count);
   zc_status s = make_lanes(ctx, K);
   if (s != ZC_OK) return s;
   for (int k = 0; k < K; k++) std::memcpy(ctx->lanes[k]->tune, ctx->tune, sizeof(ctx->tune));
@@ -127,7 +132,7 @@ zc_status batch_prepare(zc_ctx* ctx, uint32_t count, const zc_form* forms, const
 zc_status batch_enqueue(zc_ctx* ctx, uint32_t count, const zc_form* forms, const zc_params* params,
                         const void* const* const* cols, cudaStream_t st, uint8_t* const* proofs,
                         void* const* q_outs) {
-  const int K = lanes_for(count);
+  const int K = lanes_for(ctx, count);
   if ((int)ctx->lanes.size() < K) {
     ctx->err = "batch not prepared";
     return ZC_ERR_ARG;

@@ -501,17 +501,23 @@ __device__ __forceinline__ void plonk_chunk_reduce(const fr& acc, fr* out) {
 // ---------------------------------------------------------------- kernels --
 
 // Transcript: absorb the column roots, squeeze r_1..r_n; reset per-proof state.
+// The hash chain is serial (thread 0); the n conversions to Montgomery form
+// run on n threads afterwards.  Launched with at least kMaxN threads.
 __global__ void k_sc_setup(ScSetupArgs A) {
+  __shared__ fr raw[kMaxN];
   if (threadIdx.x < kMaxN) A.st->counter[threadIdx.x] = 0;
-  if (threadIdx.x != 0) return;
-  uint32_t S[8];
-  for (int i = 0; i < 8; i++) S[i] = A.S0[i];
-  for (int j = 0; j < A.c; j++) tr_absorb32(S, A.roots + 32 * j);
-  for (int i = 0; i < A.n; i++) A.st->r[i] = fr_mul(tr_squeeze(S), A.C->r2);
-  for (int i = 0; i < 8; i++) A.st->S[i] = S[i];
-  A.st->claim = fr_zero();
-  A.st->ci = A.C->one;
-  A.st->err = 0;
+  if (threadIdx.x == 0) {
+    uint32_t S[8];
+    for (int i = 0; i < 8; i++) S[i] = A.S0[i];
+    for (int j = 0; j < A.c; j++) tr_absorb32(S, A.roots + 32 * j);
+    for (int i = 0; i < A.n; i++) raw[i] = tr_squeeze(S);
+    for (int i = 0; i < 8; i++) A.st->S[i] = S[i];
+    A.st->claim = fr_zero();
+    A.st->ci = A.C->one;
+    A.st->err = 0;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < A.n) A.st->r[threadIdx.x] = fr_mul(raw[threadIdx.x], A.C->r2);
 }
 
 // Factor tables of eq_{>i} for every round, and the derived-point choice.

@@ -24,6 +24,7 @@ SC_SPACE = {
     zc.ZC_TUNE_SC_SMALL_LOG: (10, 12, 13, 14, 16),
     zc.ZC_TUNE_SC_TAIL_LOG: (4, 5, 6, 7),
 }
+BATCH_LANES = (8, 16, 32, 64)
 NTT_SPACE = {
     zc.ZC_TUNE_NTT_TILE_LOG: (10, 11, 12),
     zc.ZC_TUNE_NTT_MINB: (1, 2),
@@ -99,6 +100,9 @@ def tune_batch(ctx, forms, params, cols, proofs, q_outs=None, reps: int = 3) -> 
         if ns:
             ns_of[form] = ns
             keys += [(form, k, v) for k, v in space(form).items()]
+    # the lane count is one value per context (n = 0), tried first
+    keys.insert(0, ("lanes", zc.ZC_TUNE_BATCH_LANES, BATCH_LANES))
+    ns_of["lanes"] = [0]
     state = {"g": None}
 
     def run():
@@ -117,20 +121,21 @@ def tune_batch(ctx, forms, params, cols, proofs, q_outs=None, reps: int = 3) -> 
     trials.append(("start", None, best_ms))
     for form, key, values in keys:
         ns = ns_of[form]
-        cur = ctx.tune_get(form, ns[0], key)
+        f = zc.ZC_FORM_SUMCHECK if form == "lanes" else form
+        cur = ctx.tune_get(f, ns[0], key)
         best_v = cur
         for v in values:
             if v == cur:
                 continue
             for n in ns:
-                ctx.tune_set(form, n, key, v)
+                ctx.tune_set(f, n, key, v)
             reset()
             ms = _time(run, stream, reps)
             trials.append(((form, key), v, ms))
             if ms < best_ms:
                 best_ms, best_v = ms, v
         for n in ns:
-            ctx.tune_set(form, n, key, best_v)
+            ctx.tune_set(f, n, key, best_v)
         settings[(form, key)] = best_v
         reset()
     reset()

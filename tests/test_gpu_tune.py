@@ -66,7 +66,9 @@ def test_tune_values_checked(ctx):
                             (zc.ZC_FORM_SUMCHECK, 0, zc.ZC_TUNE_NTT_TILE_LOG, 11),
                             (zc.ZC_FORM_SUMCHECK, 29, zc.ZC_TUNE_SC_GRID, 8),
                             (zc.ZC_FORM_SUMCHECK, 0, zc.ZC_TUNE_SC_GRID, 5000),
-                            (3, 0, zc.ZC_TUNE_SC_GRID, 8)]:
+                            (3, 0, zc.ZC_TUNE_SC_GRID, 8),
+                            (zc.ZC_FORM_SUMCHECK, 12, zc.ZC_TUNE_BATCH_LANES, 8),
+                            (zc.ZC_FORM_NTT, 0, zc.ZC_TUNE_BATCH_LANES, 65)]:
         with pytest.raises(zc.ZCError):
             ctx.tune_set(form, n, key, v)
 
@@ -105,6 +107,7 @@ def test_batch_tuner_keeps_bytes(ctx):
         for n in range(8, 12):
             for k in tune.space(form):
                 ctx.tune_set(form, n, k, 0)
+    ctx.tune_set(zc.ZC_FORM_SUMCHECK, 0, zc.ZC_TUNE_BATCH_LANES, 0)
 
 
 @pytest.mark.parametrize("small,chunk", [(14, 10), (10, 14), (16, 16), (1, 1)])
