@@ -284,11 +284,15 @@ zc_status zc_serve(zc_ctx* ctx, const zc_request* reqs, uint32_t count, const zc
  *                        from the claim; 1..24, default 14.
  *   ZC_TUNE_SC_CHUNK_LOG SumCheck, Plonk gate: rounds 2.. with at most 2^value
  *                        pairs spread each pair over 16 threads; 1..24,
- *                        default 13.
+ *                        default 14.
  *   ZC_TUNE_SC_MINB      SumCheck, Plonk gate: resident CTAs per SM the large
  *                        round kernels are compiled for; 1 or 2, default 2.
  *   ZC_TUNE_SC_PROD_PPT  SumCheck, product gate: evaluation points per thread
  *                        in the large rounds; 1 or 3, default 3.
+ *   ZC_TUNE_SC_QUAD_LOG  SumCheck, Plonk gate: rounds 2.. above the chunk
+ *                        threshold with at most 2^value pairs spread each pair
+ *                        over 4 threads (larger rounds: one pair per thread);
+ *                        1..24, default 17.
  *   ZC_TUNE_BATCH_LANES  batches: concurrent lanes (streams); set with n = 0
  *                        under either form; 1..64, default 16.
  *   ZC_TUNE_NTT_TILE_LOG NTT: elements per shared-memory pass tile, 2^value;
@@ -308,7 +312,8 @@ typedef enum {
   ZC_TUNE_SC_MINB = 6,
   ZC_TUNE_SC_PROD_PPT = 7,
   ZC_TUNE_SC_CHUNK_LOG = 8,
-  ZC_TUNE_BATCH_LANES = 9
+  ZC_TUNE_BATCH_LANES = 9,
+  ZC_TUNE_SC_QUAD_LOG = 10
 } zc_tune_key;
 
 zc_status zc_tune_set(zc_ctx* ctx, zc_form form, uint32_t n, zc_tune_key key, int32_t value);

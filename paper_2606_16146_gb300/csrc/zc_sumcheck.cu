@@ -44,9 +44,11 @@ namespace zc {
 constexpr uint64_t kTailPairsPlonk = 32;
 constexpr uint64_t kTailPairsProd = 64;
 constexpr uint64_t kSmallPairsPlonk = 1ull << 14;  // rounds with at most this many pairs evaluate H(0) and H(1)
-constexpr uint64_t kChunkPairsPlonk = 1ull << 13;  // Plonk rounds 2.. with at most this many: k_sc_plonk_chunk
+constexpr uint64_t kChunkPairsPlonk = 1ull << 14;  // Plonk rounds 2.. with at most this many: 16 threads per pair
+constexpr uint64_t kQuadPairsPlonk = 1ull << 17;   // and up to this many: 4 threads per pair
 constexpr int kPP = 3;  // product gate: points per thread
-constexpr int kSmallPB = 16;  // pairs per chunk of k_sc_plonk_chunk (256 threads)
+constexpr int kSmallPB = 16;  // pairs per chunk of the 16-threads-per-pair kernel (256 threads)
+constexpr int kQuadPB = 32;   // pairs per chunk of the 4-threads-per-pair kernel (128 threads)
 constexpr int kTailPB = 32;   // pairs per chunk in the tail (512 threads)
 constexpr int kTailThreads = 16 * kTailPB;
 
@@ -404,19 +406,21 @@ __device__ __forceinline__ void prod_pair(const ScRoundArgs& A, const fr* const*
 }
 
 // Plonk round i >= 2 on a chunk of PB pairs, the work of each pair spread
-// over 16 threads (blockDim.x == 16 PB) so that a round is four
-// multiplications deep:
-//   1. thread (column, half, pair): fold by alpha_{i-1}, store, keep in smem;
-//   2. thread (pair, item): qM b, qR b, qO c at each finite point, the slope
+// over TPP threads (blockDim.x == TPP PB), so a round is a few
+// multiplications deep instead of ~30:
+//   1. fold by alpha_{i-1}: 16 items per pair (column, half), store, keep in
+//      smem; thread (slot, pair) takes items slot, slot + TPP, ...;
+//   2. items per pair: qM b, qR b, qO c at each finite point, the slope
 //      product dqM db, and the eq weight E_hi E_lo;
-//   3. thread (pair, point): s = a (qL + qM b) + qR b + qO c + qC at a finite
+//   3. thread (point, pair): s = a (qL + qM b) + qR b + qO c + qC at a finite
 //      point, dqM db da at infinity, times the eq weight.
-// FULL: points 0, 1, 2, inf; otherwise p0, 2, inf.  Threads t < NPT PB add
-// their value for (pair t / NPT, point t % NPT) into acc.
+// FULL: points 0, 1, 2, inf; otherwise p0, 2, inf.  Thread t = point * PB +
+// pair (t < NPT PB) adds its value into acc.  Pairs are the fastest thread
+// index, so every warp-wide load or store is contiguous.
 template <int PB>
 struct PlonkChunkSmem {
   fr V[8][2][PB];  // folded lo / hi per column
-  fr U[PB][12];    // products and the eq weight
+  fr U[12][PB];    // products and the eq weight
 };
 
 // column j of pair p at point pt: 0 -> lo, 1 -> hi, 2 -> 2 hi - lo, 3 -> slope
@@ -429,17 +433,21 @@ __device__ __forceinline__ fr plonk_at(const PlonkChunkSmem<PB>& S, int j, int p
   return pt == 2 ? fr_add(hi, dl) : dl;
 }
 
-template <int PB, bool FULL, bool COHERENT>
+template <int PB, int TPP, bool FULL, bool COHERENT>
 __device__ __forceinline__ void plonk_chunk(PlonkChunkSmem<PB>& S, const fr* const* src, fr* const* dst,
                                             uint64_t h, uint64_t kbase, const fr& alpha, uint32_t p0,
                                             const fr* ehi, const fr* elo, uint32_t mlo, fr& acc) {
   constexpr int NPT = FULL ? 4 : 3, NF = NPT - 1, NITEM = 3 * NF + 2;
-  const int t = threadIdx.x;
+  static_assert(TPP >= NPT, "one point per thread in phase 3");
+  const int t = threadIdx.x, p = t % PB, slot = t / PB;
+  const uint64_t k = kbase + p;
+  const bool live = k < h;
   auto point = [&](int f) { return FULL ? f : (f == 0 ? (int)p0 : 2); };  // finite point f
-  {
-    const int p = t % PB, half = (t / PB) & 1, j = t / (2 * PB);
-    const uint64_t e = kbase + p + (half ? h : 0);
-    if (kbase + p < h) {
+#pragma unroll
+  for (int item = slot; item < 16; item += TPP) {
+    const int j = item >> 1, half = item & 1;
+    const uint64_t e = k + (half ? h : 0);
+    if (live) {
       const fr x0 = ldx<COHERENT>(src[j] + e), x1 = ldx<COHERENT>(src[j] + e + 2 * h);
       const fr v = fr_add(x0, fr_mul(alpha, fr_sub(x1, x0)));
       st_fr(dst[j] + e, v);
@@ -447,10 +455,9 @@ __device__ __forceinline__ void plonk_chunk(PlonkChunkSmem<PB>& S, const fr* con
     }
   }
   __syncthreads();
-  if (t < 16 * PB) {
-    const int p = t >> 4, q = t & 15;
-    const uint64_t k = kbase + p;
-    if (k < h && q < NITEM) {
+#pragma unroll
+  for (int q = slot; q < NITEM; q += TPP) {
+    if (live) {
       fr u;
       if (q == NITEM - 1) {
         u = fr_mul(ldx<COHERENT>(ehi + (k >> mlo)), ldx<COHERENT>(elo + (k & ((1ull << mlo) - 1))));
@@ -462,38 +469,39 @@ __device__ __forceinline__ void plonk_chunk(PlonkChunkSmem<PB>& S, const fr* con
         const int jb = term == 2 ? 7 : 6;                    // b, b, c
         u = fr_mul(plonk_at(S, ja, p, pt), plonk_at(S, jb, p, pt));
       }
-      S.U[p][q] = u;
+      S.U[q][p] = u;
     }
   }
   __syncthreads();
-  if (t < NPT * PB) {
-    const int p = t / NPT, f = t % NPT;
-    if (kbase + p < h) {
-      fr v;
-      if (f < NF) {
-        const int pt = point(f);
-        v = fr_mul(plonk_at(S, 5, p, pt), fr_add(plonk_at(S, 0, p, pt), S.U[p][3 * f]));
-        v = fr_add(v, fr_add(fr_add(S.U[p][3 * f + 1], S.U[p][3 * f + 2]), plonk_at(S, 4, p, pt)));
-      } else {
-        v = fr_mul(S.U[p][NITEM - 2], plonk_at(S, 5, p, 3));
-      }
-      acc = fr_add(acc, fr_mul(v, S.U[p][NITEM - 1]));
+  if (slot < NPT && live) {
+    const int f = slot;
+    fr v;
+    if (f < NF) {
+      const int pt = point(f);
+      v = fr_mul(plonk_at(S, 5, p, pt), fr_add(plonk_at(S, 0, p, pt), S.U[3 * f][p]));
+      v = fr_add(v, fr_add(fr_add(S.U[3 * f + 1][p], S.U[3 * f + 2][p]), plonk_at(S, 4, p, pt)));
+    } else {
+      v = fr_mul(S.U[NITEM - 2][p], plonk_at(S, 5, p, 3));
     }
+    acc = fr_add(acc, fr_mul(v, S.U[NITEM - 1][p]));
   }
   __syncthreads();
 }
 
 // Sum the per-thread values of plonk_chunk over pairs: out[q] for q < NPT.
+// Warp q adds point q's PB values with shuffles.
 template <int PB, int NPT>
 __device__ __forceinline__ void plonk_chunk_reduce(const fr& acc, fr* out) {
   __shared__ fr R[NPT * PB];
   const int t = threadIdx.x;
   if (t < NPT * PB) R[t] = acc;
   __syncthreads();
-  if (t < NPT) {
+  const int lane = t & 31, q = t >> 5;
+  if (q < NPT) {
     fr s = fr_zero();
-    for (int p = 0; p < PB; p++) s = fr_add(s, R[NPT * p + t]);
-    out[t] = s;
+    for (int p = lane; p < PB; p += 32) s = fr_add(s, R[q * PB + p]);
+    s = warp_sum(s);
+    if (lane == 0) out[q] = s;
   }
   __syncthreads();
 }
@@ -544,16 +552,51 @@ __global__ void k_sc_eq(ScEqArgs A) {
   st_fr(A.E + e, acc);
 }
 
-// 1/r_i and 1/(1 - r_i) (level 1, 0 for a zero input), threads 0..2n-1
+// 1/r_i and 1/(1 - r_i) (level 1, 0 for a zero input) for i < n, by one
+// batch inversion (Montgomery's trick): prefix and suffix products of the 2n
+// values (Hillis-Steele scans in shared memory), a single binary-GCD
+// inversion of their product, then inv_t = prefix_{t-1} suffix_{t+1} / P.
+// All threads of the CTA (at least 64) reach every barrier.
 __device__ void sc_inverses(ScState* st, int n, const DevConst* C) {
-  const int t = threadIdx.x;
-  if (t < 2 * n) {
-    const int i = t >> 1;
-    const fr r = st->r[i];
-    const fr x = (t & 1) ? fr_sub(C->one, r) : r;
-    const fr inv = fr_mul(fr_inv_binary(from_mont(x)), C->r2);
-    if (t & 1) st->r1inv[i] = inv;
-    else st->rinv[i] = inv;
+  __shared__ fr pre[2 * kMaxN], suf[2 * kMaxN];
+  __shared__ fr total_inv;
+  const int t = threadIdx.x, m = 2 * n;
+  bool zero = false;
+  fr x = C->one;
+  if (t < m) {
+    const fr r = st->r[t >> 1];
+    x = (t & 1) ? fr_sub(C->one, r) : r;  // level 1
+    zero = fr_is_zero(x);
+    if (zero) x = C->one;  // leave it out of the product
+    pre[t] = x;
+    suf[t] = x;
+  }
+  __syncthreads();
+  for (int off = 1; off < m; off <<= 1) {
+    fr a, b;
+    if (t < m) {
+      a = t >= off ? fr_mul(pre[t - off], pre[t]) : pre[t];
+      b = t + off < m ? fr_mul(suf[t], suf[t + off]) : suf[t];
+    }
+    __syncthreads();
+    if (t < m) {
+      pre[t] = a;
+      suf[t] = b;
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    // pre[m-1] = P R (level 1); inv_binary gives P^-1 R^-1; times R^3 -> P^-1 R
+    total_inv = fr_mul(fr_inv_binary(pre[m - 1]), C->rpow[3]);
+  }
+  __syncthreads();
+  if (t < m) {
+    fr inv = total_inv;
+    if (t > 0) inv = fr_mul(inv, pre[t - 1]);
+    if (t + 1 < m) inv = fr_mul(inv, suf[t + 1]);
+    if (zero) inv = fr_zero();
+    if (t & 1) st->r1inv[t >> 1] = inv;
+    else st->rinv[t >> 1] = inv;
   }
 }
 
@@ -592,23 +635,23 @@ __global__ void __launch_bounds__(256, MINB) k_sc_plonk_round(ScRoundArgs A) {
   sc_finish_round(A, NP);
 }
 
-// One Plonk round i >= 2 in chunks of kSmallPB pairs, each pair's work
-// spread over 16 threads (plonk_chunk).  FULL: all of H(0), H(1), H(2),
+// One Plonk round i >= 2 in chunks of PB pairs, each pair's work spread over
+// TPP threads (plonk_chunk).  FULL: all of H(0), H(1), H(2),
 // H(inf) (small rounds: no inverse needed); otherwise H(p0), H(2), H(inf).
 // The last CTA to finish runs the challenge.
-template <bool FULL>
-__global__ void __launch_bounds__(16 * kSmallPB) k_sc_plonk_chunk(ScRoundArgs A) {
+template <int TPP, int PB, bool FULL>
+__global__ void __launch_bounds__(TPP * PB) k_sc_plonk_chunk(ScRoundArgs A) {
   constexpr int NPT = FULL ? 4 : 3;
-  __shared__ PlonkChunkSmem<kSmallPB> S;
+  __shared__ PlonkChunkSmem<PB> S;
   __shared__ fr part[NPT];
   const int i = A.round;
   const fr alpha = A.st->alpha[i - 1];
   const uint32_t p0 = FULL ? 0u : A.st->p0[i];
   fr acc = fr_zero();
-  for (uint64_t kb = (uint64_t)blockIdx.x * kSmallPB; kb < A.h; kb += (uint64_t)A.nwork * kSmallPB)
-    plonk_chunk<kSmallPB, FULL, false>(S, A.src, A.dst, A.h, kb, alpha, p0, A.E + A.eq_hi[i],
-                                       A.E + A.eq_lo[i], A.m_lo[i], acc);
-  plonk_chunk_reduce<kSmallPB, NPT>(acc, part);
+  for (uint64_t kb = (uint64_t)blockIdx.x * PB; kb < A.h; kb += (uint64_t)A.nwork * PB)
+    plonk_chunk<PB, TPP, FULL, false>(S, A.src, A.dst, A.h, kb, alpha, p0, A.E + A.eq_hi[i],
+                                      A.E + A.eq_lo[i], A.m_lo[i], acc);
+  plonk_chunk_reduce<PB, NPT>(acc, part);
   if (threadIdx.x < NPT) st_fr(A.partials + (size_t)blockIdx.x * NPT + threadIdx.x, part[threadIdx.x]);
   __syncthreads();
   sc_finish_round(A, NPT);
@@ -701,25 +744,16 @@ __global__ void __launch_bounds__(PLONK ? kTailThreads : 256, 1) k_sc_tail(ScRou
     const fr* elo = A.E + A.eq_lo[i];
     int np;
     if constexpr (PLONK) {
-      if (i == 0) {
-        np = 4;
-        fr acc[4] = {fr_zero(), fr_zero(), fr_zero(), fr_zero()};
-        for (uint64_t k = threadIdx.x; k < h; k += blockDim.x)
-          plonk_pair<true, true>(
-              cur, A.dst, C, k, h, fr_zero(), 0u,
-              fr_mul(ld_fr_cg(ehi + (k >> mlo)), ld_fr_cg(elo + (k & ((1ull << mlo) - 1)))), acc, bad);
-        block_sum<4>(acc, pg);
-      } else {
+      {  // i >= 1: round 1 never runs in the Plonk tail
         np = 4;
         fr acc = fr_zero();
         const fr alpha = A.st->alpha[i - 1];
         __shared__ PlonkChunkSmem<kTailPB> PS;
         for (uint64_t kb = 0; kb < h; kb += kTailPB)
-          plonk_chunk<kTailPB, true, true>(PS, cur, A.dst, h, kb, alpha, 0u, ehi, elo, mlo, acc);
+          plonk_chunk<kTailPB, 16, true, true>(PS, cur, A.dst, h, kb, alpha, 0u, ehi, elo, mlo, acc);
         plonk_chunk_reduce<kTailPB, 4>(acc, pg);
       }
-      // the converted wires live in dst after round 1, everything after round 2
-      for (int j = (i == 0 ? 5 : 0); j < c; j++) cur[j] = A.dst[j];
+      for (int j = 0; j < c; j++) cur[j] = A.dst[j];
     } else {
       if (i > 0) {
         const fr alpha = A.st->alpha[i - 1];
@@ -805,7 +839,8 @@ struct ScBuffers {
 struct ScPlan {
   int c, G, grid_plonk, grid_prod, npmax;
   uint64_t tail_pairs, small_pairs, chunk_pairs;
-  int grid_chunk;
+  int grid_chunk, grid_quad;
+  uint64_t quad_pairs;  // Plonk rounds 2.. in (chunk_pairs, quad_pairs]: 4 threads per pair
   int minb;  // Plonk round kernels: resident CTAs per SM they are compiled for
   int ppt;   // product round kernel: points per thread (1 or kPP)
   uint32_t eq_total, eq_hi[kMaxN], eq_lo[kMaxN], mlo[kMaxN];
@@ -814,8 +849,8 @@ struct ScPlan {
 
 // grid: most CTAs per round kernel (0: two per SM); tail_log: the tail takes
 // over at 2^tail_log pairs (0: the gate's default).
-// Resident 256-thread CTAs per SM of a kernel on the current device (cached).
-static int resident_ctas(const void* fn) {
+// Resident CTAs per SM of a kernel on the current device (cached).
+static int resident_ctas(const void* fn, int threads = 256) {
   static std::mutex mu;
   static std::vector<std::pair<std::pair<int, const void*>, int>> cache;
   int dev = 0;
@@ -824,7 +859,7 @@ static int resident_ctas(const void* fn) {
   for (auto& e : cache)
     if (e.first.first == dev && e.first.second == fn) return e.second;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, 0) != cudaSuccess || nb < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, 0) != cudaSuccess || nb < 1) {
     cudaGetLastError();
     nb = 1;
   }
@@ -838,7 +873,7 @@ static const void* plonk_round_fn(int minb) {
 }
 
 static ScPlan sc_plan(const zc_params* p, int SMs, int grid = 0, int tail_log = 0, int small_log = 0,
-                      int minb = 0, int ppt = 0, int chunk_log = 0) {
+                      int minb = 0, int ppt = 0, int chunk_log = 0, int quad_log = 0) {
   ScPlan P{};
   const uint32_t n = p->n, d = p->d;
   const bool plonk = p->gate == ZC_GATE_PLONK;
@@ -855,7 +890,9 @@ static ScPlan sc_plan(const zc_params* p, int SMs, int grid = 0, int tail_log = 
   P.tail_pairs = tail_log > 0 ? 1ull << tail_log : (plonk ? kTailPairsPlonk : kTailPairsProd);
   P.small_pairs = small_log > 0 ? 1ull << small_log : kSmallPairsPlonk;
   P.chunk_pairs = chunk_log > 0 ? 1ull << chunk_log : kChunkPairsPlonk;
-  P.grid_chunk = SMs * resident_ctas(reinterpret_cast<const void*>(k_sc_plonk_chunk<false>));
+  P.grid_chunk = SMs * resident_ctas(reinterpret_cast<const void*>(k_sc_plonk_chunk<16, kSmallPB, false>));
+  P.quad_pairs = quad_log > 0 ? 1ull << quad_log : kQuadPairsPlonk;
+  P.grid_quad = SMs * resident_ctas(reinterpret_cast<const void*>(k_sc_plonk_chunk<4, kQuadPB, false>), 4 * kQuadPB);
   P.minb = minb == 1 ? 1 : 2;
   P.npmax = (int)d + 1;
   for (uint32_t i = 0; i < n; i++) {
@@ -873,7 +910,8 @@ static ScPlan sc_plan(const zc_params* p, int SMs, int grid = 0, int tail_log = 
 }
 
 static size_t sc_partials_count(const ScPlan& P) {
-  return (size_t)(std::max(std::max(P.grid_plonk, P.grid_prod), P.grid_chunk) + 1) * (P.npmax + 1);
+  return (size_t)(std::max(std::max(P.grid_plonk, P.grid_prod), std::max(P.grid_chunk, P.grid_quad)) + 1) *
+         (P.npmax + 1);
 }
 
 // Carve the proof's buffers from an arena; false when it is too small.
@@ -950,14 +988,16 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
   auto round_full = [&](uint32_t r, uint64_t hh) {
     if (r == 0) return true;
     if (hh > P.small_pairs) return false;
-    return !plonk || hh <= P.chunk_pairs;
+    return !plonk || hh <= std::max(P.chunk_pairs, P.quad_pairs);
   };
   bool need_inv = false;
   for (uint32_t r = 1; r < n && (N >> (r + 1)) > tail_pairs; r++) need_inv |= !round_full(r, N >> (r + 1));
   const uint32_t inv_cta = need_inv ? 1u : 0u;
   for (; i < n; i++) {
     const uint64_t h = N >> (i + 1);
-    if (h <= tail_pairs) break;
+    // the Plonk tail starts at round 2 at the earliest: round 1 always runs the
+    // pair kernel, so the tail carries no round-1 code (fewer registers)
+    if (h <= tail_pairs && !(plonk && i == 0)) break;
     R.round = (int)i;
     R.h = h;
     R.full = round_full(i, h) ? 1u : 0u;
@@ -968,8 +1008,14 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
     }
     if (plonk && i > 0 && h <= P.chunk_pairs) {
       R.nwork = (uint32_t)std::min<uint64_t>((h + kSmallPB - 1) / kSmallPB, (uint64_t)P.grid_chunk);
-      if (R.full) k_sc_plonk_chunk<true><<<R.nwork, 16 * kSmallPB, 0, st>>>(R);
-      else k_sc_plonk_chunk<false><<<R.nwork, 16 * kSmallPB, 0, st>>>(R);
+      if (R.full) k_sc_plonk_chunk<16, kSmallPB, true><<<R.nwork, 16 * kSmallPB, 0, st>>>(R);
+      else k_sc_plonk_chunk<16, kSmallPB, false><<<R.nwork, 16 * kSmallPB, 0, st>>>(R);
+      for (int j = 0; j < 8; j++) cur[j] = B.tab[j];
+      *launches += 1;
+    } else if (plonk && i > 0 && h <= P.quad_pairs) {
+      R.nwork = (uint32_t)std::min<uint64_t>((h + kQuadPB - 1) / kQuadPB, (uint64_t)P.grid_quad);
+      if (R.full) k_sc_plonk_chunk<4, kQuadPB, true><<<R.nwork, 4 * kQuadPB, 0, st>>>(R);
+      else k_sc_plonk_chunk<4, kQuadPB, false><<<R.nwork, 4 * kQuadPB, 0, st>>>(R);
       for (int j = 0; j < 8; j++) cur[j] = B.tab[j];
       *launches += 1;
     } else if (plonk) {
@@ -1033,7 +1079,8 @@ size_t sumcheck_scratch_bytes(const zc_ctx* ctx, const zc_params* p) {
                            ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_SMALL_LOG),
                            ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_MINB),
                            ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_PROD_PPT),
-                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_CHUNK_LOG));
+                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_CHUNK_LOG),
+                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_QUAD_LOG));
   const uint64_t N = 1ull << p->n;
   const size_t psize = 16 + 32 * ((size_t)p->n * (p->d + 2) + P.c);
   return align_up(sizeof(fr) * N, 256) * P.c + align_up(sizeof(fr) * sc_partials_count(P), 256) +
@@ -1050,7 +1097,8 @@ zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* col
                            ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_SMALL_LOG),
                            ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_MINB),
                            ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_PROD_PPT),
-                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_CHUNK_LOG));
+                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_CHUNK_LOG),
+                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_QUAD_LOG));
   const int c = P.c;
   const uint64_t N = 1ull << n;
   const size_t psize = 16 + 32 * ((size_t)n * (d + 2) + c);

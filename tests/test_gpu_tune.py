@@ -110,8 +110,9 @@ def test_batch_tuner_keeps_bytes(ctx):
     ctx.tune_set(zc.ZC_FORM_SUMCHECK, 0, zc.ZC_TUNE_BATCH_LANES, 0)
 
 
-@pytest.mark.parametrize("small,chunk", [(14, 10), (10, 14), (16, 16), (1, 1)])
-def test_full_and_derived_rounds_mix(ctx, small, chunk):
+@pytest.mark.parametrize("small,chunk,quad", [(14, 10, 1), (10, 14, 1), (16, 16, 1), (1, 1, 1),
+                                              (14, 10, 15), (10, 12, 16), (1, 1, 24), (15, 8, 12)])
+def test_full_and_derived_rounds_mix(ctx, small, chunk, quad):
     """Rounds that derive a point and rounds that evaluate all points, in
     either kernel, interleave correctly (claims kept exactly when needed)."""
     gate, n, d = 1, 17, 3
@@ -119,8 +120,10 @@ def test_full_and_derived_rounds_mix(ctx, small, chunk):
     want = oracle.prove_sumcheck(gate, n, d, cols)
     ctx.tune_set(zc.ZC_FORM_SUMCHECK, n, zc.ZC_TUNE_SC_SMALL_LOG, small)
     ctx.tune_set(zc.ZC_FORM_SUMCHECK, n, zc.ZC_TUNE_SC_CHUNK_LOG, chunk)
+    ctx.tune_set(zc.ZC_FORM_SUMCHECK, n, zc.ZC_TUNE_SC_QUAD_LOG, quad)
     try:
         assert proof_bytes(ctx.prove_sumcheck(gate, n, d, to_device(cols))) == want
     finally:
         ctx.tune_set(zc.ZC_FORM_SUMCHECK, n, zc.ZC_TUNE_SC_SMALL_LOG, 0)
         ctx.tune_set(zc.ZC_FORM_SUMCHECK, n, zc.ZC_TUNE_SC_CHUNK_LOG, 0)
+        ctx.tune_set(zc.ZC_FORM_SUMCHECK, n, zc.ZC_TUNE_SC_QUAD_LOG, 0)
