@@ -810,6 +810,7 @@ static bool tune_value_ok(zc_tune_key key, int32_t v) {
     case ZC_TUNE_SC_CHUNK_LOG: return v >= 1 && v <= 24;
     case ZC_TUNE_BATCH_LANES: return v >= 1 && v <= 64;
     case ZC_TUNE_SC_QUAD_LOG: return v >= 1 && v <= 24;
+    case ZC_TUNE_SC_PROD_FUSE: return v == 1 || v == 2;
   }
   return false;
 }
@@ -819,7 +820,7 @@ static bool tune_form_ok(zc_form form, zc_tune_key key) {
   if (form == ZC_FORM_SUMCHECK)
     return key == ZC_TUNE_SC_GRID || key == ZC_TUNE_SC_TAIL_LOG || key == ZC_TUNE_SC_SMALL_LOG ||
            key == ZC_TUNE_SC_MINB || key == ZC_TUNE_SC_PROD_PPT || key == ZC_TUNE_SC_CHUNK_LOG ||
-           key == ZC_TUNE_SC_QUAD_LOG;
+           key == ZC_TUNE_SC_QUAD_LOG || key == ZC_TUNE_SC_PROD_FUSE;
   if (form == ZC_FORM_NTT) return key == ZC_TUNE_NTT_TILE_LOG || key == ZC_TUNE_NTT_MINB;
   return false;
 }

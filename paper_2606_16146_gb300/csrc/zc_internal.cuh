@@ -102,10 +102,10 @@ struct zc_ctx {
   uint32_t cur_n = 0;            // n of the proof being enqueued (selects tuned launch shapes)
   // launch parameters set by zc_tune_set: [form - 1][n][key - 1], 0 = unset;
   // n = 0 holds the value for sizes without their own entry
-  int32_t tune[2][zc::kMaxN + 1][10] = {};
+  int32_t tune[2][zc::kMaxN + 1][11] = {};
   int32_t tuned(zc_form form, uint32_t n, zc_tune_key key) const {
     const int f = (int)form - 1, k = (int)key - 1;
-    if (f < 0 || f > 1 || k < 0 || k > 9) return 0;
+    if (f < 0 || f > 1 || k < 0 || k > 10) return 0;
     if (n <= (uint32_t)zc::kMaxN && tune[f][n][k]) return tune[f][n][k];
     return tune[f][0][k];
   }

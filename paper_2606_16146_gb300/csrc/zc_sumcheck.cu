@@ -367,14 +367,16 @@ __device__ __forceinline__ uint32_t prod_point(int p, int np, bool full, uint32_
 }
 
 // Product gate f = q w1 .. w_{d-1} - o, pair k: this thread's kPP points.
-template <int PP, bool COHERENT>
-__device__ __forceinline__ void prod_pair(const ScRoundArgs& A, const fr* const* col, uint64_t k,
-                                          uint64_t h, int pcnt, const uint32_t (&tpt)[PP],
-                                          bool first, const fr& w, fr (&acc)[PP], uint32_t& bad) {
+// load(j, lo, hi) supplies column j of the pair (global memory or shared).
+template <int PP, class Load>
+__device__ __forceinline__ void prod_pair_g(const ScRoundArgs& A, Load load, int pcnt,
+                                            const uint32_t (&tpt)[PP], bool first, const fr& w,
+                                            fr (&acc)[PP], uint32_t& bad) {
   const int d = (int)A.d;
   fr prod[PP];
   for (int j = 0; j <= d; j++) {
-    const fr lo = ldx<COHERENT>(col[j] + k), hi = ldx<COHERENT>(col[j] + k + h);
+    fr lo, hi;
+    load(j, lo, hi);
     if (first) bad |= (!fr_is_canonical(lo)) | (!fr_is_canonical(hi));
     const fr dl = fr_sub(hi, lo);
     fr e = lo;
@@ -403,6 +405,19 @@ __device__ __forceinline__ void prod_pair(const ScRoundArgs& A, const fr* const*
 #pragma unroll
   for (int p = 0; p < PP; p++)
     if (p < pcnt) acc[p] = fr_add(acc[p], fr_mul(prod[p], w));
+}
+
+template <int PP, bool COHERENT>
+__device__ __forceinline__ void prod_pair(const ScRoundArgs& A, const fr* const* col, uint64_t k,
+                                          uint64_t h, int pcnt, const uint32_t (&tpt)[PP],
+                                          bool first, const fr& w, fr (&acc)[PP], uint32_t& bad) {
+  prod_pair_g<PP>(
+      A,
+      [&](int j, fr& lo, fr& hi) {
+        lo = ldx<COHERENT>(col[j] + k);
+        hi = ldx<COHERENT>(col[j] + k + h);
+      },
+      pcnt, tpt, first, w, acc, bad);
 }
 
 // Plonk round i >= 2 on a chunk of PB pairs, the work of each pair spread
@@ -722,6 +737,76 @@ __global__ void __launch_bounds__(256, PP == 1 ? 3 : 2) k_sc_prod_round(ScRoundA
   sc_finish_round(A, np);
 }
 
+// Product-gate round i >= 2 with the MLE update fused: each CTA first
+// folds the (d+1) columns of its spb pairs by alpha_{i-1} (all threads,
+// coalesced; written back and kept in shared memory), then evaluates them
+// from shared memory as k_sc_prod_round does.  Dynamic shared memory:
+// (d+1) x 2 x spb elements.
+template <int PP>
+__global__ void __launch_bounds__(256, 2) k_sc_prod_fused(ScRoundArgs A) {
+  extern __shared__ __align__(16) fr Vs[];
+  const int i = A.round;
+  const int d = (int)A.d, c = d + 1;
+  const bool full = A.full != 0;
+  const int np = full ? d + 1 : d;
+  const uint32_t p0 = full ? 0u : A.st->p0[i];
+  const int G = (np + PP - 1) / PP;
+  const int spb = (int)blockDim.x / G;
+  const int slot = (int)threadIdx.x / G, g = (int)threadIdx.x % G;
+  const int pbeg = g * PP, pcnt = max(0, min(PP, np - pbeg));
+  const uint32_t mlo = A.m_lo[i];
+  const fr* ehi = A.E + A.eq_hi[i];
+  const fr* elo = A.E + A.eq_lo[i];
+  const fr alpha = A.st->alpha[i - 1];
+  const uint64_t h = A.h;
+  uint32_t bad = 0;
+  fr acc[PP];
+  uint32_t tpt[PP];
+#pragma unroll
+  for (int p = 0; p < PP; p++) {
+    acc[p] = fr_zero();
+    tpt[p] = p < pcnt ? prod_point(pbeg + p, np, full, p0) : 0u;
+  }
+  for (uint64_t kb = (uint64_t)blockIdx.x * spb; kb < h; kb += (uint64_t)A.nwork * spb) {
+    for (int e = threadIdx.x; e < c * 2 * spb; e += blockDim.x) {
+      const int p = e % spb, rest = e / spb, half = rest & 1, j = rest >> 1;
+      const uint64_t k = kb + p;
+      if (k < h) {
+        const uint64_t idx = k + (half ? h : 0);
+        const fr x0 = ld_fr(A.src[j] + idx), x1 = ld_fr(A.src[j] + idx + 2 * h);
+        const fr v = fr_add(x0, fr_mul(alpha, fr_sub(x1, x0)));
+        st_fr(A.dst[j] + idx, v);
+        Vs[(size_t)rest * spb + p] = v;
+      }
+    }
+    __syncthreads();
+    const uint64_t k = kb + slot;
+    if (slot < spb && k < h) {
+      const fr w = fr_mul(ld_fr(ehi + (k >> mlo)), ld_fr(elo + (k & ((1ull << mlo) - 1))));
+      prod_pair_g<PP>(
+          A,
+          [&](int j, fr& lo, fr& hi) {
+            lo = Vs[(size_t)(2 * j) * spb + slot];
+            hi = Vs[(size_t)(2 * j + 1) * spb + slot];
+          },
+          pcnt, tpt, false, w, acc, bad);
+    }
+    __syncthreads();
+  }
+  __shared__ fr red[256][PP];
+#pragma unroll
+  for (int p = 0; p < PP; p++) red[threadIdx.x][p] = acc[p];
+  __syncthreads();
+  if ((int)threadIdx.x < np) {
+    const int q = threadIdx.x, gq = q / PP, pq = q % PP;
+    fr v = fr_zero();
+    for (int sl = 0; sl < spb; sl++) v = fr_add(v, red[sl * G + gq][pq]);
+    st_fr(A.partials + (size_t)blockIdx.x * np + q, v);
+  }
+  __syncthreads();
+  sc_finish_round(A, np);
+}
+
 // All rounds from A.round on, their challenges and the final values, in one
 // CTA of kTailThreads threads.  Tables are read with coherent loads: they
 // are rewritten between rounds inside this launch.
@@ -842,13 +927,36 @@ struct ScPlan {
   int grid_chunk, grid_quad;
   uint64_t quad_pairs;  // Plonk rounds 2.. in (chunk_pairs, quad_pairs]: 4 threads per pair
   int minb;  // Plonk round kernels: resident CTAs per SM they are compiled for
-  int ppt;   // product round kernel: points per thread (1 or kPP)
+  int ppt;   // product round kernel: points per thread (1 or kPP; 0: by round, prod_ppt)
+  bool prod_fused;  // product rounds 2..: fold inside the evaluation kernel
   uint32_t eq_total, eq_hi[kMaxN], eq_lo[kMaxN], mlo[kMaxN];
   EqTask tasks[2 * kMaxN];
 };
 
 // grid: most CTAs per round kernel (0: two per SM); tail_log: the tail takes
 // over at 2^tail_log pairs (0: the gate's default).
+// The fused product kernel takes up to 48 KB of dynamic shared memory on top
+// of its static arrays: opt in once per device.
+static void ensure_prod_fused_attr() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev < 0 || dev >= 64 || done[dev]) return;
+  cudaFuncSetAttribute(k_sc_prod_fused<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
+  cudaFuncSetAttribute(k_sc_prod_fused<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
+  done[dev] = true;
+}
+
+// Points per thread of a product round with np points over h pairs: one
+// (np threads per pair, most parallel) for small rounds and low degree, three
+// (extensions by additions, fewer redundant loads) for large high-degree rounds.
+static int prod_ppt(int forced, int np, uint64_t h) {
+  if (forced) return forced;
+  return (np <= 5 || h <= (1ull << 16)) ? 1 : 3;
+}
+
 // Resident CTAs per SM of a kernel on the current device (cached).
 static int resident_ctas(const void* fn, int threads = 256) {
   static std::mutex mu;
@@ -873,7 +981,7 @@ static const void* plonk_round_fn(int minb) {
 }
 
 static ScPlan sc_plan(const zc_params* p, int SMs, int grid = 0, int tail_log = 0, int small_log = 0,
-                      int minb = 0, int ppt = 0, int chunk_log = 0, int quad_log = 0) {
+                      int minb = 0, int ppt = 0, int chunk_log = 0, int quad_log = 0, int fuse = 0) {
   ScPlan P{};
   const uint32_t n = p->n, d = p->d;
   const bool plonk = p->gate == ZC_GATE_PLONK;
@@ -883,10 +991,12 @@ static ScPlan sc_plan(const zc_params* p, int SMs, int grid = 0, int tail_log = 
   // default: one wave of resident CTAs for the Plonk kernels (register bound,
   // one CTA per SM), two waves for the product kernel
   P.grid_plonk = grid > 0 ? grid : SMs * resident_ctas(plonk_round_fn(minb == 1 ? 1 : 2));
-  P.ppt = ppt == 1 ? 1 : 3;
+  P.ppt = ppt == 1 || ppt == 3 ? ppt : 0;  // 0: per round (see prod_ppt)
+  P.prod_fused = fuse == 2;
+  if (P.prod_fused) ensure_prod_fused_attr();
   P.grid_prod = grid > 0 ? grid
-                         : 2 * SMs * resident_ctas(P.ppt == 1 ? reinterpret_cast<const void*>(k_sc_prod_round<1>)
-                                                              : reinterpret_cast<const void*>(k_sc_prod_round<3>));
+                         : 2 * SMs * std::max(resident_ctas(reinterpret_cast<const void*>(k_sc_prod_round<1>)),
+                                              resident_ctas(reinterpret_cast<const void*>(k_sc_prod_round<3>)));
   P.tail_pairs = tail_log > 0 ? 1ull << tail_log : (plonk ? kTailPairsPlonk : kTailPairsProd);
   P.small_pairs = small_log > 0 ? 1ull << small_log : kSmallPairsPlonk;
   P.chunk_pairs = chunk_log > 0 ? 1ull << chunk_log : kChunkPairsPlonk;
@@ -1031,6 +1141,20 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
       }
       *launches += 1;
     } else {
+      if (i > 0 && P.prod_fused) {
+        // fold fused into the evaluation (rounds 2..)
+        const int npr = R.full ? (int)d + 1 : (int)d;
+        const int ppt = prod_ppt(P.ppt, npr, h);
+        const int G = (npr + ppt - 1) / ppt, spb = 256 / G;
+        R.nwork = (uint32_t)std::min<uint64_t>((h + spb - 1) / spb, (uint64_t)P.grid_prod);
+        const size_t dyn = sizeof(fr) * (size_t)(d + 1) * 2 * spb;
+        if (ppt == 1) k_sc_prod_fused<1><<<R.nwork, 256, dyn, st>>>(R);
+        else k_sc_prod_fused<3><<<R.nwork, 256, dyn, st>>>(R);
+        for (int j = 0; j < c; j++) cur[j] = B.tab[j];
+        *launches += 1;
+        if (i == 0 && ev) cudaEventRecord(ev[3], st);
+        continue;
+      }
       if (i > 0) {
         ScFoldArgs fa{};
         for (int j = 0; j < c; j++) {
@@ -1048,10 +1172,12 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
         for (int j = 0; j < c; j++) R.src[j] = cur[j];
         *launches += 1;
       }
-      const uint64_t slots_per_blk = 256 / (((R.full ? d + 1 : d) + P.ppt - 1) / P.ppt);
+      const int npr = R.full ? (int)d + 1 : (int)d;
+      const int ppt = prod_ppt(P.ppt, npr, h);
+      const uint64_t slots_per_blk = 256 / ((npr + ppt - 1) / ppt);
       R.nwork = (uint32_t)std::min<uint64_t>((h + slots_per_blk - 1) / slots_per_blk, (uint64_t)P.grid_prod);
       const uint32_t ctas = R.nwork + (i == 0 ? inv_cta : 0u);
-      if (P.ppt == 1) k_sc_prod_round<1><<<ctas, 256, 0, st>>>(R);
+      if (ppt == 1) k_sc_prod_round<1><<<ctas, 256, 0, st>>>(R);
       else k_sc_prod_round<3><<<ctas, 256, 0, st>>>(R);
       *launches += 1;
     }
@@ -1080,7 +1206,8 @@ size_t sumcheck_scratch_bytes(const zc_ctx* ctx, const zc_params* p) {
                            ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_MINB),
                            ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_PROD_PPT),
                            ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_CHUNK_LOG),
-                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_QUAD_LOG));
+                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_QUAD_LOG),
+                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_PROD_FUSE));
   const uint64_t N = 1ull << p->n;
   const size_t psize = 16 + 32 * ((size_t)p->n * (p->d + 2) + P.c);
   return align_up(sizeof(fr) * N, 256) * P.c + align_up(sizeof(fr) * sc_partials_count(P), 256) +
@@ -1098,7 +1225,8 @@ zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* col
                            ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_MINB),
                            ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_PROD_PPT),
                            ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_CHUNK_LOG),
-                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_QUAD_LOG));
+                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_QUAD_LOG),
+                           ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_PROD_FUSE));
   const int c = P.c;
   const uint64_t N = 1ull << n;
   const size_t psize = 16 + 32 * ((size_t)n * (d + 2) + c);
