@@ -288,15 +288,17 @@ zc_status zc_serve(zc_ctx* ctx, const zc_request* reqs, uint32_t count, const zc
  *   ZC_TUNE_SC_MINB      SumCheck, Plonk gate: resident CTAs per SM the large
  *                        round kernels are compiled for; 1 or 2, default 2.
  *   ZC_TUNE_SC_PROD_PPT  SumCheck, product gate: evaluation points per thread
- *                        in the large rounds; 1 or 3, default per round (1 for
- *                        at most 5 points or 2^16 pairs, else 3).
+ *                        in the large rounds; 1 or 3, default per round (3 for
+ *                        at most 3 points, 1 for 4-5 points or at most 2^16
+ *                        pairs, else 3).
  *   ZC_TUNE_SC_QUAD_LOG  SumCheck, Plonk gate: rounds 2.. above the chunk
  *                        threshold with at most 2^value pairs spread each pair
  *                        over 4 threads (larger rounds: one pair per thread);
  *                        1..24, default 17.
- *   ZC_TUNE_SC_PROD_FUSE SumCheck, product gate, rounds 2..: 1 = separate
- *                        MLE-update kernel, 2 = update fused into the
- *                        evaluation; default 1.
+ *   ZC_TUNE_SC_PROD_FUSE SumCheck, product gate: rounds 2.. with at most
+ *                        2^value pairs fold inside the evaluation kernel
+ *                        (larger rounds: a separate MLE-update kernel);
+ *                        1..24, default 16.
  *   ZC_TUNE_BATCH_LANES  batches: concurrent lanes (streams); set with n = 0
  *                        under either form; 1..64, default 16.
  *   ZC_TUNE_NTT_TILE_LOG NTT: elements per shared-memory pass tile, 2^value;

@@ -810,7 +810,7 @@ static bool tune_value_ok(zc_tune_key key, int32_t v) {
     case ZC_TUNE_SC_CHUNK_LOG: return v >= 1 && v <= 24;
     case ZC_TUNE_BATCH_LANES: return v >= 1 && v <= 64;
     case ZC_TUNE_SC_QUAD_LOG: return v >= 1 && v <= 24;
-    case ZC_TUNE_SC_PROD_FUSE: return v == 1 || v == 2;
+    case ZC_TUNE_SC_PROD_FUSE: return v >= 1 && v <= 24;
   }
   return false;
 }

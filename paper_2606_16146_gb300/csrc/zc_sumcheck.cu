@@ -42,10 +42,11 @@
 namespace zc {
 
 constexpr uint64_t kTailPairsPlonk = 32;
-constexpr uint64_t kTailPairsProd = 64;
+constexpr uint64_t kTailPairsProd = 32;
 constexpr uint64_t kSmallPairsPlonk = 1ull << 14;  // rounds with at most this many pairs evaluate H(0) and H(1)
 constexpr uint64_t kChunkPairsPlonk = 1ull << 14;  // Plonk rounds 2.. with at most this many: 16 threads per pair
 constexpr uint64_t kQuadPairsPlonk = 1ull << 17;   // and up to this many: 4 threads per pair
+constexpr uint64_t kFusePairsProd = 1ull << 16;    // product rounds 2.. with at most this many: fused update
 constexpr int kPP = 3;  // product gate: points per thread
 constexpr int kSmallPB = 16;  // pairs per chunk of the 16-threads-per-pair kernel (256 threads)
 constexpr int kQuadPB = 32;   // pairs per chunk of the 4-threads-per-pair kernel (128 threads)
@@ -928,7 +929,7 @@ struct ScPlan {
   uint64_t quad_pairs;  // Plonk rounds 2.. in (chunk_pairs, quad_pairs]: 4 threads per pair
   int minb;  // Plonk round kernels: resident CTAs per SM they are compiled for
   int ppt;   // product round kernel: points per thread (1 or kPP; 0: by round, prod_ppt)
-  bool prod_fused;  // product rounds 2..: fold inside the evaluation kernel
+  uint64_t fuse_pairs;  // product rounds 2.. with at most this many pairs fold inside the evaluation
   uint32_t eq_total, eq_hi[kMaxN], eq_lo[kMaxN], mlo[kMaxN];
   EqTask tasks[2 * kMaxN];
 };
@@ -949,11 +950,13 @@ static void ensure_prod_fused_attr() {
   done[dev] = true;
 }
 
-// Points per thread of a product round with np points over h pairs: one
-// (np threads per pair, most parallel) for small rounds and low degree, three
-// (extensions by additions, fewer redundant loads) for large high-degree rounds.
+// Points per thread of a product round with np points over h pairs: three
+// when that is one thread per pair (d = 2), else one (np threads per pair,
+// most parallel) for small rounds and 4-5 points, else three (extensions by
+// additions, fewer redundant loads) for large high-degree rounds.
 static int prod_ppt(int forced, int np, uint64_t h) {
   if (forced) return forced;
+  if (np <= 3) return 3;  // one thread per pair
   return (np <= 5 || h <= (1ull << 16)) ? 1 : 3;
 }
 
@@ -992,8 +995,8 @@ static ScPlan sc_plan(const zc_params* p, int SMs, int grid = 0, int tail_log = 
   // one CTA per SM), two waves for the product kernel
   P.grid_plonk = grid > 0 ? grid : SMs * resident_ctas(plonk_round_fn(minb == 1 ? 1 : 2));
   P.ppt = ppt == 1 || ppt == 3 ? ppt : 0;  // 0: per round (see prod_ppt)
-  P.prod_fused = fuse == 2;
-  if (P.prod_fused) ensure_prod_fused_attr();
+  P.fuse_pairs = fuse > 0 ? 1ull << fuse : kFusePairsProd;
+  ensure_prod_fused_attr();
   P.grid_prod = grid > 0 ? grid
                          : 2 * SMs * std::max(resident_ctas(reinterpret_cast<const void*>(k_sc_prod_round<1>)),
                                               resident_ctas(reinterpret_cast<const void*>(k_sc_prod_round<3>)));
@@ -1141,7 +1144,7 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
       }
       *launches += 1;
     } else {
-      if (i > 0 && P.prod_fused) {
+      if (i > 0 && h <= P.fuse_pairs) {
         // fold fused into the evaluation (rounds 2..)
         const int npr = R.full ? (int)d + 1 : (int)d;
         const int ppt = prod_ppt(P.ppt, npr, h);

@@ -20,7 +20,7 @@ SC_SPACE = {
     zc.ZC_TUNE_SC_GRID: (152, 304, 456, 608, 912),
     zc.ZC_TUNE_SC_MINB: (1, 2),
     zc.ZC_TUNE_SC_PROD_PPT: (1, 3),
-    zc.ZC_TUNE_SC_PROD_FUSE: (1, 2),
+    zc.ZC_TUNE_SC_PROD_FUSE: (1, 10, 14, 18, 24),
     zc.ZC_TUNE_SC_QUAD_LOG: (13, 15, 16, 17, 18),
     zc.ZC_TUNE_SC_CHUNK_LOG: (12, 13, 14, 16),
     zc.ZC_TUNE_SC_SMALL_LOG: (10, 12, 13, 14, 16),
