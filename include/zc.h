@@ -277,8 +277,8 @@ zc_status zc_serve(zc_ctx* ctx, const zc_request* reqs, uint32_t count, const zc
  *                        (the fold/evaluate split); 1..4096, default one wave
  *                        of resident CTAs (Plonk) or two (product gate).
  *   ZC_TUNE_SC_TAIL_LOG  SumCheck: the single-CTA tail takes over once a round
- *                        has at most 2^value pairs; 0..24, default 8 (Plonk
- *                        gate) or 6 (product gate).
+ *                        has at most 2^value pairs (the Plonk tail starts at
+ *                        round 2 at the earliest); 1..24, default 5.
  *   ZC_TUNE_SC_SMALL_LOG SumCheck: rounds 2.. with at most 2^value pairs
  *                        evaluate both H(0) and H(1) instead of deriving one
  *                        from the claim; 1..24, default 14.
