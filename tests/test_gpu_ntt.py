@@ -93,3 +93,12 @@ def test_product_config_n22_verified(ctx, d):
     p, q = ctx.prove_ntt(gate, n, d, to_device(cols))
     pb = proof_bytes(p)
     assert oracle.verify_ntt(gate, n, d, cols, pb, np.asarray(q))
+
+
+def test_largest_size_verified(ctx):
+    """n = 24 (M = 2^26), the largest NTT size: the oracle's verifier accepts
+    the GPU proof and the 2 GiB quotient."""
+    gate, n, d = 1, 24, 3
+    cols = witness.generate(gate, n, d, 6003)
+    p, q = ctx.prove_ntt(gate, n, d, to_device(cols))
+    assert oracle.verify_ntt(gate, n, d, cols, proof_bytes(p), np.asarray(q))

@@ -105,3 +105,10 @@ def test_product_gate_config_size(ctx, d):
 @pytest.mark.parametrize("d", [4, 8, 16])
 def test_product_gate_mid_degrees(ctx, d):
     _check(ctx, 2, 16, d, 2000 + d)
+
+
+@pytest.mark.parametrize("gate,d", [(1, 3), (2, 16)])
+def test_largest_served_size(ctx, gate, d):
+    """n = 24, the largest size of the served mix (Plonk, and the degree-16
+    product gate, the largest served degree): bit-exact against the oracle."""
+    _check(ctx, gate, 24, d, 6000 + d)
