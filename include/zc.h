@@ -303,6 +303,10 @@ zc_status zc_serve(zc_ctx* ctx, const zc_request* reqs, uint32_t count, const zc
  *                        under either form; 1..64, default 16.
  *   ZC_TUNE_NTT_TILE_LOG NTT: elements per shared-memory pass tile, 2^value;
  *                        10, 11 or 12, default 11.
+ *   ZC_TUNE_NTT_TWO_LOG  NTT: sizes 2^n with n >= value run each transform as
+ *                        two four-step passes (more, smaller CTAs), smaller
+ *                        ones as one pass (always two above n = 12); 2..24,
+ *                        default 12.
  *   ZC_TUNE_NTT_MINB     NTT: resident CTAs per SM the 2^11 tile is compiled
  *                        for; 1 or 2, default 2.
  *
@@ -320,7 +324,8 @@ typedef enum {
   ZC_TUNE_SC_CHUNK_LOG = 8,
   ZC_TUNE_BATCH_LANES = 9,
   ZC_TUNE_SC_QUAD_LOG = 10,
-  ZC_TUNE_SC_PROD_FUSE = 11
+  ZC_TUNE_SC_PROD_FUSE = 11,
+  ZC_TUNE_NTT_TWO_LOG = 12
 } zc_tune_key;
 
 zc_status zc_tune_set(zc_ctx* ctx, zc_form form, uint32_t n, zc_tune_key key, int32_t value);

@@ -635,6 +635,9 @@ void zc_destroy(zc_ctx* ctx) {
   cudaDeviceSynchronize();
   destroy_lanes(ctx);
   destroy_serve_pool(ctx);
+  for (cudaEvent_t e : ctx->up_ev) cudaEventDestroy(e);
+  if (ctx->up_fork) cudaEventDestroy(ctx->up_fork);
+  if (ctx->up_stream) cudaStreamDestroy(ctx->up_stream);
   if (ctx->arena.base) cudaFree(ctx->arena.base);
   for (auto& t : ctx->ntt_cache)
     if (t.mem) cudaFree(t.mem);
@@ -811,6 +814,7 @@ static bool tune_value_ok(zc_tune_key key, int32_t v) {
     case ZC_TUNE_BATCH_LANES: return v >= 1 && v <= 64;
     case ZC_TUNE_SC_QUAD_LOG: return v >= 1 && v <= 24;
     case ZC_TUNE_SC_PROD_FUSE: return v >= 1 && v <= 24;
+    case ZC_TUNE_NTT_TWO_LOG: return v >= 2 && v <= 24;
   }
   return false;
 }
@@ -821,7 +825,8 @@ static bool tune_form_ok(zc_form form, zc_tune_key key) {
     return key == ZC_TUNE_SC_GRID || key == ZC_TUNE_SC_TAIL_LOG || key == ZC_TUNE_SC_SMALL_LOG ||
            key == ZC_TUNE_SC_MINB || key == ZC_TUNE_SC_PROD_PPT || key == ZC_TUNE_SC_CHUNK_LOG ||
            key == ZC_TUNE_SC_QUAD_LOG || key == ZC_TUNE_SC_PROD_FUSE;
-  if (form == ZC_FORM_NTT) return key == ZC_TUNE_NTT_TILE_LOG || key == ZC_TUNE_NTT_MINB;
+  if (form == ZC_FORM_NTT)
+    return key == ZC_TUNE_NTT_TILE_LOG || key == ZC_TUNE_NTT_MINB || key == ZC_TUNE_NTT_TWO_LOG;
   return false;
 }
 

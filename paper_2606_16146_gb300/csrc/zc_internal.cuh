@@ -102,21 +102,22 @@ struct zc_ctx {
   uint32_t cur_n = 0;            // n of the proof being enqueued (selects tuned launch shapes)
   // launch parameters set by zc_tune_set: [form - 1][n][key - 1], 0 = unset;
   // n = 0 holds the value for sizes without their own entry
-  int32_t tune[2][zc::kMaxN + 1][11] = {};
+  int32_t tune[2][zc::kMaxN + 1][12] = {};
   int32_t tuned(zc_form form, uint32_t n, zc_tune_key key) const {
     const int f = (int)form - 1, k = (int)key - 1;
-    if (f < 0 || f > 1 || k < 0 || k > 10) return 0;
+    if (f < 0 || f > 1 || k < 0 || k > 11) return 0;
     if (n <= (uint32_t)zc::kMaxN && tune[f][n][k]) return tune[f][n][k];
     return tune[f][0][k];
   }
   // per-size NTT tables (twiddles, coset factors, quotient scale), built on
   // first use of a size; see zc_ntt.cu
   struct NttSizeTables {
-    uint32_t n = 0, lb = 0;
+    uint32_t n = 0, lb = 0, l1 = 0;
     void* mem = nullptr;
     size_t bytes = 0;
     uint64_t stamp = 0;
     zc::fr *tw_fwd = nullptr, *tw_inv = nullptr, *coset = nullptr, *outer = nullptr, *fin = nullptr;
+    zc::fr* zinv = nullptr;  // per slice: (7^N w_s^j - 1)^-1 M^-1, level 1
   };
   std::vector<NttSizeTables> ntt_cache;
   uint64_t ntt_cache_clock = 0;
@@ -132,6 +133,10 @@ struct zc_ctx {
   std::vector<cudaStream_t> lane_streams;
   std::vector<cudaEvent_t> lane_join;
   cudaEvent_t fork_ev = nullptr;
+  // pipelined uploads of host columns (NTT form)
+  cudaStream_t up_stream = nullptr;
+  cudaEvent_t up_fork = nullptr;
+  std::vector<cudaEvent_t> up_ev;
   // serving: one device pool that in-flight proofs take their scratch from
   void* serve_pool = nullptr;
   size_t serve_pool_cap = 0;

@@ -38,6 +38,7 @@ constexpr int kMaxNttN = 24;
 
 struct NttTables {
   bool ready = false;
+  fr w32h;                 // 7^((r-1)/2^32), canonical, host copy
   fr* dft_fwd = nullptr;   // w_4096^m, m < 4096 (level 1)
   fr* dft_inv = nullptr;
   fr* wf_lo = nullptr;     // w_2^30^b, b < 2^15 (level 1)
@@ -546,16 +547,20 @@ struct NttFinalArgs {
 };
 
 __global__ void k_ntt_final(NttFinalArgs A) {
-  const int item = threadIdx.x;
-  if (item <= A.c) {
+  // one warp per opening: lanes add strided block partials, then shuffles
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int item = threadIdx.x >> 5; item <= A.c; item += nw) {
     fr s = fr_zero();
-    for (uint32_t b = 0; b < A.nblk; b++) s = fr_add(s, ld_fr_cg(A.partials + (size_t)item * A.nblk + b));
-    if (item < A.c) s = fr_mul(s, A.ninv_l1);  // coefficients carry the factor N
-    uint8_t* o = A.proof + 52 + 32 * item;
-    for (int i = 0; i < 8; i++)
-      for (int b = 0; b < 4; b++) o[4 * i + b] = (uint8_t)(s.v[i] >> (8 * b));
+    for (uint32_t b = lane; b < A.nblk; b += 32) s = fr_add(s, ld_fr_cg(A.partials + (size_t)item * A.nblk + b));
+    s = warp_sum(s);
+    if (lane == 0) {
+      if (item < A.c) s = fr_mul(s, A.ninv_l1);  // coefficients carry the factor N
+      uint8_t* o = A.proof + 52 + 32 * item;
+      for (int i = 0; i < 8; i++)
+        for (int b = 0; b < 4; b++) o[4 * i + b] = (uint8_t)(s.v[i] >> (8 * b));
+    }
   }
-  if (item == 0) {
+  if (threadIdx.x == 0) {
     const char* mg = A.st->err ? "ZCE!" : "ZCN1";
     for (int b = 0; b < 4; b++) A.proof[b] = (uint8_t)mg[b];
     uint32_t hv[4] = {A.gate, A.n, A.d, A.logm};
@@ -622,6 +627,7 @@ static zc_status ensure_tables(zc_ctx* ctx, cudaStream_t st, NttTables** out) {
         if ((e[i] >> b) & 1) acc = h_canon_mul(acc, base, C);
         base = h_canon_mul(base, base, C);
       }
+    T.w32h = acc;
     fr w30 = h_canon_mul(acc, acc, C);
     w30 = h_canon_mul(w30, w30, C);
     NttTabArgs a{};
@@ -702,11 +708,12 @@ static zc_ctx::NttSizeTables* size_tables(zc_ctx* user, const NttTables* T, uint
   zc_ctx* ctx = user->table_owner ? user->table_owner : user;
   const uint64_t N = 1ull << n, M = N << lb;
   for (auto& e : ctx->ntt_cache)
-    if (e.n == n && e.lb == lb) {
+    if (e.n == n && e.lb == lb && e.l1 == l1) {
       e.stamp = ++ctx->ntt_cache_clock;
       return &e;
     }
-  const size_t bytes = sizeof(fr) * (2 * N + 3 * M);
+  const uint64_t s = 1ull << lb;
+  const size_t bytes = sizeof(fr) * (2 * N + 3 * M + s);
   if (ctx->ntt_cache_frozen || bytes > ctx->ntt_cache_budget) return nullptr;
   size_t used = 0;
   for (auto& e : ctx->ntt_cache) used += e.bytes;
@@ -726,13 +733,34 @@ static zc_ctx::NttSizeTables* size_tables(zc_ctx* user, const NttTables* T, uint
   }
   e.n = n;
   e.lb = lb;
+  e.l1 = l1;
   e.bytes = bytes;
   fr* q = static_cast<fr*>(e.mem);
   e.tw_fwd = q; q += N;
   e.tw_inv = q; q += N;
   e.coset = q; q += M;
   e.outer = q; q += M;
-  e.fin = q;
+  e.fin = q; q += M;
+  e.zinv = q;
+  {
+    // (z_H on slice j)^-1 M^-1 = (7^N w_s^j - 1)^-1 M^-1, level 1, on the host
+    const DevConst& C = ctx->hconst;
+    const fr ws = h_pow(T->w32h, (1ull << 32) >> lb, C);
+    const fr s7n = h_pow(h_from_u64(7), N, C), minv = h_inv(h_from_u64(M), C);
+    std::vector<fr> zi(s);
+    fr wj = h_from_u64(1);
+    for (uint64_t j = 0; j < s; j++) {
+      const fr v = fr_sub_g(h_canon_mul(s7n, wj, C), h_from_u64(1));
+      zi[j] = h_canon_mul(h_canon_mul(h_inv(v, C), minv, C), C.one, C);
+      wj = h_canon_mul(wj, ws, C);
+    }
+    if (cudaMemcpyAsync(e.zinv, zi.data(), sizeof(fr) * s, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(e.mem);
+      return nullptr;
+    }
+  }
   NttSizeArgs a{};
   a.tw_fwd = e.tw_fwd;
   a.tw_inv = e.tw_inv;
@@ -786,13 +814,46 @@ size_t ntt_scratch_bytes(const zc_params* p, int sm_count, bool q_direct) {
   return need;
 }
 
+// Side stream and per-column events for pipelined uploads of host columns
+// (created on first use, freed by zc_destroy).
+static zc_status ensure_upload_stream(zc_ctx* ctx, int c) {
+  if (!ctx->up_stream) {
+    if (cudaStreamCreateWithFlags(&ctx->up_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->up_fork, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->err = "cannot create the upload stream";
+      return ZC_ERR_CUDA;
+    }
+  }
+  while ((int)ctx->up_ev.size() < c) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->err = "cannot create an upload event";
+      return ZC_ERR_CUDA;
+    }
+    ctx->up_ev.push_back(e);
+  }
+  return ZC_OK;
+}
+
+// Transforms of 2^n points run as two four-step passes (sub-DFTs of
+// 2^ceil(n/2) and 2^floor(n/2) points) from n = 12 on (a single pass holds at
+// most 2^12 points; at 2^12 the two passes' extra CTAs already win), or from
+// a tuned size, else as one pass per transform.
+static bool ntt_two_pass(const zc_ctx* ctx, uint32_t n) {
+  if (n > 12) return true;  // one pass holds at most a 2^12 transform
+  const int32_t t = ctx->tuned(ZC_FORM_NTT, n, ZC_TUNE_NTT_TWO_LOG);
+  return n >= (uint32_t)(t > 0 ? t : 12) && n >= 2;
+}
+
 zc_status ntt_prepare(zc_ctx* ctx, const zc_params* p, cudaStream_t st) {
   ensure_pass_attributes(ctx->device);
   NttTables* T = nullptr;
   zc_status s0 = ensure_tables(ctx, st, &T);
   if (s0 != ZC_OK) return s0;
   const uint32_t n = p->n, lb = ntt_log_blowup(p);
-  const bool two = n > 12;
+  const bool two = ntt_two_pass(ctx, n);
   size_tables(ctx, T, n, lb, two ? (n + 1) / 2 : n, two ? n / 2 : 0, st);
   return cudaStreamSynchronize(st) == cudaSuccess ? ZC_OK : ZC_ERR_CUDA;
 }
@@ -850,9 +911,55 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
   ctx->launches = 0;
   ctx->nev = 7;
 
+  const bool two = ntt_two_pass(ctx, n);
+  const uint32_t l1 = two ? (n + 1) / 2 : n;   // first digit
+  const uint32_t l2 = two ? n / 2 : 0;         // second digit
+  const uint64_t L1 = 1ull << l1, L2 = 1ull << l2;
+  zc_status rs;
+  zc_ctx::NttSizeTables* ST = size_tables(ctx, T, n, lb, l1, l2, st);
+
+  // N1's first pass (rows over i2, twiddled) for the columns [j0, j1)
+  auto n1_first = [&](const fr* const* in, int j0, int j1) -> zc_status {
+    NttPassArgs a;
+    pass_defaults(a);
+    for (int j = j0; j < j1; j++) {
+      a.in[j - j0] = in[j];
+      a.out[j - j0] = coef[j];
+    }
+    a.logL = l2;                       // rows of length L2 over i2
+    a.in_bs_lo = 1; a.in_ts = L1;      // element (i1, i2) read from e[i1 + L1 i2]
+    a.out_bs_lo = L2; a.out_ts = 1;
+    a.dft = T->dft_inv;
+    a.post = POST_TW; a.tw_lo = T->wi_lo; a.tw_hi = T->wi_hi;
+    a.tw_lbmod = l1; a.tw_shift = kLog30 - n;
+    if (ST) {  // w_N^-(i1 k2) = tw_inv[i1 L2 + k2]
+      a.post = POST_TAB; a.post_tab = ST->tw_inv;
+      a.p_lbdiv = 63; a.p_ls = L2; a.p_ts = 1;
+    }
+    return run_pass(ctx, st, a, j1 - j0, L1);
+  };
+
+  // Host columns: uploaded one by one on a side stream; with two passes the
+  // first N1 pass of column j starts as soon as column j has arrived.
   const fr* src[kMaxCols];
+  const bool pipelined = !on_dev && two;
   if (on_dev) {
     for (int j = 0; j < c; j++) src[j] = static_cast<const fr*>(cols[j]);
+  } else if (pipelined) {
+    zc_status us = ensure_upload_stream(ctx, c);
+    if (us != ZC_OK) return us;
+    ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->up_fork, st));
+    ZC_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->up_stream, ctx->up_fork, 0));
+    for (int j = 0; j < c; j++) {
+      ZC_CUDA_TRY(ctx, cudaMemcpyAsync(slb[j], cols[j], N * sizeof(fr), cudaMemcpyHostToDevice,
+                                       ctx->up_stream));
+      ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->up_ev[j], ctx->up_stream));
+      src[j] = slb[j];
+    }
+    for (int j = 0; j < c; j++) {
+      ZC_CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->up_ev[j], 0));
+      if ((rs = n1_first(src, j, j + 1)) != ZC_OK) return rs;
+    }
   } else {
     for (int j = 0; j < c; j++) {
       ZC_CUDA_TRY(ctx, cudaMemcpyAsync(slb[j], cols[j], N * sizeof(fr), cudaMemcpyHostToDevice, st));
@@ -881,10 +988,10 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
   }
   ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[1], st));
 
-  // per-slice coset tables and z_H inverses
+  // per-slice coset tables and z_H inverses (only without per-size tables)
   const DevConst& C = ctx->hconst;
   fr ninv = h_inv(h_from_u64(N), C), minv = h_inv(h_from_u64(M), C);
-  {
+  if (!ST) {
     NttSliceTabArgs ta{};
     ta.lo = tlo;
     ta.hi = thi;
@@ -903,32 +1010,10 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
     ctx->launches++;
   }
 
-  const bool two = n > 12;
-  const uint32_t l1 = two ? (n + 1) / 2 : n;   // first digit
-  const uint32_t l2 = two ? n / 2 : 0;         // second digit
-  const uint64_t L1 = 1ull << l1, L2 = 1ull << l2;
-  zc_status rs;
-  zc_ctx::NttSizeTables* ST = size_tables(ctx, T, n, lb, l1, l2, st);
-
   // ---- N1: g_j = DFT^-1(e_j) (the factor 1/N is applied later), natural out
   if (two) {
+    if (!pipelined && (rs = n1_first(src, 0, c)) != ZC_OK) return rs;
     NttPassArgs a;
-    pass_defaults(a);
-    for (int j = 0; j < c; j++) {
-      a.in[j] = src[j];
-      a.out[j] = coef[j];
-    }
-    a.logL = l2;                       // rows of length L2 over i2
-    a.in_bs_lo = 1; a.in_ts = L1;      // element (i1, i2) read from e[i1 + L1 i2]
-    a.out_bs_lo = L2; a.out_ts = 1;
-    a.dft = T->dft_inv;
-    a.post = POST_TW; a.tw_lo = T->wi_lo; a.tw_hi = T->wi_hi;
-    a.tw_lbmod = l1; a.tw_shift = kLog30 - n;
-    if (ST) {  // w_N^-(i1 k2) = tw_inv[i1 L2 + k2]
-      a.post = POST_TAB; a.post_tab = ST->tw_inv;
-      a.p_lbdiv = 63; a.p_ls = L2; a.p_ts = 1;
-    }
-    if ((rs = run_pass(ctx, st, a, c, L1)) != ZC_OK) return rs;
     pass_defaults(a);
     for (int j = 0; j < c; j++) {
       a.in[j] = coef[j];
@@ -1005,7 +1090,7 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
     NttGateArgs ga{};
     for (int i = 0; i < c; i++) ga.col[i] = slb[i];
     ga.qhat = qhat + j * N;
-    ga.zinv = zinv + j;
+    ga.zinv = (ST ? ST->zinv : zinv) + j;
     ga.N = N;
     ga.gate = gate;
     ga.d = d;
@@ -1075,6 +1160,15 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
     if ((rs = run_pass(ctx, st, a, 1, N)) != ZC_OK) return rs;
   }
   ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[4], st));
+  // a host q leaves on the side stream while the root and the openings run
+  const bool q_async = q_out && !q_direct && !q_on_dev;
+  if (q_async) {
+    zc_status us = ensure_upload_stream(ctx, 1);
+    if (us != ZC_OK) return us;
+    ZC_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->up_stream, ctx->ev[4], 0));
+    ZC_CUDA_TRY(ctx, cudaMemcpyAsync(q_out, qv, M * sizeof(fr), cudaMemcpyDeviceToHost, ctx->up_stream));
+    ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->up_ev[0], ctx->up_stream));
+  }
 
   // ---- N4: root(q), z
   {
@@ -1120,15 +1214,18 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
     fa.qroot = droots + 32 * (size_t)c;
     fa.st = dstate;
     fa.proof = dproof;
-    k_ntt_final<<<1, 128, 0, st>>>(fa);
+    k_ntt_final<<<1, 256, 0, st>>>(fa);
     ctx->launches++;
   }
   ZC_CUDA_TRY(ctx, cudaGetLastError());
   ZC_CUDA_TRY(ctx, cudaMemcpyAsync(proof, dproof, psize,
                                    proof_on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                    st));
-  if (q_out && !q_direct)
+  if (q_async) {
+    ZC_CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->up_ev[0], 0));
+  } else if (q_out && !q_direct) {
     ZC_CUDA_TRY(ctx, cudaMemcpyAsync(q_out, qv, M * sizeof(fr), cudaMemcpyDeviceToHost, st));
+  }
   ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[6], st));
   // dominant launch: one N2 column pass over all c columns of a slice
   const double Lc = two ? (double)l1 : (double)n;

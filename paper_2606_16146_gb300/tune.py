@@ -28,6 +28,7 @@ SC_SPACE = {
 }
 BATCH_LANES = (8, 16, 32, 64)
 NTT_SPACE = {
+    zc.ZC_TUNE_NTT_TWO_LOG: (6, 8, 10, 12, 13),
     zc.ZC_TUNE_NTT_TILE_LOG: (10, 11, 12),
     zc.ZC_TUNE_NTT_MINB: (1, 2),
 }

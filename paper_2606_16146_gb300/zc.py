@@ -25,7 +25,7 @@ ZC_GATE_PLONK, ZC_GATE_PRODUCT = 1, 2
 ZC_FORM_SUMCHECK, ZC_FORM_NTT = 1, 2
 ZC_TUNE_SC_GRID, ZC_TUNE_SC_TAIL_LOG, ZC_TUNE_NTT_TILE_LOG, ZC_TUNE_NTT_MINB = 1, 2, 3, 4
 ZC_TUNE_SC_SMALL_LOG, ZC_TUNE_SC_MINB, ZC_TUNE_SC_PROD_PPT, ZC_TUNE_SC_CHUNK_LOG = 5, 6, 7, 8
-ZC_TUNE_BATCH_LANES, ZC_TUNE_SC_QUAD_LOG, ZC_TUNE_SC_PROD_FUSE = 9, 10, 11
+ZC_TUNE_BATCH_LANES, ZC_TUNE_SC_QUAD_LOG, ZC_TUNE_SC_PROD_FUSE, ZC_TUNE_NTT_TWO_LOG = 9, 10, 11, 12
 
 
 class ZCError(RuntimeError):

@@ -37,19 +37,20 @@ def test_sumcheck_candidates_same_bytes(ctx, gate, n, d):
         ctx.tune_set(zc.ZC_FORM_SUMCHECK, n, k, 0)
 
 
-@pytest.mark.parametrize("gate,n,d", [(1, 14, 3), (2, 13, 5)])
+@pytest.mark.parametrize("gate,n,d", [(1, 14, 3), (2, 13, 5), (1, 9, 3), (2, 6, 8)])
 def test_ntt_candidates_same_bytes(ctx, gate, n, d):
     cols = witness.generate(gate, n, d, 8200 + n)
     want_p, want_q = oracle.prove_ntt(gate, n, d, cols)
     dc = to_device(cols)
     cands = [{zc.ZC_TUNE_NTT_TILE_LOG: t, zc.ZC_TUNE_NTT_MINB: m} for t in (10, 11, 12) for m in (1, 2)]
+    cands += [{zc.ZC_TUNE_NTT_TWO_LOG: v} for v in (2, 4, 6, 9, 13, 24)]
     for cand in cands:
-        for k in (zc.ZC_TUNE_NTT_TILE_LOG, zc.ZC_TUNE_NTT_MINB):
+        for k in (zc.ZC_TUNE_NTT_TILE_LOG, zc.ZC_TUNE_NTT_MINB, zc.ZC_TUNE_NTT_TWO_LOG):
             ctx.tune_set(zc.ZC_FORM_NTT, n, k, cand.get(k, 0))
         p, q = ctx.prove_ntt(gate, n, d, dc)
         assert proof_bytes(p) == want_p, cand
         assert proof_bytes(q) == want_q.tobytes(), cand
-    for k in (zc.ZC_TUNE_NTT_TILE_LOG, zc.ZC_TUNE_NTT_MINB):
+    for k in (zc.ZC_TUNE_NTT_TILE_LOG, zc.ZC_TUNE_NTT_MINB, zc.ZC_TUNE_NTT_TWO_LOG):
         ctx.tune_set(zc.ZC_FORM_NTT, n, k, 0)
 
 
