@@ -424,6 +424,33 @@ def run_sweep(args, world, rank, local):
     ctx.close()
 
 
+def run_mulpeak(args, world, rank, local):
+    """Throughput ceiling of the field multiplication alone (csrc/mul_ceiling.cu):
+    products/s of the kernels' multiplier and its variants, and the per-
+    instruction rates they are built from, against the ALU roofline's peak."""
+    import subprocess
+    from paper_2606_16146_gb300 import build
+    exe = build.build_mul_ceiling()
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES=os.environ.get("CUDA_VISIBLE_DEVICES", str(local)))
+    clocks = ClockSampler(local)
+    clocks.start()
+    out = subprocess.run([exe], check=True, capture_output=True, text=True, env=env).stdout
+    clk = clocks.stop()
+    res = json.loads(out.strip().splitlines()[-1])
+    best = res["mulmod_per_s"]["fr_mul_call"]
+    config = {"workload": "field multiplication alone: 152 SMs x 8 CTAs x 256 threads, two dependent "
+                          "product chains per thread, BLS12-381 Fr Montgomery (8 x 32-bit limbs)"}
+    line = _base_line(args, world, best, "mulmod/s", True, config)
+    line["value_is"] = "fr_mul (the kernels' out-of-line multiplier) products per second"
+    line["alu_roofline_peak_mulmod_s"] = ALU_PEAK_MULMOD
+    line["frac_of_alu_roofline"] = {k: v / ALU_PEAK_MULMOD for k, v in res["mulmod_per_s"].items()}
+    line["result"] = res
+    line["clocks"] = clk
+    line["e2e"] = None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_served(args, world, rank, local):
     """Poisson request loop (n 12..24, d in {3, 8, 16}), admission by HBM
     footprint against a 180 GB pool, cost-model routing; against the same
@@ -500,9 +527,10 @@ def main():
     ap.add_argument("--gate", type=int, default=1, choices=[1, 2])
     ap.add_argument("--form", default="both", choices=["both", "sumcheck", "ntt"],
                     help="restrict the step to one form (profiling); the bench line uses both")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "served", "sweep"],
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "served", "sweep", "mulpeak"],
                     help="plain: one Plonk n=22 proof per form (the headline line); batched: 64 "
-                         "mixed instances in one graph; served: Poisson request loop")
+                         "mixed instances in one graph; served: Poisson request loop; sweep: "
+                         "sizes and degrees; mulpeak: the field multiplication alone")
     ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="served: arrival rates (req/s)")
     ap.add_argument("--requests", type=int, default=200, help="served: requests per rate")
     args = ap.parse_args()
@@ -523,6 +551,9 @@ def main():
         return
     if args.workload == "sweep":
         run_sweep(args, world, rank, local)
+        return
+    if args.workload == "mulpeak":
+        run_mulpeak(args, world, rank, local)
         return
     import torch
     from paper_2606_16146_gb300 import witness, zc
