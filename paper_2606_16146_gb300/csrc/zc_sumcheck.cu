@@ -177,6 +177,7 @@ struct ChalSmem {
   fr alpha;
   uint32_t msg[8 + 8 * kMaxPts];
 };
+static_assert(2 * kMaxPts >= 32, "tmp holds one partial sum per warp of a 1024-thread CTA");
 
 // Finish round `i` from the sums Hc (shared memory, np values): either all
 // of H(0..d-1) and H(inf) (np = d + 1) or H(p0), H(2..d-1), H(inf) (np = d,
@@ -279,14 +280,36 @@ __device__ void sc_finish_round(const ScRoundArgs& A, int np) {
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int p = warp; p < np; p += nw) {
+  // G warps share each point; every lane issues its L2 loads four at a time,
+  // so the sum costs a few L2 round trips however many CTAs wrote partials.
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+  const int G = np < nw ? nw / np : 1, per_pass = nw / G;
+  fr* W = &S.tmp[0][0];  // nw <= 2 kMaxPts partial sums, free until the challenge
+  for (int base = 0; base < np; base += per_pass) {
+    const int p = base + warp / G, g = warp % G;
     fr s = fr_zero();
-    for (uint32_t b = lane; b < A.nwork; b += 32) s = fr_add(s, ld_fr_l2(A.partials + (size_t)b * np + p));
+    if (warp / G < per_pass && p < np) {
+      const uint32_t stride = 32u * G;
+      uint32_t b = lane + 32u * g;
+      for (; b + 3 * stride < A.nwork; b += 4 * stride) {
+        const fr x0 = ld_fr_l2(A.partials + (size_t)b * np + p);
+        const fr x1 = ld_fr_l2(A.partials + (size_t)(b + stride) * np + p);
+        const fr x2 = ld_fr_l2(A.partials + (size_t)(b + 2 * stride) * np + p);
+        const fr x3 = ld_fr_l2(A.partials + (size_t)(b + 3 * stride) * np + p);
+        s = fr_add(s, fr_add(fr_add(x0, x1), fr_add(x2, x3)));
+      }
+      for (; b < A.nwork; b += stride) s = fr_add(s, ld_fr_l2(A.partials + (size_t)b * np + p));
+    }
     s = warp_sum(s);
-    if (lane == 0) S.Hc[p] = s;
+    if (lane == 0) W[warp] = s;
+    __syncthreads();
+    if (t < per_pass && base + t < np) {
+      fr v = W[t * G];
+      for (int q = 1; q < G; q++) v = fr_add(v, W[t * G + q]);
+      S.Hc[base + t] = v;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   sc_challenge(S, np, (int)A.d, A.round, A.st, A.proof, A.C, A.tabs, A.next_derives != 0);
 }
 
