@@ -92,6 +92,7 @@ struct ScRoundArgs {
   int n, c;
   uint32_t gate, d;
   int G;               // product gate: threads per pair
+  uint32_t spb;        // product gate: pairs per CTA (at most 256 / threads per pair)
   uint32_t nwork;      // CTAs that evaluate pairs (round 1 may add one for the inverses)
   uint32_t full;       // evaluate H at all of 0..d-1 (no point derived from the claim)
   uint32_t next_derives;  // the next round derives a point: keep the claim
@@ -709,6 +710,20 @@ __global__ void __launch_bounds__(256) k_sc_fold(ScFoldArgs A) {
   }
 }
 
+// A product CTA's partial sums: point q is the sum of red[sl G + q / PP][q % PP]
+// over its spb pair slots.  Warps take points, lanes take slots.
+template <int PP>
+__device__ __forceinline__ void prod_cta_sums(const fr (&red)[256][PP], int np, int G, int spb, fr* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int q = warp; q < np; q += nw) {
+    const int gq = q / PP, pq = q % PP;
+    fr v = fr_zero();
+    for (int sl = lane; sl < spb; sl += 32) v = fr_add(v, red[sl * G + gq][pq]);
+    v = warp_sum(v);
+    if (lane == 0) st_fr(out + q, v);
+  }
+}
+
 // Product-gate evaluation of one large round (columns already folded): G =
 // ceil(np / PP) threads per pair, each evaluating up to PP consecutive
 // points (the extensions lo + t (hi - lo) advance by one addition per
@@ -726,7 +741,7 @@ __global__ void __launch_bounds__(256, PP == 1 ? 3 : 2) k_sc_prod_round(ScRoundA
   const int np = full ? d + 1 : d;
   const uint32_t p0 = full ? 0u : A.st->p0[i];
   const int G = (np + PP - 1) / PP;
-  const int spb = (int)blockDim.x / G;
+  const int spb = (int)A.spb;
   const int slot = (int)threadIdx.x / G, g = (int)threadIdx.x % G;
   const int pbeg = g * PP, pcnt = max(0, min(PP, np - pbeg));
   const uint32_t mlo = A.m_lo[i];
@@ -751,12 +766,7 @@ __global__ void __launch_bounds__(256, PP == 1 ? 3 : 2) k_sc_prod_round(ScRoundA
 #pragma unroll
   for (int p = 0; p < PP; p++) red[threadIdx.x][p] = acc[p];
   __syncthreads();
-  if ((int)threadIdx.x < np) {
-    const int q = threadIdx.x, gq = q / PP, pq = q % PP;
-    fr v = fr_zero();
-    for (int sl = 0; sl < spb; sl++) v = fr_add(v, red[sl * G + gq][pq]);
-    st_fr(A.partials + (size_t)blockIdx.x * np + q, v);
-  }
+  prod_cta_sums<PP>(red, np, G, spb, A.partials + (size_t)blockIdx.x * np);
   __syncthreads();
   sc_finish_round(A, np);
 }
@@ -775,7 +785,7 @@ __global__ void __launch_bounds__(256, 2) k_sc_prod_fused(ScRoundArgs A) {
   const int np = full ? d + 1 : d;
   const uint32_t p0 = full ? 0u : A.st->p0[i];
   const int G = (np + PP - 1) / PP;
-  const int spb = (int)blockDim.x / G;
+  const int spb = (int)A.spb;
   const int slot = (int)threadIdx.x / G, g = (int)threadIdx.x % G;
   const int pbeg = g * PP, pcnt = max(0, min(PP, np - pbeg));
   const uint32_t mlo = A.m_lo[i];
@@ -821,12 +831,7 @@ __global__ void __launch_bounds__(256, 2) k_sc_prod_fused(ScRoundArgs A) {
 #pragma unroll
   for (int p = 0; p < PP; p++) red[threadIdx.x][p] = acc[p];
   __syncthreads();
-  if ((int)threadIdx.x < np) {
-    const int q = threadIdx.x, gq = q / PP, pq = q % PP;
-    fr v = fr_zero();
-    for (int sl = 0; sl < spb; sl++) v = fr_add(v, red[sl * G + gq][pq]);
-    st_fr(A.partials + (size_t)blockIdx.x * np + q, v);
-  }
+  prod_cta_sums<PP>(red, np, G, spb, A.partials + (size_t)blockIdx.x * np);
   __syncthreads();
   sc_finish_round(A, np);
 }
@@ -973,14 +978,16 @@ static void ensure_prod_fused_attr() {
   done[dev] = true;
 }
 
-// Points per thread of a product round with np points over h pairs: three
-// when that is one thread per pair (d = 2), else one (np threads per pair,
-// most parallel) for small rounds and 4-5 points, else three (extensions by
-// additions, fewer redundant loads) for large high-degree rounds.
+// Points per thread of a product round with np points over h pairs: one
+// (np threads per pair, the shortest chain) in small rounds, which are
+// latency-bound; in large rounds three when that is one thread per pair
+// (d = 2), one for 4-5 points, else three (extensions by additions, fewer
+// redundant loads).
 static int prod_ppt(int forced, int np, uint64_t h) {
   if (forced) return forced;
-  if (np <= 3) return 3;  // one thread per pair
-  return (np <= 5 || h <= (1ull << 16)) ? 1 : 3;
+  if (h <= (1ull << 16)) return 1;  // small rounds: shortest per-thread chain
+  if (np <= 3) return 3;            // one thread per pair
+  return np <= 5 ? 1 : 3;
 }
 
 // Resident CTAs per SM of a kernel on the current device (cached).
@@ -1171,7 +1178,9 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
         // fold fused into the evaluation (rounds 2..)
         const int npr = R.full ? (int)d + 1 : (int)d;
         const int ppt = prod_ppt(P.ppt, npr, h);
-        const int G = (npr + ppt - 1) / ppt, spb = 256 / G;
+        // at most two fold items per thread: the round is latency-bound
+        const int G = (npr + ppt - 1) / ppt, spb = std::max(1, std::min(256 / G, 256 / c));
+        R.spb = (uint32_t)spb;
         R.nwork = (uint32_t)std::min<uint64_t>((h + spb - 1) / spb, (uint64_t)P.grid_prod);
         const size_t dyn = sizeof(fr) * (size_t)(d + 1) * 2 * spb;
         if (ppt == 1) k_sc_prod_fused<1><<<R.nwork, 256, dyn, st>>>(R);
@@ -1201,6 +1210,7 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
       const int npr = R.full ? (int)d + 1 : (int)d;
       const int ppt = prod_ppt(P.ppt, npr, h);
       const uint64_t slots_per_blk = 256 / ((npr + ppt - 1) / ppt);
+      R.spb = (uint32_t)slots_per_blk;
       R.nwork = (uint32_t)std::min<uint64_t>((h + slots_per_blk - 1) / slots_per_blk, (uint64_t)P.grid_prod);
       const uint32_t ctas = R.nwork + (i == 0 ? inv_cta : 0u);
       if (ppt == 1) k_sc_prod_round<1><<<ctas, 256, 0, st>>>(R);
