@@ -130,16 +130,17 @@ __device__ __forceinline__ fr ldx(const fr* p) {
   return COHERENT ? ld_fr_l2(p) : ld_fr(p);
 }
 
-// small integer t times x by double-and-add (t < 128), additions only
+// small integer t times x by double-and-add, additions only.  The lanes of a
+// warp may hold different t, so the loop starts at the highest bit set in
+// any of them: a warp whose t are at most 6 runs two steps, not seven.
 __device__ __forceinline__ fr fr_mul_small(const fr& x, uint32_t t) {
-  fr acc = fr_zero();
-  bool started = false;
-  for (int b = 6; b >= 0; b--) {
-    if (started) acc = fr_add(acc, acc);
-    if ((t >> b) & 1) {
-      acc = started ? fr_add(acc, x) : x;
-      started = true;
-    }
+  const uint32_t any = __reduce_or_sync(__activemask(), t);
+  if (any == 0) return fr_zero();
+  const int top = 31 - __clz(any);
+  fr acc = ((t >> top) & 1) ? x : fr_zero();
+  for (int b = top - 1; b >= 0; b--) {
+    acc = fr_add(acc, acc);
+    if ((t >> b) & 1) acc = fr_add(acc, x);
   }
   return acc;
 }
@@ -403,6 +404,13 @@ __device__ __forceinline__ void prod_pair_g(const ScRoundArgs& A, Load load, int
     fr lo, hi;
     load(j, lo, hi);
     if (first) bad |= (!fr_is_canonical(lo)) | (!fr_is_canonical(hi));
+    // o enters at level 0 and is brought to level 1-d by kcomp: with several
+    // points per thread, scale the two ends once instead of every point
+    const bool oscale = PP > 1 && j == d && pcnt >= 2;
+    if (oscale) {
+      lo = fr_mul(lo, A.kcomp);
+      hi = fr_mul(hi, A.kcomp);
+    }
     const fr dl = fr_sub(hi, lo);
     fr e = lo;
     uint32_t tcur = 0;
@@ -420,8 +428,8 @@ __device__ __forceinline__ void prod_pair_g(const ScRoundArgs& A, Load load, int
         x = e;
       }
       if (j == d) {
-        // o enters at level 0; bring it to level 1-d.  Infinity has no o term.
-        if (tpt[p] != kInf) prod[p] = fr_sub(prod[p], fr_mul(x, A.kcomp));
+        // infinity has no o term
+        if (tpt[p] != kInf) prod[p] = fr_sub(prod[p], oscale ? x : fr_mul(x, A.kcomp));
       } else {
         prod[p] = j == 0 ? x : fr_mul(prod[p], x);
       }
