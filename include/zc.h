@@ -21,7 +21,16 @@
  *   ZC_GATE_PLONK   (d = 3, c = 8): [qL, qR, qM, qO, qC, a, b, c],
  *                   f = qL a + qR b + qM a b + qO c + qC;
  *   ZC_GATE_PRODUCT (d >= 2, c = d + 1): [q, w1, ..., w_{d-1}, o],
- *                   f = q w1 ... w_{d-1} - o.
+ *                   f = q w1 ... w_{d-1} - o;
+ *   ZC_GATE_SUM_OF(m) (d >= 2, m >= 0, c = d + m <= 65): [g_1, ..., g_{d+m}],
+ *                   f = g_1 ... g_d + g_{d+1} + ... + g_{d+m}: one product of
+ *                   d columns plus m single columns, the family of
+ *                   polynomials the paper evaluates (Sec. 5, Table
+ *                   poly_examples: g1 g2 = ZC_GATE_SUM_OF(0) with d = 2,
+ *                   g1 g2 + g3 + g4 + g5 = ZC_GATE_SUM_OF(3) with d = 2,
+ *                   g1 g2 g3 g4 = ZC_GATE_SUM_OF(0) with d = 4).
+ * The gate word is what the proof header and the transcript carry, so m is
+ * bound into both.
  *
  * Ownership.  The caller owns every buffer it passes.  A context owns the
  * device scratch memory, constant tables and streams it creates, and reuses
@@ -68,11 +77,13 @@ typedef enum {
   ZC_ERR_BUFFER_TOO_SMALL = 6  /* proof capacity below zc_proof_size */
 } zc_status;
 
-typedef enum { ZC_GATE_PLONK = 1, ZC_GATE_PRODUCT = 2 } zc_gate;
+typedef enum { ZC_GATE_PLONK = 1, ZC_GATE_PRODUCT = 2, ZC_GATE_SUM = 3 } zc_gate;
+/* Gate word of the sum gate with m single columns (m in bits 8..15). */
+#define ZC_GATE_SUM_OF(m) ((uint32_t)ZC_GATE_SUM | ((uint32_t)(m) << 8))
 typedef enum { ZC_FORM_SUMCHECK = 1, ZC_FORM_NTT = 2 } zc_form;
 
-/* One ZeroCheck instance: gate, n (N = 2^n, 1 <= n <= 28), degree d
- * (3 for Plonk, 2..64 for the product gate) and log2(|D| / N) for the NTT
+/* One ZeroCheck instance: gate word, n (N = 2^n, 1 <= n <= 28), degree d
+ * (3 for Plonk, 2..64 for the product and sum gates) and log2(|D| / N) for the NTT
  * form (0 selects log2(next_pow2(d)); |D| must be >= d N).  SumCheck
  * ignores log_blowup. */
 typedef struct {

@@ -28,6 +28,7 @@ _lib = None
 
 GATE_PLONK = 1
 GATE_PRODUCT = 2
+GATE_SUM = 3
 
 
 def build(force: bool = False) -> str:
@@ -95,7 +96,9 @@ def _roots_buf(roots):
 
 
 def ncols(gate: int, d: int) -> int:
-    return 8 if gate == GATE_PLONK else d + 1
+    if gate == GATE_PLONK:
+        return 8
+    return d + 1 if gate == GATE_PRODUCT else d + (gate >> 8)
 
 
 def proof_size(form: int, gate: int, n: int, d: int) -> int:

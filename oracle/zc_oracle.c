@@ -378,12 +378,18 @@ static fe tr_squeeze(transcript *t) {
 
 /* ------------------------------------------------------------- gates --- */
 /* Plonk gate (columns qL,qR,qM,qO,qC,a,b,c):  qL a + qR b + qM a b + qO c + qC
- * Product gate (columns q,w1..w_{d-1},o):     q w1 ... w_{d-1} - o            */
-enum { GATE_PLONK = 1, GATE_PRODUCT = 2 };
+ * Product gate (columns q,w1..w_{d-1},o):     q w1 ... w_{d-1} - o
+ * Sum gate (columns g_1..g_{d+m}):            g_1 ... g_d + g_{d+1} + ... + g_{d+m}
+ * The sum gate is the paper's workload family (Table poly_examples: g1 g2,
+ * g1 g2 + g3, ..., g1 g2 g3 g4): one product of d columns plus m single
+ * columns.  Its gate word carries m in bits 8..15 (GATE_SUM | m << 8). */
+enum { GATE_PLONK = 1, GATE_PRODUCT = 2, GATE_SUM = 3 };
 
 static int gate_cols(uint32_t gate, uint32_t d) {
-    if (gate == GATE_PLONK) return d == 3 ? 8 : -1;
-    if (gate == GATE_PRODUCT) return (d >= 2 && d <= 64) ? (int)d + 1 : -1;
+    const uint32_t base = gate & 0xff, m = gate >> 8;
+    if (base == GATE_PLONK) return (m == 0 && d == 3) ? 8 : -1;
+    if (base == GATE_PRODUCT) return (m == 0 && d >= 2 && d <= 64) ? (int)d + 1 : -1;
+    if (base == GATE_SUM) return (m <= 63 && d >= 2 && d <= 64 && d + m <= 65) ? (int)(d + m) : -1;
     return -1;
 }
 
@@ -398,7 +404,9 @@ static fe gate_eval(uint32_t gate, uint32_t d, const fe *x) {
     }
     fe p = x[0];
     for (uint32_t i = 1; i < d; i++) p = f_mul(p, x[i]);
-    return f_sub(p, x[d]);
+    if ((gate & 0xff) == GATE_PRODUCT) return f_sub(p, x[d]);
+    for (uint32_t i = d; i < d + (gate >> 8); i++) p = f_add(p, x[i]);
+    return p;
 }
 
 /* ------------------------------------------------------------ NTT ------ */
@@ -699,16 +707,26 @@ int zo_prove_ntt(uint32_t gate, uint32_t n, uint32_t d, uint32_t log_blowup,
         }
         for (int j = 0; j < 8; j++) free(L[j]);
     } else {
-        /* running product q * w1 * ... * w_{d-1}, then minus o */
+        /* running product of the first d columns, then minus o (product gate)
+         * or plus the single columns (sum gate) */
         coset_lde(G[0], n, logm, fh);
         for (uint32_t j = 1; j < d; j++) {
             coset_lde(G[j], n, logm, tmp);
             #pragma omp parallel for schedule(static)
             for (long i = 0; i < (long)M; i++) fh[i] = f_mul(fh[i], tmp[i]);
         }
-        coset_lde(G[d], n, logm, tmp);
-        #pragma omp parallel for schedule(static)
-        for (long i = 0; i < (long)M; i++) fh[i] = f_sub(fh[i], tmp[i]);
+        if ((gate & 0xff) == GATE_PRODUCT) {
+            coset_lde(G[d], n, logm, tmp);
+            #pragma omp parallel for schedule(static)
+            for (long i = 0; i < (long)M; i++) fh[i] = f_sub(fh[i], tmp[i]);
+        } else {
+            /* sum gate: plus g_{d+1} .. g_{d+m} */
+            for (int j = (int)d; j < c; j++) {
+                coset_lde(G[j], n, logm, tmp);
+                #pragma omp parallel for schedule(static)
+                for (long i = 0; i < (long)M; i++) fh[i] = f_add(fh[i], tmp[i]);
+            }
+        }
     }
 
     /* evals of z_H = x^N - 1 on D, then element-wise division */

@@ -4,7 +4,7 @@ These are the counts the roofline is taken against (per proof, by form):
 
 SumCheck, per round pair and summed over all rounds (N - 1 pairs): the
 eq-weighted gate at d + 1 points with g + 1 multiplications each
-(g = 5 for the Plonk gate, d - 1 for the product gate), the eq weight, and
+(g = 5 for the Plonk gate, d - 1 for the product and sum gates), the eq weight, and
 one fold multiplication per column.  Bytes: every column read twice and
 written once over the rounds (2 c N reads + c N writes, at 32 bytes, taken
 as 128 c N bytes with the round-1 conversions).
@@ -22,7 +22,9 @@ import math
 
 
 def ncols(gate: int, d: int) -> int:
-    return 8 if gate == 1 else d + 1
+    if gate == 1:
+        return 8
+    return d + 1 if gate == 2 else d + (gate >> 8)
 
 
 def blowup(d: int) -> int:

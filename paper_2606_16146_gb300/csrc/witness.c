@@ -8,6 +8,10 @@
  * domain, as the workload definition requires:
  *   Plonk   : columns qL,qR,qM,qO,qC,a,b,c ; c = -(qL a + qR b + qM a b + qC) / qO
  *   Product : columns q,w1..w_{d-1},o      ; o = q w1 ... w_{d-1}
+ *   Sum     : columns g_1..g_{d+m}          ; g_{d+m} = -(g_1 ... g_d + g_{d+1} + ... + g_{d+m-1})
+ *             for m >= 1; for m = 0 (f = g_1 ... g_d) every point zeroes one
+ *             factor, chosen uniformly by the stream seeded with
+ *             seed ^ 0xD1B54A32D192ED03.
  * Column j draws from a stream seeded with seed ^ (0x9E3779B97F4A7C15 (j+1)).
  * Each draw takes four 64-bit outputs as a little-endian 256-bit integer,
  * clears bit 255 and is kept if it is below r (rejection sampling).
@@ -156,8 +160,10 @@ static void fill_uniform(uint8_t *col, size_t N, uint64_t seed, int j, int nonze
     for (size_t k = 0; k < N; k++) put(col + 32 * k, draw(&s, nonzero));
 }
 
-/* gate 1 = Plonk (d must be 3), gate 2 = product (d >= 2).  cols[j] holds
- * N*32 bytes.  tamper != 0 adds 1 to column a (Plonk) or w1 (product) at
+/* gate 1 = Plonk (d must be 3), gate 2 = product (d >= 2), gate 3 | m << 8 =
+ * sum of one d-fold product and m single columns.  cols[j] holds N*32 bytes.
+ * tamper != 0 adds 1 to column a (Plonk), w1 (product) or the solved last
+ * column (sum gate, m >= 1), or sets the zeroed factor to 1 (m = 0), at
  * index seed mod N afterwards.  Returns 0 on success. */
 int zw_generate(uint32_t gate, uint32_t n, uint32_t d, uint64_t seed, int tamper, uint8_t *const *cols) {
     setup();
@@ -210,6 +216,42 @@ int zw_generate(uint32_t gate, uint32_t n, uint32_t d, uint64_t seed, int tamper
             size_t k = (size_t)(seed % N);
             el one = {{1, 0, 0, 0}};
             put(cols[1] + 32 * k, addm(get(cols[1] + 32 * k), one));
+        }
+        return 0;
+    }
+    if ((gate & 0xff) == 3) {
+        const uint32_t m = gate >> 8, c = d + m;
+        if (d < 2 || d > 64 || m > 63 || c > 65) return 1;
+        if (m == 0) {
+            for (uint32_t j = 0; j < d; j++) fill_uniform(cols[j], N, seed, (int)j, 1);
+            uint64_t s = seed ^ 0xD1B54A32D192ED03ULL;
+            const el zero = {{0, 0, 0, 0}};
+            for (size_t k = 0; k < N; k++) put(cols[splitmix64(&s) % d] + 32 * k, zero);
+            if (tamper) {
+                /* the zeroed factor of point seed mod N becomes 1 */
+                size_t k0 = (size_t)(seed % N);
+                uint64_t s2 = seed ^ 0xD1B54A32D192ED03ULL;
+                uint32_t jz = 0;
+                for (size_t k = 0; k <= k0; k++) jz = (uint32_t)(splitmix64(&s2) % d);
+                const el one = {{1, 0, 0, 0}};
+                put(cols[jz] + 32 * k0, one);
+            }
+            return 0;
+        }
+        for (uint32_t j = 0; j + 1 < c; j++) fill_uniform(cols[j], N, seed, (int)j, 0);
+        #pragma omp parallel for schedule(static)
+        for (long kk = 0; kk < (long)N; kk++) {
+            size_t k = (size_t)kk;
+            el p = to_m(get(cols[0] + 32 * k));
+            for (uint32_t j = 1; j < d; j++) p = montmul(p, to_m(get(cols[j] + 32 * k)));
+            el sum = from_m(p);
+            for (uint32_t j = d; j + 1 < c; j++) sum = addm(sum, get(cols[j] + 32 * k));
+            put(cols[c - 1] + 32 * k, negm(sum));
+        }
+        if (tamper) {
+            size_t k = (size_t)(seed % N);
+            el one = {{1, 0, 0, 0}};
+            put(cols[c - 1] + 32 * k, addm(get(cols[c - 1] + 32 * k), one));
         }
         return 0;
     }

@@ -4,7 +4,9 @@ Shared by the tests, the benchmark and the oracle runs; holds no prover
 arithmetic.  The C source ``csrc/witness.c`` documents the distribution:
 uniform field elements from per-column splitmix64 streams, with the last
 column solved so that the gate vanishes on the whole domain (Plonk:
-c = -(qL a + qR b + qM a b + qC)/qO; product gate: o = q w1 ... w_{d-1}).
+c = -(qL a + qR b + qM a b + qC)/qO; product gate: o = q w1 ... w_{d-1};
+sum gate: the last single column is minus the rest, or with no single
+column one factor is zeroed at every point).
 Columns come back as ``numpy.uint8`` arrays of N*32 canonical little-endian
 bytes.
 """
@@ -25,6 +27,12 @@ _lib = None
 
 GATE_PLONK = 1
 GATE_PRODUCT = 2
+GATE_SUM = 3
+
+
+def gate_sum(m: int) -> int:
+    """Gate word of the sum gate g_1 ... g_d + g_{d+1} + ... + g_{d+m}."""
+    return GATE_SUM | (m << 8)
 
 
 def build(force: bool = False) -> str:
@@ -52,7 +60,9 @@ def _load():
 
 
 def ncols(gate: int, d: int) -> int:
-    return 8 if gate == GATE_PLONK else d + 1
+    if gate == GATE_PLONK:
+        return 8
+    return d + 1 if gate == GATE_PRODUCT else d + (gate >> 8)
 
 
 def generate(gate: int, n: int, d: int, seed: int, tamper: bool = False) -> list[np.ndarray]:

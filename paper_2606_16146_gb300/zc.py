@@ -21,7 +21,14 @@ STATUS = {0: "ZC_OK", 1: "ZC_ERR_ARG", 2: "ZC_ERR_OOM", 3: "ZC_ERR_CUDA", 4: "ZC
           5: "ZC_ERR_UNSUPPORTED", 6: "ZC_ERR_BUFFER_TOO_SMALL"}
 (ZC_ERR_ARG, ZC_ERR_OOM, ZC_ERR_CUDA, ZC_ERR_TIMEOUT, ZC_ERR_UNSUPPORTED,
  ZC_ERR_BUFFER_TOO_SMALL) = 1, 2, 3, 4, 5, 6
-ZC_GATE_PLONK, ZC_GATE_PRODUCT = 1, 2
+ZC_GATE_PLONK, ZC_GATE_PRODUCT, ZC_GATE_SUM = 1, 2, 3
+
+
+def gate_sum(m: int) -> int:
+    """ZC_GATE_SUM_OF(m): gate word of g_1 ... g_d + g_{d+1} + ... + g_{d+m}."""
+    return ZC_GATE_SUM | (m << 8)
+
+
 ZC_FORM_SUMCHECK, ZC_FORM_NTT = 1, 2
 ZC_TUNE_SC_GRID, ZC_TUNE_SC_TAIL_LOG, ZC_TUNE_NTT_TILE_LOG, ZC_TUNE_NTT_MINB = 1, 2, 3, 4
 ZC_TUNE_SC_SMALL_LOG, ZC_TUNE_SC_MINB, ZC_TUNE_SC_PROD_PPT, ZC_TUNE_SC_CHUNK_LOG = 5, 6, 7, 8

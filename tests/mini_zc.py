@@ -65,7 +65,9 @@ def gate_eval(gate, d, x):
     if gate == 1:
         qL, qR, qM, qO, qC, a, b, c = x
         return (qL * a + qR * b + qM * a * b + qO * c + qC) % R
-    return (math.prod(x[:d]) - x[d]) % R
+    if gate & 0xFF == 2:
+        return (math.prod(x[:d]) - x[d]) % R
+    return (math.prod(x[:d]) + sum(x[d:d + (gate >> 8)])) % R
 
 
 # ---------------------------------------------------------------- MLE ---
@@ -164,7 +166,11 @@ def gate_poly(gate, d, polys):
     f = polys[0]
     for p in polys[1:d]:
         f = pmul(f, p)
-    return padd(f, [(-x) % R for x in polys[d]])
+    if gate & 0xFF == 2:
+        return padd(f, [(-x) % R for x in polys[d]])
+    for p in polys[d:d + (gate >> 8)]:
+        f = padd(f, p)
+    return f
 
 
 def divide_by_zh(f, N):

@@ -124,7 +124,12 @@ def _cols_int(cols):
     return [mz.ints(c) for c in cols]
 
 
+# the paper's workload family (Table poly_examples) as sum gates: gate word, d
+FAMILY = [(witness.gate_sum(0), 2), (witness.gate_sum(1), 2), (witness.gate_sum(2), 2),
+          (witness.gate_sum(3), 2), (witness.gate_sum(0), 3), (witness.gate_sum(0), 4)]
+
 SC_CASES = [(1, 1, 3), (1, 2, 3), (1, 3, 3), (1, 4, 3), (2, 1, 2), (2, 3, 2), (2, 3, 3), (2, 2, 5), (2, 4, 4)]
+SC_CASES += [(g, n, d) for (g, d), n in zip(FAMILY, (1, 3, 2, 3, 3, 2))]
 
 
 @pytest.mark.parametrize("gate,n,d", SC_CASES)
@@ -137,7 +142,8 @@ def test_sumcheck_proof_matches_bruteforce(gate, n, d):
     assert pb == ref
 
 
-@pytest.mark.parametrize("gate,n,d", [(1, 3, 3), (2, 3, 4)])
+@pytest.mark.parametrize("gate,n,d", [(1, 3, 3), (2, 3, 4), (witness.gate_sum(2), 3, 2),
+                                      (witness.gate_sum(0), 2, 3)])
 def test_sumcheck_tampered_matches_bruteforce(gate, n, d):
     cols = witness.generate(gate, n, d, 91, tamper=True)
     pb = oracle.prove_sumcheck(gate, n, d, cols)
@@ -196,6 +202,7 @@ def test_sumcheck_round_invariant_and_final():
 
 
 NTT_CASES = [(1, 1, 3), (1, 2, 3), (1, 3, 3), (1, 5, 3), (2, 1, 2), (2, 3, 2), (2, 2, 3), (2, 3, 4), (2, 2, 5), (2, 4, 8)]
+NTT_CASES += [(g, n, d) for (g, d), n in zip(FAMILY, (2, 1, 3, 2, 3, 2))]
 
 
 @pytest.mark.parametrize("gate,n,d", NTT_CASES)
@@ -242,7 +249,8 @@ def test_ntt_tampered_quotient_interpolates_on_coset():
 
 
 @pytest.mark.parametrize("form", [1, 2])
-@pytest.mark.parametrize("gate,n,d", [(1, 7, 3), (2, 6, 4)])
+@pytest.mark.parametrize("gate,n,d", [(1, 7, 3), (2, 6, 4), (witness.gate_sum(1), 6, 2),
+                                      (witness.gate_sum(0), 5, 4)])
 def test_verifier_accepts_honest_rejects_tampered(form, gate, n, d):
     cols = witness.generate(gate, n, d, 500 + n)
     bad = witness.generate(gate, n, d, 500 + n, tamper=True)
@@ -272,7 +280,7 @@ def test_verifier_accepts_honest_rejects_tampered(form, gate, n, d):
 
 
 def test_witness_generator_satisfies_gate():
-    for gate, n, d in [(1, 5, 3), (2, 5, 2), (2, 4, 7)]:
+    for gate, n, d in [(1, 5, 3), (2, 5, 2), (2, 4, 7)] + [(g, 5, d) for g, d in FAMILY]:
         cols = _cols_int(witness.generate(gate, n, d, 9))
         for k in range(1 << n):
             assert mz.gate_eval(gate, d, [c[k] for c in cols]) == 0
