@@ -12,8 +12,11 @@ namespace zc {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 int gate_ncols(uint32_t gate, uint32_t d) {
-  if (gate == ZC_GATE_PLONK) return d == 3 ? 8 : -1;
-  if (gate == ZC_GATE_PRODUCT) return (d >= 2 && d <= (uint32_t)kMaxDeg) ? (int)d + 1 : -1;
+  const uint32_t base = gate & 0xffu, m = gate >> 8;
+  if (base == ZC_GATE_PLONK) return (m == 0 && d == 3) ? 8 : -1;
+  if (base == ZC_GATE_PRODUCT) return (m == 0 && d >= 2 && d <= (uint32_t)kMaxDeg) ? (int)d + 1 : -1;
+  if (base == ZC_GATE_SUM)
+    return (m <= 0xffu && d >= 2 && d <= (uint32_t)kMaxDeg && d + m <= (uint32_t)kMaxCols) ? (int)(d + m) : -1;
   return -1;
 }
 
@@ -335,7 +338,9 @@ static fr host_gate(uint32_t gate, uint32_t d, const fr* x, const DevConst& C) {
   }
   fr pr = x[0];
   for (uint32_t j = 1; j < d; j++) pr = h_canon_mul(pr, x[j], C);
-  return fr_sub_g(pr, x[d]);
+  if (gate == ZC_GATE_PRODUCT) return fr_sub_g(pr, x[d]);
+  for (uint32_t j = d; j < d + (gate >> 8); j++) pr = fr_add_g(pr, x[j]);  // sum gate
+  return pr;
 }
 
 static fr host_lagrange(const fr* y, int m, const fr& x, const DevConst& C) {

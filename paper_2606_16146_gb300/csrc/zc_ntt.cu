@@ -424,9 +424,11 @@ struct NttGateArgs {
   fr* qhat;                 // slice output
   const fr* zinv;           // constant of this slice
   uint64_t N;
-  uint32_t gate, d;
+  uint32_t gate, d, c;       // gate word, degree, columns
 };
 
+// f at the slice points, times the slice constant 1 / (z_H M): Plonk; product
+// q w1 .. w_{d-1} - o; sum g_1 .. g_d + g_{d+1} + .. + g_c (all at level 1).
 __global__ void __launch_bounds__(256) k_ntt_gate(NttGateArgs A) {
   const fr zi = ld_fr(A.zinv);
   for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < A.N;
@@ -442,7 +444,9 @@ __global__ void __launch_bounds__(256) k_ntt_gate(NttGateArgs A) {
     } else {
       f = ld_fr(A.col[0] + p);
       for (uint32_t j = 1; j < A.d; j++) f = fr_mul(f, ld_fr(A.col[j] + p));
-      f = fr_sub(f, ld_fr(A.col[A.d] + p));
+      if (A.gate == ZC_GATE_PRODUCT) f = fr_sub(f, ld_fr(A.col[A.d] + p));
+      else
+        for (uint32_t j = A.d; j < A.c; j++) f = fr_add(f, ld_fr(A.col[j] + p));
     }
     st_fr(A.qhat + p, fr_mul(f, zi));
   }
@@ -1094,6 +1098,7 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
     ga.N = N;
     ga.gate = gate;
     ga.d = d;
+    ga.c = (uint32_t)c;
     uint32_t gb = (uint32_t)std::min<uint64_t>((N + 255) / 256, (uint64_t)ctx->sm_count * 8);
     k_ntt_gate<<<gb, 256, 0, st>>>(ga);
     ctx->launches++;

@@ -392,21 +392,24 @@ __device__ __forceinline__ uint32_t prod_point(int p, int np, bool full, uint32_
   return p == 0 ? p0 : (uint32_t)p + 1;  // p0, 2, ..., d-1
 }
 
-// Product gate f = q w1 .. w_{d-1} - o, pair k: this thread's kPP points.
-// load(j, lo, hi) supplies column j of the pair (global memory or shared).
+// Product gate f = q w1 .. w_{d-1} - o, or sum gate f = g_1 .. g_d + g_{d+1}
+// + .. + g_c, pair k: this thread's kPP points.  load(j, lo, hi) supplies
+// column j of the pair (global memory or shared).
 template <int PP, class Load>
 __device__ __forceinline__ void prod_pair_g(const ScRoundArgs& A, Load load, int pcnt,
                                             const uint32_t (&tpt)[PP], bool first, const fr& w,
                                             fr (&acc)[PP], uint32_t& bad) {
-  const int d = (int)A.d;
+  const int d = (int)A.d, c = A.c;
+  const bool minus = (A.gate & 0xffu) == ZC_GATE_PRODUCT;  // o is subtracted; sum-gate columns add
   fr prod[PP];
-  for (int j = 0; j <= d; j++) {
+  for (int j = 0; j < c; j++) {
     fr lo, hi;
     load(j, lo, hi);
     if (first) bad |= (!fr_is_canonical(lo)) | (!fr_is_canonical(hi));
-    // o enters at level 0 and is brought to level 1-d by kcomp: with several
-    // points per thread, scale the two ends once instead of every point
-    const bool oscale = PP > 1 && j == d && pcnt >= 2;
+    // o (or a single sum-gate column) enters at level 0 and is brought to
+    // level 1-d by kcomp: with several points per thread, scale the two ends
+    // once instead of every point
+    const bool oscale = PP > 1 && j >= d && pcnt >= 2;
     if (oscale) {
       lo = fr_mul(lo, A.kcomp);
       hi = fr_mul(hi, A.kcomp);
@@ -427,9 +430,12 @@ __device__ __forceinline__ void prod_pair_g(const ScRoundArgs& A, Load load, int
         tcur = tpt[p];
         x = e;
       }
-      if (j == d) {
-        // infinity has no o term
-        if (tpt[p] != kInf) prod[p] = fr_sub(prod[p], oscale ? x : fr_mul(x, A.kcomp));
+      if (j >= d) {
+        // infinity has no degree-1 term
+        if (tpt[p] != kInf) {
+          const fr xs = oscale ? x : fr_mul(x, A.kcomp);
+          prod[p] = minus ? fr_sub(prod[p], xs) : fr_add(prod[p], xs);
+        }
       } else {
         prod[p] = j == 0 ? x : fr_mul(prod[p], x);
       }
@@ -788,7 +794,7 @@ template <int PP>
 __global__ void __launch_bounds__(256, 2) k_sc_prod_fused(ScRoundArgs A) {
   extern __shared__ __align__(16) fr Vs[];
   const int i = A.round;
-  const int d = (int)A.d, c = d + 1;
+  const int d = (int)A.d, c = A.c;
   const bool full = A.full != 0;
   const int np = full ? d + 1 : d;
   const uint32_t p0 = full ? 0u : A.st->p0[i];
@@ -1190,7 +1196,7 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
         const int G = (npr + ppt - 1) / ppt, spb = std::max(1, std::min(256 / G, 256 / c));
         R.spb = (uint32_t)spb;
         R.nwork = (uint32_t)std::min<uint64_t>((h + spb - 1) / spb, (uint64_t)P.grid_prod);
-        const size_t dyn = sizeof(fr) * (size_t)(d + 1) * 2 * spb;
+        const size_t dyn = sizeof(fr) * (size_t)c * 2 * spb;
         if (ppt == 1) k_sc_prod_fused<1><<<R.nwork, 256, dyn, st>>>(R);
         else k_sc_prod_fused<3><<<R.nwork, 256, dyn, st>>>(R);
         for (int j = 0; j < c; j++) cur[j] = B.tab[j];

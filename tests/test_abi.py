@@ -28,7 +28,7 @@ def test_library_builds_and_exports_every_declared_symbol():
         assert hasattr(L, name), name
 
 
-@pytest.mark.parametrize("gate,n,d", [(1, 5, 3), (2, 7, 2), (2, 3, 32), (1, 24, 3)])
+@pytest.mark.parametrize("gate,n,d", [(1, 5, 3), (2, 7, 2), (2, 3, 32), (1, 24, 3), (3 | 3 << 8, 9, 2), (3, 6, 4)])
 def test_proof_size_matches_oracle(gate, n, d):
     for form in (1, 2):
         assert zc.proof_size(gate, n, d, form) == oracle.proof_size(form, gate, n, d)
@@ -40,7 +40,13 @@ def test_bad_params_rejected():
     with pytest.raises(zc.ZCError):
         zc.proof_size(2, 0, 2, 1)          # n >= 1
     with pytest.raises(zc.ZCError):
-        zc.proof_size(3, 5, 3, 1)          # unknown gate
+        zc.proof_size(4, 5, 3, 1)          # unknown gate
+    with pytest.raises(zc.ZCError):
+        zc.proof_size(zc.gate_sum(0), 5, 1, 1)   # sum gate needs a product of >= 2
+    with pytest.raises(zc.ZCError):
+        zc.proof_size(zc.gate_sum(60), 5, 8, 1)  # more than 65 columns
+    with pytest.raises(zc.ZCError):
+        zc.proof_size(2 | (1 << 8), 5, 3, 1)     # only the sum gate carries m
 
 
 def test_setup_fails_loudly_without_a_gpu():
@@ -51,7 +57,8 @@ def test_setup_fails_loudly_without_a_gpu():
         zc.Context(0, 12, 3)
 
 
-@pytest.mark.parametrize("gate,n,d", [(1, 6, 3), (2, 5, 4), (2, 1, 2), (1, 1, 3)])
+@pytest.mark.parametrize("gate,n,d", [(1, 6, 3), (2, 5, 4), (2, 1, 2), (1, 1, 3),
+                                      (zc.gate_sum(3), 5, 2), (zc.gate_sum(0), 4, 3)])
 def test_host_verifier_agrees_with_oracle(gate, n, d):
     cols = witness.generate(gate, n, d, 40 + n)
     bad = witness.generate(gate, n, d, 40 + n, tamper=True)
