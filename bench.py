@@ -371,9 +371,9 @@ def cpu_sample_batched(inst, cols, forms):
 SWEEP = [(1, 12, 3), (1, 20, 3), (1, 22, 3), (2, 22, 2), (2, 22, 4), (2, 22, 8), (2, 22, 16), (2, 22, 32)]
 
 
-def run_sweep(args, world, rank, local):
-    """Both forms, one proof at a time, over the plain and high-degree shapes:
-    Plonk n = 12, 20, 22 and the product gate at n = 22 for d = 2..32."""
+def _time_shapes(local, shapes, K, W, seed_of, label_of):
+    """One proof of each form at a time per (gate, n, d) shape, column roots
+    given (untimed): median CUDA-event ms, roofline ms and fraction, phases."""
     import torch
     from paper_2606_16146_gb300 import witness, zc
     torch.cuda.set_device(local)
@@ -381,14 +381,14 @@ def run_sweep(args, world, rank, local):
     ctx = zc.Context(local, max_n=24, max_d=32)
     stream = torch.cuda.Stream(dev)
     rows = []
-    K, W = max(1, args.steps), max(3, args.warmup)
     clocks = ClockSampler(local)
     clocks.start()
-    for gate, n, d in SWEEP:
-        cols = witness.generate(gate, n, d, 1000 + n if gate == 1 else 2000 + 10 * d + n)
+    for gate, n, d in shapes:
+        cols = witness.generate(gate, n, d, seed_of(gate, n, d))
         dcols = [torch.from_numpy(c).to(dev) for c in cols]
+        del cols
         roots = ctx.roots(gate, n, d, dcols)
-        row = {"gate": "plonk" if gate == 1 else "product", "n": n, "d": d}
+        row = {"gate": label_of(gate, d), "n": n, "d": d}
         for form, name in ((zc.ZC_FORM_SUMCHECK, "sumcheck"), (zc.ZC_FORM_NTT, "ntt")):
             proof = torch.zeros(zc.proof_size(gate, n, d, form), dtype=torch.uint8, device=dev)
             if form == zc.ZC_FORM_SUMCHECK:
@@ -409,6 +409,17 @@ def run_sweep(args, world, rank, local):
         del dcols
         torch.cuda.empty_cache()
     clk = clocks.stop()
+    ctx.close()
+    return rows, clk
+
+
+def run_sweep(args, world, rank, local):
+    """Both forms, one proof at a time, over the plain and high-degree shapes:
+    Plonk n = 12, 20, 22 and the product gate at n = 22 for d = 2..32."""
+    K, W = max(1, args.steps), max(3, args.warmup)
+    rows, clk = _time_shapes(local, SWEEP, K, W,
+                             lambda g, n, d: 1000 + n if g == 1 else 2000 + 10 * d + n,
+                             lambda g, d: "plonk" if g == 1 else "product")
     head = rows[2]
     config = {"workload": "sweep: one proof of each form at a time; Plonk n=12, 20, 22 and product gate "
                           "n=22, d in {2, 4, 8, 16, 32}; column roots given (untimed)",
@@ -421,7 +432,38 @@ def run_sweep(args, world, rank, local):
     line["e2e_note"] = "device-resident columns; the plain workload line carries the host-buffer run"
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
+
+
+# The paper's polynomials (Sec. 5, Table poly_examples) as sum gates: (name, m, d)
+FAMILY = [("g1g2", 0, 2), ("g1g2+g3", 1, 2), ("g1g2+g3+g4", 2, 2), ("g1g2+g3+g4+g5", 3, 2),
+          ("g1g2g3", 0, 3), ("g1g2g3g4", 0, 4)]
+FAMILY_N = (18, 20, 22, 24)
+
+
+def run_family(args, world, rank, local):
+    """The paper's workload family through the sum gate, both forms, one proof
+    at a time, at N = 2^18 .. 2^24 (the paper sweeps 2^17 .. 2^32)."""
+    from paper_2606_16146_gb300 import witness
+    K, W = max(1, args.steps), max(3, args.warmup)
+    names = {(witness.gate_sum(m), d): name for name, m, d in FAMILY}
+    shapes = [(witness.gate_sum(m), n, d) for n in FAMILY_N for _, m, d in FAMILY]
+    rows, clk = _time_shapes(local, shapes, K, W,
+                             lambda g, n, d: 7000 + 100 * (g >> 8) + 10 * d + n,
+                             lambda g, d: names[(g, d)])
+    config = {"workload": "family: the paper's six polynomials (g1g2, g1g2+g3, g1g2+g3+g4, "
+                          "g1g2+g3+g4+g5, g1g2g3, g1g2g3g4) as sum gates, one proof of each form at "
+                          "a time, n in {18, 20, 22, 24}; column roots given (untimed)",
+              "parallelism": f"replicas x{world}", "l2": "n >= 20 inputs larger than L2; no flush"}
+    at22 = [r for r in rows if r["n"] == 22]
+    line = _base_line(args, world, sum(r["sumcheck"]["ms"] + r["ntt"]["ms"] for r in at22), "ms",
+                      False, config)
+    line["value_is"] = "n=22: sum over the six polynomials of SumCheck ms + NTT ms"
+    line["rows"] = rows
+    line["clocks"] = clk
+    line["e2e"] = None
+    line["e2e_note"] = "device-resident columns; the plain workload line carries the host-buffer run"
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def run_mulpeak(args, world, rank, local):
@@ -527,10 +569,11 @@ def main():
     ap.add_argument("--gate", type=int, default=1, choices=[1, 2])
     ap.add_argument("--form", default="both", choices=["both", "sumcheck", "ntt"],
                     help="restrict the step to one form (profiling); the bench line uses both")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "served", "sweep", "mulpeak"],
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "served", "sweep", "family", "mulpeak"],
                     help="plain: one Plonk n=22 proof per form (the headline line); batched: 64 "
                          "mixed instances in one graph; served: Poisson request loop; sweep: "
-                         "sizes and degrees; mulpeak: the field multiplication alone")
+                         "sizes and degrees; family: the paper's polynomials as sum gates; "
+                         "mulpeak: the field multiplication alone")
     ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="served: arrival rates (req/s)")
     ap.add_argument("--requests", type=int, default=200, help="served: requests per rate")
     args = ap.parse_args()
@@ -551,6 +594,9 @@ def main():
         return
     if args.workload == "sweep":
         run_sweep(args, world, rank, local)
+        return
+    if args.workload == "family":
+        run_family(args, world, rank, local)
         return
     if args.workload == "mulpeak":
         run_mulpeak(args, world, rank, local)
