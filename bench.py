@@ -368,7 +368,8 @@ def cpu_sample_batched(inst, cols, forms):
                       f"all 64 by algorithmic mulmods (x{mm_all / mm_s:.1f})"}
 
 
-SWEEP = [(1, 12, 3), (1, 20, 3), (1, 22, 3), (2, 22, 2), (2, 22, 4), (2, 22, 8), (2, 22, 16), (2, 22, 32)]
+SWEEP = [(1, 12, 3), (1, 20, 3), (1, 22, 3), (2, 22, 2), (2, 22, 4), (2, 22, 8), (2, 22, 16), (2, 22, 32),
+         (1, 22, 3, 1)]   # last: Plonk with the quotient-sized 2N domain
 
 
 def _time_shapes(local, shapes, K, W, seed_of, label_of):
@@ -383,12 +384,16 @@ def _time_shapes(local, shapes, K, W, seed_of, label_of):
     rows = []
     clocks = ClockSampler(local)
     clocks.start()
-    for gate, n, d in shapes:
+    for shape in shapes:
+        gate, n, d = shape[:3]
+        lb = shape[3] if len(shape) > 3 else 0
         cols = witness.generate(gate, n, d, seed_of(gate, n, d))
         dcols = [torch.from_numpy(c).to(dev) for c in cols]
         del cols
         roots = ctx.roots(gate, n, d, dcols)
         row = {"gate": label_of(gate, d), "n": n, "d": d}
+        if lb:
+            row["ntt_log_blowup"] = lb
         for form, name in ((zc.ZC_FORM_SUMCHECK, "sumcheck"), (zc.ZC_FORM_NTT, "ntt")):
             proof = torch.zeros(zc.proof_size(gate, n, d, form), dtype=torch.uint8, device=dev)
             if form == zc.ZC_FORM_SUMCHECK:
@@ -397,12 +402,12 @@ def _time_shapes(local, shapes, K, W, seed_of, label_of):
             else:
                 def fn():
                     ctx.prove_ntt(gate, n, d, dcols, roots=roots, stream=stream, proof_out=proof,
-                                  want_q=False)
+                                  want_q=False, log_blowup=lb)
             for _ in range(W):
                 fn()
             ms, _ = _median_event_ms(fn, stream, K)
-            roof = 1e3 * max(algorithmic_mulmods(name, n, d, gate) / ALU_PEAK_MULMOD,
-                             algorithmic_bytes(name, n, d, gate) / HBM_PEAK)
+            roof = 1e3 * max(algorithmic_mulmods(name, n, d, gate, lb) / ALU_PEAK_MULMOD,
+                             algorithmic_bytes(name, n, d, gate, lb) / HBM_PEAK)
             row[name] = {"ms": ms, "roofline_ms": roof, "roofline_frac": roof / ms,
                          "phases_ms": [round(x, 4) for x in ctx.stats()[:6]]}
         rows.append(row)

@@ -646,7 +646,8 @@ int zo_verify_sumcheck(uint32_t gate, uint32_t n, uint32_t d, const uint8_t *con
 
 /* ------------------------------------------------- NTT ZeroCheck ------- */
 /* Fig. side-by-side-zc (left), Sec. 3.2.  Column j holds g_j(w_N^i) at
- * index i.  D = {7 w_M^i}, M = 2^(log_blowup) N.
+ * index i.  D = {7 w_M^i}, M = 2^(log_blowup) N, by default next_pow2(d) N;
+ * any M >= (d-1) N holds the quotient.
  * Proof = "ZCN1" | gate | n | d | logM | root(q) | g_j(z) ... | q(z). */
 
 static uint32_t default_blowup(uint32_t d) { return ilog2(d); }
@@ -678,7 +679,9 @@ int zo_prove_ntt(uint32_t gate, uint32_t n, uint32_t d, uint32_t log_blowup,
     int c = gate_cols(gate, d);
     if (c < 0 || n < 1 || n > 28) return 1;
     if (log_blowup == 0) log_blowup = default_blowup(d);
-    if ((1u << log_blowup) < d) return 1;          /* |D| must exceed deg f */
+    /* |D| must hold the quotient's (d-1)N - d + 1 coefficients (Sec. 4,
+     * degree scaling: the NTT size follows the degree of q) */
+    if ((1u << log_blowup) + 1 < d) return 1;
     unsigned logm = n + log_blowup;
     if (logm > 32) return 1;
     size_t need; zo_proof_size(2, gate, n, d, &need);
@@ -795,7 +798,7 @@ int zo_verify_ntt(uint32_t gate, uint32_t n, uint32_t d, const uint8_t *const *c
     if (len != need || memcmp(proof, "ZCN1", 4) != 0) return 1;
     uint32_t logm = 0;
     for (int i = 3; i >= 0; i--) logm = (logm << 8) | proof[16 + i];
-    if (logm < n || logm > 32 || (1u << (logm - n)) < d) return 1;
+    if (logm < n || logm > 32 || (1u << (logm - n)) + 1 < d) return 1;
     uint8_t hdr[20]; memcpy(hdr, "ZCN1", 4);
     le32(hdr + 4, gate); le32(hdr + 8, n); le32(hdr + 12, d); le32(hdr + 16, logm);
     if (memcmp(hdr, proof, 20) != 0) return 1;

@@ -31,11 +31,11 @@ def blowup(d: int) -> int:
     return 1 << max(0, (d - 1).bit_length())
 
 
-def algorithmic_mulmods(form: str, n: int, d: int = 3, gate: int = 1) -> float:
+def algorithmic_mulmods(form: str, n: int, d: int = 3, gate: int = 1, log_blowup: int = 0) -> float:
     N = 1 << n
     c = ncols(gate, d)
     g = 5 if gate == 1 else d - 1
-    s = blowup(d)
+    s = 1 << log_blowup if log_blowup else blowup(d)
     M = s * N
     if form == "sumcheck":
         return (N - 1) * ((d + 1) * (g + 1) + 1 + c)
@@ -43,10 +43,10 @@ def algorithmic_mulmods(form: str, n: int, d: int = 3, gate: int = 1) -> float:
             + (M / 2) * math.log2(M) + M + c * N + (d - 1) * N)
 
 
-def algorithmic_bytes(form: str, n: int, d: int = 3, gate: int = 1) -> float:
+def algorithmic_bytes(form: str, n: int, d: int = 3, gate: int = 1, log_blowup: int = 0) -> float:
     N = 1 << n
     c = ncols(gate, d)
-    M = blowup(d) * N
+    M = (1 << log_blowup if log_blowup else blowup(d)) * N
     if form == "sumcheck":
         return 128.0 * c * N
     return 32.0 * (2 * c * N + c * M + M + 2 * M + c * N + M)

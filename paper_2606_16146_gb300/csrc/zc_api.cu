@@ -37,7 +37,8 @@ zc_status check_params(zc_ctx* ctx, const zc_params* p, zc_form form) {
   }
   if (form == ZC_FORM_NTT) {
     uint32_t lb = p->log_blowup ? p->log_blowup : default_log_blowup(p->d);
-    if ((1u << lb) < p->d || p->n + lb > (uint32_t)kMaxN + 2) {
+    // |D| = 2^lb N must hold the quotient's (d-1) N - d + 1 coefficients
+    if ((1u << lb) + 1 < p->d || p->n + lb > (uint32_t)kMaxN + 2) {
       if (ctx) ctx->err = "log_blowup too small for the degree, or domain too large";
       return ZC_ERR_ARG;
     }

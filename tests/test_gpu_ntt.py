@@ -102,3 +102,17 @@ def test_largest_size_verified(ctx):
     cols = witness.generate(gate, n, d, 6003)
     p, q = ctx.prove_ntt(gate, n, d, to_device(cols))
     assert oracle.verify_ntt(gate, n, d, cols, proof_bytes(p), np.asarray(q))
+
+
+@pytest.mark.parametrize("gate,n,d", [(1, 2, 3), (1, 9, 3), (1, 14, 3), (2, 10, 3),
+                                      (witness.gate_sum(0), 12, 3), (witness.gate_sum(1), 5, 2)])
+def test_quotient_sized_domain(ctx, gate, n, d):
+    # |D| = 2N for degree 3 and 2: the smallest power-of-two domain that
+    # holds the quotient (Sec. 4, degree scaling); same bytes as the oracle
+    lb = 1
+    cols = witness.generate(gate, n, d, 8000 + n)
+    want_p, want_q = oracle.prove_ntt(gate, n, d, cols, log_blowup=lb)
+    p, q = ctx.prove_ntt(gate, n, d, to_device(cols), log_blowup=lb)
+    assert _q_bytes(q) == want_q.tobytes()
+    assert proof_bytes(p) == want_p
+    assert zc.verify(gate, n, d, zc.ZC_FORM_NTT, cols, proof_bytes(p), q=_q_bytes(q), log_blowup=lb)

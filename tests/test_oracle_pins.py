@@ -214,6 +214,24 @@ def test_ntt_proof_matches_long_division(gate, n, d):
     assert pb == ref
 
 
+@pytest.mark.parametrize("gate,n,d", [(1, 3, 3), (1, 5, 3), (2, 4, 3), (witness.gate_sum(0), 3, 3),
+                                      (witness.gate_sum(1), 4, 3)])
+def test_ntt_quotient_sized_domain_matches_long_division(gate, n, d):
+    # |D| = 2N for degree 3: the quotient's (d-1)N - d + 1 coefficients fit (Sec. 4)
+    cols = witness.generate(gate, n, d, 350 + n * d)
+    pb, q = oracle.prove_ntt(gate, n, d, cols, log_blowup=1)
+    ref, qref, _ = mz.prove_ntt(gate, n, d, _cols_int(cols), logb=1)
+    assert mz.ints(q) == qref
+    assert pb == ref
+    assert oracle.verify_ntt(gate, n, d, cols, pb, q)
+
+
+def test_ntt_domain_below_the_quotient_rejected():
+    cols = witness.generate(2, 3, 4, 7)
+    with pytest.raises(Exception):
+        oracle.prove_ntt(2, 3, 4, cols, log_blowup=1)   # 2N < 3N - 3
+
+
 def test_ntt_quotient_degree_and_identity():
     gate, n, d = 1, 8, 3
     cols = witness.generate(gate, n, d, 1008)
