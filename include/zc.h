@@ -84,8 +84,9 @@ typedef enum { ZC_FORM_SUMCHECK = 1, ZC_FORM_NTT = 2 } zc_form;
 
 /* One ZeroCheck instance: gate word, n (N = 2^n, 1 <= n <= 28), degree d
  * (3 for Plonk, 2..64 for the product and sum gates) and log2(|D| / N) for the NTT
- * form (0 selects log2(next_pow2(d)); |D| must be >= d N).  SumCheck
- * ignores log_blowup. */
+ * form (0 selects log2(next_pow2(d)); |D| = 2^log_blowup N must hold the
+ * quotient, 2^log_blowup >= d - 1: Sec. 4 sizes the quotient transform by
+ * the degree of q, e.g. 2N for degree 3).  SumCheck ignores log_blowup. */
 typedef struct {
   uint32_t gate, n, d;
   uint32_t log_blowup;
