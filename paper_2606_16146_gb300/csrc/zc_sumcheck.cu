@@ -394,26 +394,20 @@ __device__ __forceinline__ uint32_t prod_point(int p, int np, bool full, uint32_
 
 // Product gate f = q w1 .. w_{d-1} - o, or sum gate f = g_1 .. g_d + g_{d+1}
 // + .. + g_c, pair k: this thread's kPP points.  load(j, lo, hi) supplies
-// column j of the pair (global memory or shared).
+// column j of the pair (global memory or shared).  The degree-1 part (-o, or
+// the sum of the single columns) is added up at level 0 over the pair's two
+// ends first, then brought to the product's level 1-d by one kcomp
+// multiplication per end (several points per thread) or per point.
 template <int PP, class Load>
 __device__ __forceinline__ void prod_pair_g(const ScRoundArgs& A, Load load, int pcnt,
                                             const uint32_t (&tpt)[PP], bool first, const fr& w,
                                             fr (&acc)[PP], uint32_t& bad) {
   const int d = (int)A.d, c = A.c;
-  const bool minus = (A.gate & 0xffu) == ZC_GATE_PRODUCT;  // o is subtracted; sum-gate columns add
   fr prod[PP];
-  for (int j = 0; j < c; j++) {
+  for (int j = 0; j < d; j++) {
     fr lo, hi;
     load(j, lo, hi);
     if (first) bad |= (!fr_is_canonical(lo)) | (!fr_is_canonical(hi));
-    // o (or a single sum-gate column) enters at level 0 and is brought to
-    // level 1-d by kcomp: with several points per thread, scale the two ends
-    // once instead of every point
-    const bool oscale = PP > 1 && j >= d && pcnt >= 2;
-    if (oscale) {
-      lo = fr_mul(lo, A.kcomp);
-      hi = fr_mul(hi, A.kcomp);
-    }
     const fr dl = fr_sub(hi, lo);
     fr e = lo;
     uint32_t tcur = 0;
@@ -430,15 +424,36 @@ __device__ __forceinline__ void prod_pair_g(const ScRoundArgs& A, Load load, int
         tcur = tpt[p];
         x = e;
       }
-      if (j >= d) {
-        // infinity has no degree-1 term
-        if (tpt[p] != kInf) {
-          const fr xs = oscale ? x : fr_mul(x, A.kcomp);
-          prod[p] = minus ? fr_sub(prod[p], xs) : fr_add(prod[p], xs);
-        }
-      } else {
-        prod[p] = j == 0 ? x : fr_mul(prod[p], x);
-      }
+      prod[p] = j == 0 ? x : fr_mul(prod[p], x);
+    }
+  }
+  if (c > d) {
+    const bool minus = (A.gate & 0xffu) == ZC_GATE_PRODUCT;  // o is subtracted; sum-gate columns add
+    fr lo = fr_zero(), hi = fr_zero();  // degree-1 part at the two ends, level 0
+    for (int j = d; j < c; j++) {
+      fr xl, xh;
+      load(j, xl, xh);
+      if (first) bad |= (!fr_is_canonical(xl)) | (!fr_is_canonical(xh));
+      lo = minus ? fr_sub(lo, xl) : fr_add(lo, xl);
+      hi = minus ? fr_sub(hi, xh) : fr_add(hi, xh);
+    }
+    const bool scale_ends = PP > 1 && pcnt >= 2;
+    if (scale_ends) {
+      lo = fr_mul(lo, A.kcomp);
+      hi = fr_mul(hi, A.kcomp);
+    }
+    const fr dl = fr_sub(hi, lo);
+    fr e = lo;
+    uint32_t tcur = 0;
+#pragma unroll
+    for (int p = 0; p < PP; p++) {
+      if (p >= pcnt) break;
+      if (tpt[p] == kInf) continue;  // infinity has no degree-1 term
+      if (p == 0) e = fr_add(lo, fr_mul_small(dl, tpt[p]));
+      else
+        for (uint32_t s2 = tcur; s2 < tpt[p]; s2++) e = fr_add(e, dl);
+      tcur = tpt[p];
+      prod[p] = fr_add(prod[p], scale_ends ? e : fr_mul(e, A.kcomp));
     }
   }
 #pragma unroll
