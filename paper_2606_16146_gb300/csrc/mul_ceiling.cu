@@ -7,9 +7,10 @@
 //   * the multiplier the kernels use (fr_mul, one out-of-line copy),
 //   * the same code inlined at the call site (fr_mul_inl),
 //   * the carry-chain IMAD form (fr_mul_cc: mad.lo.cc / madc.hi.cc),
-//   * an unsaturated form for comparison: nine 29-bit limbs, each column a
-//     64-bit accumulator fed by mad.wide.u32 (no carry chains inside the
-//     product), R = 2^261; checked against fr_mul on random inputs,
+//   * an unsaturated form for comparison: nine 29-bit limbs, each of the 18
+//     product columns a 64-bit accumulator fed by 32x32->64 multiply-adds
+//     (no carry chains inside the product), R = 2^261; checked against
+//     fr_mul on random inputs,
 // and the per-instruction rates of the integer operations they are built
 // from.  Every thread runs two independent chains of dependent products.
 // Prints one JSON object on stdout.
@@ -45,12 +46,6 @@ struct f29 {
   uint32_t l[9];
 };
 
-__device__ __forceinline__ uint64_t mad_wide(uint32_t a, uint32_t b, uint64_t c) {
-  uint64_t d;
-  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
-  return d;
-}
-
 // radix-2^29 limbs of (a << S); a < 2^256, S <= 5
 template <int S>
 __device__ __forceinline__ f29 to29(const fr& a) {
@@ -73,30 +68,29 @@ __device__ __forceinline__ f29 to29(const fr& a) {
 
 // (a b + m r) / 2^261, limbs normalised; a, b < 2^261 with a b < 2^261 r
 // gives a result below 2r.  -r^{-1} = -1 mod 2^29 because r = 1 mod 2^29.
+// Column k of a b + m r accumulates in its own 64-bit register T[k] through
+// mad.wide.u32 (at most 18 products of 58 bits: below 2^63); after row i the
+// low 29 bits of T[i] are zero and its carry moves to T[i+1].
 __device__ __forceinline__ f29 mont29(const f29& a, const f29& b) {
-  uint64_t t[9];
+  uint64_t T[18];
 #pragma unroll
-  for (int j = 0; j < 9; j++) t[j] = 0;
+  for (int k = 0; k < 18; k++) T[k] = 0;
 #pragma unroll
   for (int i = 0; i < 9; i++) {
 #pragma unroll
-    for (int j = 0; j < 9; j++) t[j] = mad_wide(a.l[i], b.l[j], t[j]);
-    const uint32_t m = (0u - static_cast<uint32_t>(t[0])) & kM29;
-    const uint64_t carry = (t[0] + m) >> 29;
+    for (int j = 0; j < 9; j++) T[i + j] += static_cast<uint64_t>(a.l[i]) * b.l[j];
+    const uint32_t m = (0u - static_cast<uint32_t>(T[i])) & kM29;
 #pragma unroll
-    for (int j = 1; j < 9; j++) t[j] = mad_wide(m, r29(j), t[j]);
-#pragma unroll
-    for (int j = 0; j < 8; j++) t[j] = t[j + 1];
-    t[8] = 0;
-    t[0] += carry;
+    for (int j = 1; j < 9; j++) T[i + j] += static_cast<uint64_t>(m) * r29(j);
+    T[i + 1] += (T[i] + m) >> 29;
   }
   f29 o;
 #pragma unroll
-  for (int j = 0; j < 8; j++) {
-    t[j + 1] += t[j] >> 29;
-    o.l[j] = static_cast<uint32_t>(t[j]) & kM29;
+  for (int k = 9; k < 17; k++) {
+    T[k + 1] += T[k] >> 29;
+    o.l[k - 9] = static_cast<uint32_t>(T[k]) & kM29;
   }
-  o.l[8] = static_cast<uint32_t>(t[8]);
+  o.l[8] = static_cast<uint32_t>(T[17]);
   return o;
 }
 
