@@ -452,14 +452,17 @@ def run_family(args, world, rank, local):
     K, W = max(1, args.steps), max(3, args.warmup)
     names = {(witness.gate_sum(m), d): name for name, m, d in FAMILY}
     shapes = [(witness.gate_sum(m), n, d) for n in FAMILY_N for _, m, d in FAMILY]
+    # g1g2g3 again on the quotient-sized 2N domain (Sec. 4 sizes its transform at 2N)
+    shapes += [(witness.gate_sum(0), n, 3, 1) for n in FAMILY_N]
     rows, clk = _time_shapes(local, shapes, K, W,
                              lambda g, n, d: 7000 + 100 * (g >> 8) + 10 * d + n,
                              lambda g, d: names[(g, d)])
     config = {"workload": "family: the paper's six polynomials (g1g2, g1g2+g3, g1g2+g3+g4, "
                           "g1g2+g3+g4+g5, g1g2g3, g1g2g3g4) as sum gates, one proof of each form at "
-                          "a time, n in {18, 20, 22, 24}; column roots given (untimed)",
+                          "a time, n in {18, 20, 22, 24}, plus g1g2g3 on the 2N domain; column roots "
+                          "given (untimed)",
               "parallelism": f"replicas x{world}", "l2": "n >= 20 inputs larger than L2; no flush"}
-    at22 = [r for r in rows if r["n"] == 22]
+    at22 = [r for r in rows if r["n"] == 22 and "ntt_log_blowup" not in r]
     line = _base_line(args, world, sum(r["sumcheck"]["ms"] + r["ntt"]["ms"] for r in at22), "ms",
                       False, config)
     line["value_is"] = "n=22: sum over the six polynomials of SumCheck ms + NTT ms"
