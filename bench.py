@@ -15,11 +15,15 @@ Lines:
                H2D of the columns, D2H of the proofs and the quotient.
   roofline     dominant kernel launch, integer-pipe bound: algorithmic
                modular multiplications / launch time against
-               152 SMs x 64 IMAD/clk x 2.07 GHz / 272 IMAD per mulmod.
-  cpu_baseline the CPU oracle on a bounded sample (n = 18), scaled to n = 22
-               by the algorithmic-work ratio.
---impl reference times the CPU oracle instead (each step the n = 18 sample,
-scaled), since the paper ships no implementation.
+               SMs x 64 IMAD/clk x max SM clock / 272 IMAD per mulmod, with
+               the SM count and the maximum SM clock queried on the device.
+  cpu_baseline the CPU oracle on the same n = 22 step (one SumCheck and one
+               NTT proof, all host cores, measured once, no scaling), plus
+               the SumCheck proof on one core.
+--impl reference times the CPU oracle instead (the paper ships no
+implementation): each step is the whole n = 22 step; the number of steps is
+capped so that the run stays within a few minutes, and the line reports the
+steps it ran.
 """
 from __future__ import annotations
 
@@ -41,9 +45,41 @@ from paper_2606_16146_gb300.costs import algorithmic_bytes, algorithmic_mulmods,
 
 METRIC = "ZeroCheck prove ms (SumCheck vs NTT) by n, degree; served p50/p99 ms"
 GATE, N_LOG, DEG = 1, 22, 3
-SAMPLE_N = 18
-SM_COUNT, IMAD_PER_CLK, SM_MAX_MHZ, IMAD_PER_MULMOD = 152, 64, 2070.0, 272
+IMAD_PER_CLK, IMAD_PER_MULMOD = 64, 272
+# GB300 figures, used only until the device has been queried (alu_peak)
+SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 ALU_PEAK_MULMOD = SM_COUNT * IMAD_PER_CLK * SM_MAX_MHZ * 1e6 / IMAD_PER_MULMOD
+REF_BUDGET_S = 150.0   # reference arm: timed CPU work per run
+
+
+def query_device(local: int) -> dict:
+    """SM count (CUDA device properties) and maximum SM clock (nvidia-smi) of
+    the GPU, and the integer-pipe roofline they give: SMs x 64 IMAD/clk x
+    clock / 272 IMAD per modular multiplication."""
+    import torch
+    sms = int(torch.cuda.get_device_properties(local).multi_processor_count)
+    mhz, src = None, "nvidia-smi clocks.max.sm"
+    try:
+        out = subprocess.run(["nvidia-smi", f"--id={local}", "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                             timeout=20).stdout.strip()
+        mhz = float(out.splitlines()[0])
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        mhz, src = SM_MAX_MHZ, "fallback 2070 MHz (nvidia-smi unavailable)"
+    return {"sm_count": sms, "sm_max_mhz": mhz, "clock_source": src,
+            "alu_peak_mulmod_s": sms * IMAD_PER_CLK * mhz * 1e6 / IMAD_PER_MULMOD}
+
+
+def set_alu_peak(local: int) -> dict:
+    global SM_COUNT, SM_MAX_MHZ, ALU_PEAK_MULMOD
+    info = query_device(local)
+    SM_COUNT, SM_MAX_MHZ, ALU_PEAK_MULMOD = info["sm_count"], info["sm_max_mhz"], info["alu_peak_mulmod_s"]
+    return info
+
+
+def peak_note() -> str:
+    return (f"queried: {SM_COUNT} SMs x {IMAD_PER_CLK} IMAD/clk x {SM_MAX_MHZ:.0f} MHz / "
+            f"{IMAD_PER_MULMOD} IMAD per mulmod")
 
 
 def _hbm_peak_bytes_s() -> float:
@@ -134,32 +170,81 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_sample(steps: int = 1, warmup: int = 0) -> dict:
-    """Time the CPU oracle on the n = SAMPLE_N witness; scale to n = N_LOG.
-    warmup untimed samples first; the value is the median of `steps` samples."""
+def cpu_model() -> str:
+    """The host CPU's model name (as /proc/cpuinfo or lscpu report it)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
+def _oracle_step(cols, roots):
+    """One SumCheck and one NTT proof by the oracle: (sumcheck s, ntt s)."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.prove_sumcheck(GATE, N_LOG, DEG, cols, roots=roots)
+    t1 = time.perf_counter()
+    oracle.prove_ntt(GATE, N_LOG, DEG, cols, roots=roots)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1
+
+
+_ONE_CORE_SCRIPT = """
+import json, sys, time
+sys.path.insert(0, sys.argv[1])
+import oracle
+from paper_2606_16146_gb300 import witness
+g, n, d, seed = (int(x) for x in sys.argv[2:6])
+cols = witness.generate(g, n, d, seed)
+roots = [oracle.root(c) for c in cols]
+t0 = time.perf_counter()
+oracle.prove_sumcheck(g, n, d, cols, roots=roots)
+print(json.dumps({"s": time.perf_counter() - t0, "threads": oracle.num_threads()}))
+"""
+
+
+def cpu_one_core_sumcheck() -> dict | None:
+    """The oracle's SumCheck proof of the same witness on one core (a child
+    process with OMP_NUM_THREADS=1)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", _ONE_CORE_SCRIPT, ROOT, str(GATE), str(N_LOG), str(DEG),
+                              str(1000 + N_LOG)], capture_output=True, text=True, env=env, timeout=600,
+                             check=True).stdout
+        r = json.loads(out.strip().splitlines()[-1])
+        return {"sumcheck_ms": r["s"] * 1e3, "cores": r["threads"]}
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError) as e:
+        return {"error": str(e)[:200]}
+
+
+def cpu_sample() -> dict:
+    """The CPU oracle on the bench step itself (Plonk n = 22, one proof of each
+    form, roots given), all host cores, measured once with no scaling; plus the
+    SumCheck proof on one core."""
     import oracle
     from paper_2606_16146_gb300 import witness
-    cols = witness.generate(GATE, SAMPLE_N, DEG, 1000 + SAMPLE_N)
+    cols = witness.generate(GATE, N_LOG, DEG, 1000 + N_LOG)
     roots = [oracle.root(c) for c in cols]
-    ts, tn = [], []
-    for it in range(warmup + steps):
-        t0 = time.perf_counter()
-        oracle.prove_sumcheck(GATE, SAMPLE_N, DEG, cols, roots=roots)
-        t1 = time.perf_counter()
-        oracle.prove_ntt(GATE, SAMPLE_N, DEG, cols, roots=roots)
-        t2 = time.perf_counter()
-        if it >= warmup:
-            ts.append(t1 - t0)
-            tn.append(t2 - t1)
-    ks = algorithmic_mulmods("sumcheck", N_LOG) / algorithmic_mulmods("sumcheck", SAMPLE_N)
-    kn = algorithmic_mulmods("ntt", N_LOG) / algorithmic_mulmods("ntt", SAMPLE_N)
-    sc_ms = float(np.median(ts)) * 1e3 * ks
-    nt_ms = float(np.median(tn)) * 1e3 * kn
-    return {"value": sc_ms + nt_ms, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": (f"one SumCheck and one NTT proof of the Plonk witness at n={SAMPLE_N} (median of "
-                       f"{steps} after {warmup} warm-up), scaled to n={N_LOG} by the algorithmic mulmod "
-                       f"ratio (x{ks:.1f} SumCheck, x{kn:.1f} NTT)"),
-            "sumcheck_ms": sc_ms, "ntt_ms": nt_ms, "raw_s": [float(np.median(ts)), float(np.median(tn))]}
+    ts, tn = _oracle_step(cols, roots)
+    del cols
+    one = cpu_one_core_sumcheck()
+    return {"value": (ts + tn) * 1e3, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
+            "cpu": cpu_model(),
+            "sample": (f"the bench step itself: one SumCheck and one NTT proof of the Plonk witness at "
+                       f"n={N_LOG} (seed {1000 + N_LOG}, roots given), measured once on all host cores, "
+                       f"no scaling"),
+            "sumcheck_ms": ts * 1e3, "ntt_ms": tn * 1e3, "one_core": one}
 
 
 def dist_setup():
@@ -190,17 +275,38 @@ def barrier(world: int) -> None:
 
 
 def run_reference(args, world, rank):
+    """The CPU oracle on the bench step (Plonk n = 22, one proof of each form):
+    every step is the whole step, measured, with no scaling.  A step takes the
+    oracle tens of seconds, so warm-up steps are skipped and the timed steps
+    are capped at what fits REF_BUDGET_S (at least one); the line reports the
+    steps it ran."""
     if rank != 0:
         return
-    base = cpu_sample(steps=args.steps, warmup=args.warmup)
-    ms = base["value"]
+    import oracle
+    from paper_2606_16146_gb300 import witness
+    cols = witness.generate(GATE, N_LOG, DEG, 1000 + N_LOG)
+    roots = [oracle.root(c) for c in cols]
+    per = []
+    t_start = time.perf_counter()
+    while len(per) < max(1, args.steps):
+        ts, tn = _oracle_step(cols, roots)
+        per.append((ts + tn) * 1e3)
+        spent = time.perf_counter() - t_start
+        if spent + spent / len(per) > REF_BUDGET_S:
+            break
+    ms = float(np.median(per))
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32x8 (255-bit field, exact)",
-            "data": "synthetic", "config": workload_config(world),
-            "cpu_baseline": {"value": ms, "unit": "ms", "cores": base["cores"], "kind": "oracle",
-                             "sample": base["sample"]},
-            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "steps": len(per), "warmup": 0, "steps_requested": args.steps, "warmup_requested": args.warmup,
+            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32x8 (255-bit field, exact)", "data": "synthetic", "config": workload_config(world),
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
+                             "cpu": cpu_model(),
+                             "sample": (f"each step the whole bench step: one SumCheck and one NTT proof of "
+                                        f"the Plonk witness at n={N_LOG} by the CPU oracle, roots given; "
+                                        f"{len(per)} steps (capped to ~{REF_BUDGET_S:.0f} s of CPU work), "
+                                        f"no warm-up, no scaling")},
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "step_ms": per}
     print(json.dumps(line), flush=True)
 
 
@@ -237,6 +343,7 @@ def run_batched(args, world, rank, local):
     3000+i: one CUDA graph per batch against 64 sequential plain calls, for
     all-SumCheck, all-NTT and cost-model-routed form assignments."""
     import torch
+    device_info = set_alu_peak(local)
     from paper_2606_16146_gb300 import tune, witness, workloads, zc
     from paper_2606_16146_gb300.router import CostModel
     torch.cuda.set_device(local)
@@ -334,9 +441,10 @@ def run_batched(args, world, rank, local):
     line["roofline"] = {"bound": "alu", "kernel": "whole batch graph (all instances)", "achieved": achieved,
                         "peak": ALU_PEAK_MULMOD, "unit": "mulmod/s", "frac": achieved / ALU_PEAK_MULMOD,
                         "traffic": None,
-                        "peak_note": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz / 272 IMAD per mulmod"}
+                        "peak_note": peak_note()}
     line["clocks"] = best["clocks"]
     line["cost_model_ms"] = [[*k, v] for k, v in sorted(model.table.items())]
+    line["device"] = device_info
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_sample_batched(inst, cols, forms)
     if rank == 0:
@@ -376,6 +484,7 @@ def _time_shapes(local, shapes, K, W, seed_of, label_of):
     """One proof of each form at a time per (gate, n, d) shape, column roots
     given (untimed): median CUDA-event ms, roofline ms and fraction, phases."""
     import torch
+    set_alu_peak(local)
     from paper_2606_16146_gb300 import witness, zc
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -474,38 +583,12 @@ def run_family(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
-def run_mulpeak(args, world, rank, local):
-    """Throughput ceiling of the field multiplication alone (csrc/mul_ceiling.cu):
-    products/s of the kernels' multiplier and its variants, and the per-
-    instruction rates they are built from, against the ALU roofline's peak."""
-    import subprocess
-    from paper_2606_16146_gb300 import build
-    exe = build.build_mul_ceiling()
-    env = dict(os.environ, CUDA_VISIBLE_DEVICES=os.environ.get("CUDA_VISIBLE_DEVICES", str(local)))
-    clocks = ClockSampler(local)
-    clocks.start()
-    out = subprocess.run([exe], check=True, capture_output=True, text=True, env=env).stdout
-    clk = clocks.stop()
-    res = json.loads(out.strip().splitlines()[-1])
-    best = res["mulmod_per_s"]["fr_mul_call"]
-    config = {"workload": "field multiplication alone: 152 SMs x 8 CTAs x 256 threads, two dependent "
-                          "product chains per thread, BLS12-381 Fr Montgomery (8 x 32-bit limbs)"}
-    line = _base_line(args, world, best, "mulmod/s", True, config)
-    line["value_is"] = "fr_mul (the kernels' out-of-line multiplier) products per second"
-    line["alu_roofline_peak_mulmod_s"] = ALU_PEAK_MULMOD
-    line["frac_of_alu_roofline"] = {k: v / ALU_PEAK_MULMOD for k, v in res["mulmod_per_s"].items()}
-    line["result"] = res
-    line["clocks"] = clk
-    line["e2e"] = None
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-
-
 def run_served(args, world, rank, local):
     """Poisson request loop (n 12..24, d in {3, 8, 16}), admission by HBM
     footprint against a 180 GB pool, cost-model routing; against the same
     requests one at a time (one slot)."""
     import torch
+    device_info = set_alu_peak(local)
     from paper_2606_16146_gb300 import serve, workloads, zc
     from paper_2606_16146_gb300.router import CostModel
     torch.cuda.set_device(local)
@@ -555,6 +638,7 @@ def run_served(args, world, rank, local):
     line["gpu_launches"] = int(launches)
     line["clocks"] = clk
     line["pool_setup_s"] = t_pool
+    line["device"] = device_info
     line["cost_model_ms"] = [[*k, v] for k, v in sorted(model.table.items())]
     line["e2e"] = None
     line["e2e_note"] = ("latencies are host-observed from arrival to completion; request columns come "
@@ -577,11 +661,10 @@ def main():
     ap.add_argument("--gate", type=int, default=1, choices=[1, 2])
     ap.add_argument("--form", default="both", choices=["both", "sumcheck", "ntt"],
                     help="restrict the step to one form (profiling); the bench line uses both")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "served", "sweep", "family", "mulpeak"],
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "served", "sweep", "family"],
                     help="plain: one Plonk n=22 proof per form (the headline line); batched: 64 "
                          "mixed instances in one graph; served: Poisson request loop; sweep: "
-                         "sizes and degrees; family: the paper's polynomials as sum gates; "
-                         "mulpeak: the field multiplication alone")
+                         "sizes and degrees; family: the paper's polynomials as sum gates")
     ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="served: arrival rates (req/s)")
     ap.add_argument("--requests", type=int, default=200, help="served: requests per rate")
     args = ap.parse_args()
@@ -606,13 +689,11 @@ def main():
     if args.workload == "family":
         run_family(args, world, rank, local)
         return
-    if args.workload == "mulpeak":
-        run_mulpeak(args, world, rank, local)
-        return
     import torch
     from paper_2606_16146_gb300 import witness, zc
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    device_info = set_alu_peak(local)
     ctx = zc.Context(local, max_n=24, max_d=8)
     cols = witness.generate(GATE, N_LOG, DEG, 1000 + N_LOG)
     dcols = [torch.from_numpy(c).to(dev) for c in cols]
@@ -720,7 +801,7 @@ def main():
             "traffic_source": "profiles/ntt_pass_plonk_n22_traffic.md" if traffic else None,
             "algorithmic_mulmods_per_launch": dom[7], "algorithmic_bytes_per_launch": dom[8],
             "hbm_gbs_at_algorithmic_bytes": dom[8] / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None,
-            "peak_note": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz / 272 IMAD per mulmod"}
+            "peak_note": peak_note()}
     by_form = {"sumcheck": {"ms": float(np.median(sc_ms)) if run_sc else None,
                             "roofline_ms": 1e3 * max(algorithmic_mulmods("sumcheck", N_LOG, DEG, GATE) / ALU_PEAK_MULMOD,
                                                       algorithmic_bytes("sumcheck", N_LOG, DEG, GATE) / HBM_PEAK),
@@ -743,9 +824,10 @@ def main():
                 "data": "synthetic", "config": workload_config(world),
                 "e2e": {"value": float(np.median(e2e_ms)), "unit": "ms", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches, "roofline": roof, "clocks": clk, "by_form": by_form}
+                "gpu_launches": launches, "roofline": roof, "clocks": clk, "by_form": by_form,
+                "device": device_info}
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_sample(1)
+            line["cpu_baseline"] = cpu_sample()
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

@@ -60,20 +60,6 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
-MUL_CEILING = os.path.join(BUILD, "mul_ceiling")
-
-
-def build_mul_ceiling(force: bool = False) -> str:
-    """The standalone field-multiplication throughput program (mul_ceiling.cu)."""
-    os.makedirs(BUILD, exist_ok=True)
-    src = os.path.join(CSRC, "mul_ceiling.cu")
-    if force or _stale(MUL_CEILING, [src, os.path.join(CSRC, "zc_field.cuh")]):
-        tmp = MUL_CEILING + f".tmp{os.getpid()}"
-        subprocess.run([nvcc(), "-O3", "-lineinfo", "-std=c++17", *ARCH, "-o", tmp, src], check=True)
-        os.replace(tmp, MUL_CEILING)
-    return MUL_CEILING
-
-
 if __name__ == "__main__":
     import sys
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
