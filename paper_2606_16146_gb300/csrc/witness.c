@@ -17,6 +17,13 @@
  * clears bit 255 and is kept if it is below r (rejection sampling).
  * Values are written canonical, 32 bytes little-endian per element.
  *
+ * zw_generate_edge draws instead from a list of boundary values of the field
+ * (0, 1, 2, r-1, r-2, r - 2^k, 2^k, 2^256 mod r and its square, (r +- 1)/2,
+ * all-ones limbs below r, ...) mixed with uniform draws; no column is solved,
+ * so the gate does not vanish.  The provers' bytes are defined for any
+ * canonical input, and such columns push values next to the modulus and
+ * zero limbs through every carry and conditional subtraction.
+ *
  * Its modular arithmetic (a small Montgomery multiplier over 64-bit words)
  * exists only to construct satisfying inputs; it is not the prover's.
  */
@@ -256,4 +263,76 @@ int zw_generate(uint32_t gate, uint32_t n, uint32_t d, uint64_t seed, int tamper
         return 0;
     }
     return 1;
+}
+
+/* Boundary values of the field, canonical (each < r). */
+static int edge_values(el *out) {
+    const el one = {{1, 0, 0, 0}};
+    int k = 0;
+    el z = {{0, 0, 0, 0}};
+    out[k++] = z;                                   /* 0 */
+    out[k++] = one;                                 /* 1 */
+    out[k++] = addm(one, one);                      /* 2 */
+    el rm1 = negm(one);
+    out[k++] = rm1;                                 /* r - 1 */
+    out[k++] = addm(rm1, rm1);                      /* r - 2 */
+    out[k++] = negm(addm(one, addm(one, one)));     /* r - 3 */
+    const int sh[] = {31, 32, 63, 64, 127, 128, 191, 192, 224, 253, 254};
+    for (unsigned t = 0; t < sizeof sh / sizeof sh[0]; t++) {
+        el p2 = z;
+        p2.v[sh[t] / 64] = 1ULL << (sh[t] % 64);    /* 2^k < r for k <= 254 */
+        out[k++] = p2;                              /* 2^k */
+        out[k++] = negm(p2);                        /* r - 2^k */
+        el m1 = p2;                                 /* 2^k - 1: all-ones limbs */
+        u128 br = 1;
+        for (int i = 0; i < 4; i++) { u128 x = (u128)m1.v[i] - br; m1.v[i] = (uint64_t)x; br = (x >> 127) & 1; }
+        out[k++] = m1;
+    }
+    out[k++] = ONE_M;                               /* 2^256 mod r (Montgomery one) */
+    out[k++] = to_m(RR);                            /* 2^768 mod r */
+    out[k++] = RR;                                  /* 2^512 mod r */
+    out[k++] = negm(ONE_M);                         /* r - R */
+    el half = MODULUS;                              /* (r - 1) / 2 */
+    for (int i = 0; i < 4; i++) half.v[i] = (MODULUS.v[i] >> 1) | (i < 3 ? MODULUS.v[i + 1] << 63 : 0);
+    out[k++] = half;
+    out[k++] = addm(half, one);                     /* (r + 1) / 2 */
+    el top = MODULUS;                               /* r with its low limb cleared: < r */
+    top.v[0] = 0;
+    out[k++] = top;
+    el lowmax = {{~0ULL, ~0ULL, ~0ULL, 0}};         /* 2^192 - 1 */
+    out[k++] = lowmax;
+    el lim = MODULUS;                               /* limbs of r - 1 with the top limb one less */
+    lim.v[0] -= 1;
+    lim.v[3] -= 1;
+    out[k++] = lim;
+    return k;
+}
+
+/* Columns of boundary values (see the header).  only_edges != 0 draws every
+ * element from the boundary list, else half of them (per element) are
+ * uniform.  Column j uses the stream seed ^ (0x9E3779B97F4A7C15 (j+1)), as
+ * zw_generate does.  Returns 0 on success. */
+int zw_generate_edge(uint32_t gate, uint32_t n, uint32_t d, uint64_t seed, int only_edges,
+                     uint8_t *const *cols) {
+    setup();
+    int c;
+    if (gate == 1) { if (d != 3) return 1; c = 8; }
+    else if (gate == 2) { if (d < 2 || d > 64) return 1; c = (int)d + 1; }
+    else if ((gate & 0xff) == 3) {
+        const uint32_t m = gate >> 8;
+        if (d < 2 || d > 64 || m > 63 || d + m > 65) return 1;
+        c = (int)(d + m);
+    } else return 1;
+    el edges[64];
+    const int ne = edge_values(edges);
+    size_t N = (size_t)1 << n;
+    for (int j = 0; j < c; j++) {
+        uint64_t s = seed ^ (0x9E3779B97F4A7C15ULL * (uint64_t)(j + 1));
+        for (size_t k = 0; k < N; k++) {
+            const uint64_t pick = splitmix64(&s);
+            if (!only_edges && (pick & 1)) put(cols[j] + 32 * k, draw(&s, 0));
+            else put(cols[j] + 32 * k, edges[(pick >> 1) % (uint64_t)ne]);
+        }
+    }
+    return 0;
 }

@@ -55,6 +55,8 @@ def _load():
             L = ctypes.CDLL(_LIB_PATH)
             L.zw_generate.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                       ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p]
+            L.zw_generate_edge.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                           ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p]
             _lib = L
     return _lib
 
@@ -75,6 +77,20 @@ def generate(gate: int, n: int, d: int, seed: int, tamper: bool = False) -> list
                              ctypes.cast(ptrs, ctypes.c_void_p))
     if st != 0:
         raise ValueError(f"witness generation failed (status {st})")
+    return cols
+
+
+def generate_edge(gate: int, n: int, d: int, seed: int, only_edges: bool = False) -> list[np.ndarray]:
+    """Columns of boundary field values (0, 1, r-1, r-2^k, 2^k, 2^256 mod r, ...),
+    half of the elements uniform unless ``only_edges``; the gate does not vanish."""
+    c = ncols(gate, d)
+    N = 1 << n
+    cols = [np.empty(N * 32, dtype=np.uint8) for _ in range(c)]
+    ptrs = (ctypes.c_void_p * c)(*[a.ctypes.data for a in cols])
+    st = _load().zw_generate_edge(gate, n, d, seed & (2**64 - 1), 1 if only_edges else 0,
+                                  ctypes.cast(ptrs, ctypes.c_void_p))
+    if st != 0:
+        raise ValueError(f"edge witness generation failed (status {st})")
     return cols
 
 

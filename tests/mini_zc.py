@@ -197,8 +197,18 @@ def prove_ntt(gate, n, d, cols_int, logb=None):
     coefs = [interpolate_h(c) for c in cols_int]
     f = gate_poly(gate, d, coefs)
     q, rem = divide_by_zh(f, N)
-    assert all(x == 0 for x in rem), "witness does not vanish on H"
-    q = (q + [0] * M)[:M]
+    if all(x == 0 for x in rem):
+        q = (q + [0] * M)[:M]
+    else:
+        # f does not vanish on H: q is the degree < M interpolant of f / z_H
+        # on D = {7 w_M^i}, by the inverse DFT on the coset
+        w = omega(logm)
+        vals = []
+        for i in range(M):
+            x = 7 * pow(w, i, R) % R
+            vals.append(horner(f, x) * inv(pow(x, N, R) - 1) % R)
+        minv, sinv = inv(M), inv(7)
+        q = [c * minv * pow(sinv, k, R) % R for k, c in enumerate(dft(vals, inv(w)))]
     qroot = merkle_root(q)
     tr = Transcript(2, gate, n, d, logm)
     for col in cols_int:

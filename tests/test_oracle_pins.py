@@ -305,3 +305,30 @@ def test_witness_generator_satisfies_gate():
         bad = _cols_int(witness.generate(gate, n, d, 9, tamper=True))
         viol = [k for k in range(1 << n) if mz.gate_eval(gate, d, [c[k] for c in bad]) != 0]
         assert viol == [9 % (1 << n)]
+
+
+EDGE_CASES = [(1, 2, 3), (1, 3, 3), (2, 3, 2), (2, 2, 4), (witness.gate_sum(2), 2, 2), (witness.gate_sum(0), 3, 3)]
+
+
+@pytest.mark.parametrize("gate,n,d", EDGE_CASES)
+def test_edge_value_inputs_match_bruteforce(gate, n, d):
+    """Boundary field values (0, 1, r-1, r-2^k, 2^k, ...), gate not satisfied:
+    both oracle provers still equal the big-integer restatement."""
+    cols = witness.generate_edge(gate, n, d, 4242 + n, only_edges=True)
+    ci = _cols_int(cols)
+    assert all(v < R for c in ci for v in c)
+    ref, _, _ = mz.prove_sumcheck(gate, n, d, ci)
+    assert oracle.prove_sumcheck(gate, n, d, cols) == ref
+    pb, q = oracle.prove_ntt(gate, n, d, cols)
+    refn, qref, _ = mz.prove_ntt(gate, n, d, ci)
+    assert mz.ints(q) == qref
+    assert pb == refn
+
+
+def test_edge_witness_covers_the_boundaries():
+    vals = {v for c in _cols_int(witness.generate_edge(2, 8, 4, 1, only_edges=True)) for v in c}
+    for v in (0, 1, 2, R - 1, R - 2, R - 3, 2**254, R - 2**254, 2**32 - 1, R - 2**32, (R - 1) // 2,
+              (R + 1) // 2, 2**256 % R, 2**512 % R):
+        assert v in vals, hex(v)
+    mixed = _cols_int(witness.generate_edge(1, 8, 3, 1))
+    assert any(v not in vals for c in mixed for v in c)
