@@ -210,18 +210,31 @@ void zc_batch_destroy(zc_batch* batch);
  *
  * params: as for zc_prove_sumcheck.  cols: c DEVICE pointers (N*32 canonical
  * bytes each) on the current device.  col_roots: host array of c roots, or
- * NULL to compute them inside the static scratch.  cuda_stream: the stream
- * the work is queued on.  proof: DEVICE buffer of cap bytes; *len receives
- * the proof size.  The call is asynchronous: the proof is ready when the
- * stream reaches it.  The bytes equal zc_prove_sumcheck's.
+ * NULL to compute them inside the static scratch; given roots are copied
+ * from the caller's (pageable) host array by a host-to-device copy queued on
+ * cuda_stream.  cuda_stream: the stream the work is queued on.  proof:
+ * DEVICE buffer of cap bytes; *len receives the proof size.  The call is
+ * asynchronous: the proof is ready when the stream reaches it.  The bytes
+ * equal zc_prove_sumcheck's.
+ *
+ * Errors: argument and size errors are returned at once.  A column value
+ * >= r cannot be reported by the return status, because the call does not
+ * wait for the device: the proof buffer then starts with the four bytes
+ * "ZCE!" instead of "ZCS1", and the caller checks them once the stream has
+ * completed (zc_prove_sumcheck returns ZC_ERR_ARG for the same input).
  *
  * Limits: the instance must fit the 32 MiB scratch (tables c*N*32 bytes plus
- * small per-round buffers, e.g. the Plonk gate up to n = 16); larger
- * instances return ZC_ERR_UNSUPPORTED without launching anything.
+ * small per-round buffers, e.g. the Plonk gate up to n = 16; with
+ * col_roots = NULL also the commitment's node buffers); larger instances
+ * return ZC_ERR_UNSUPPORTED without launching anything.  The environment
+ * variable ZC_STATIC_SCRATCH_BYTES, if set, lowers the usable part of the
+ * scratch (for tests of the size checks).
  * Set-up: the first call on each device looks up the device addresses of the
  * static arrays (cudaGetSymbolAddress) with that device current and copies
  * the field constants into them with synchronous copies, so make that first
- * call outside any stream capture.  Sharing: every call on a device uses the
+ * call outside any stream capture.  The set-up is redone when the device's
+ * CUDA context changes (after cudaDeviceReset the arrays are new), so the
+ * first call after such a reset is a set-up call too.  Sharing: every call on a device uses the
  * same arrays and leaves its data in them (the per-proof state is reset by
  * the call itself), so calls whose work overlaps on the GPU (different
  * streams, or different host threads) race and corrupt each other; order

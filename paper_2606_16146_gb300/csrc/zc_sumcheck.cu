@@ -32,6 +32,7 @@
 // at level 0; the product of d factors lands on level 1-d, which the eq
 // weight (stored at level d) and a per-degree constant for o bring back to 0.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -1379,6 +1380,7 @@ static __device__ __align__(256) fr g_static_tabs[kStaticTabCap];
 
 struct StaticDev {
   bool ready = false;
+  unsigned long long ctx_id = 0;  // the CUDA context the addresses belong to
   void* scratch = nullptr;
   DevConst* dconst = nullptr;
   fr* dtabs = nullptr;
@@ -1387,13 +1389,48 @@ struct StaticDev {
 static StaticDev g_static_dev[kStaticMaxDevices];
 static std::mutex g_static_mu;
 
+// Unique id of the current CUDA context (0 if the driver cannot say).  A
+// cudaDeviceReset followed by new work creates a new primary context in
+// which the static arrays are fresh, so set-up must run again there.
+static unsigned long long current_context_id() {
+  typedef int (*GetCurrentFn)(void**);
+  typedef int (*GetIdFn)(void*, unsigned long long*);
+  static GetCurrentFn get_cur = nullptr;
+  static GetIdFn get_id = nullptr;
+  static bool looked = false;
+  if (!looked) {  // called under g_static_mu
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void**)&get_cur, 12000, cudaEnableDefault, &q1) !=
+            cudaSuccess || q1 != cudaDriverEntryPointSuccess)
+      get_cur = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", (void**)&get_id, 12000, cudaEnableDefault, &q2) !=
+            cudaSuccess || q2 != cudaDriverEntryPointSuccess)
+      get_id = nullptr;
+    cudaGetLastError();
+    looked = true;
+  }
+  void* cu = nullptr;
+  unsigned long long id = 0;
+  if (get_cur && get_id && get_cur(&cu) == 0 && cu && get_id(cu, &id) == 0) return id;
+  return 0;
+}
+
 // Set-up for the current device: look up the device addresses of the static
 // arrays and copy the field constants into them.  Runs on the first call per
-// device (synchronous copies), so that first call must not be inside a
-// stream capture.
+// device and context (synchronous copies), so that first call must not be
+// inside a stream capture.
 static zc_status static_setup(int dev, StaticDev** out) {
   std::lock_guard<std::mutex> lk(g_static_mu);
   StaticDev& S = g_static_dev[dev];
+  // the symbol lookup makes the device's context current (creating it if
+  // needed) and is cheap once the module is loaded
+  void* scratch = nullptr;
+  if (cudaGetSymbolAddress(&scratch, g_static_scratch) != cudaSuccess) {
+    cudaGetLastError();
+    return ZC_ERR_CUDA;
+  }
+  const unsigned long long id = current_context_id();
+  if (S.ready && (id != S.ctx_id || scratch != S.scratch)) S.ready = false;  // a new context
   if (!S.ready) {
     std::vector<fr> tabs;
     static_constants(&S.hconst, &tabs);
@@ -1410,10 +1447,21 @@ static zc_status static_setup(int dev, StaticDev** out) {
       cudaGetLastError();
       return ZC_ERR_CUDA;
     }
+    S.ctx_id = id;
     S.ready = true;
   }
   *out = &S;
   return ZC_OK;
+}
+
+// Usable bytes of the static scratch: all of it, or less when the
+// environment variable ZC_STATIC_SCRATCH_BYTES asks for a smaller limit
+// (tests use it to reach the size checks with small instances).
+static size_t static_scratch_limit() {
+  const char* e = std::getenv("ZC_STATIC_SCRATCH_BYTES");
+  if (!e || !*e) return kStaticScratchBytes;
+  const unsigned long long v = std::strtoull(e, nullptr, 10);
+  return v < kStaticScratchBytes ? (size_t)v : kStaticScratchBytes;
 }
 
 static zc_status static_prove(const zc_params* p, const void* const* cols,
@@ -1430,7 +1478,7 @@ static zc_status static_prove(const zc_params* p, const void* const* cols,
   // carve the static array; reject instances that do not fit
   Arena ar;
   ar.base = static_cast<char*>(S.scratch);
-  ar.cap = kStaticScratchBytes;
+  ar.cap = static_scratch_limit();
   ScBuffers B{};
   if (!sc_carve(ar, P, N, psize, B) || (!roots && ar.used + root_scratch_bytes(c, N) > ar.cap))
     return ZC_ERR_UNSUPPORTED;  // instance larger than the static scratch
