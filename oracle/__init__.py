@@ -139,17 +139,31 @@ def verify_sumcheck(gate, n, d, cols, proof, roots=None) -> bool:
     return bool(acc.value)
 
 
+def domain_word(k: int, s: int | None = None) -> int:
+    """Domain word of the NTT form: 2^k N points, or with s (< k) the
+    step-radix domain of 2^k N + 2^s N points."""
+    return k if s is None else k | ((s + 1) << 8)
+
+
+def domain_size(n: int, d: int, log_blowup: int = 0) -> int:
+    """Number of points M of the NTT domain for a domain word (0: default)."""
+    k, sp1 = log_blowup & 0xFF, (log_blowup >> 8) & 0xFF
+    if not sp1:
+        return 1 << (n + (k or (max(d, 1) - 1).bit_length()))
+    return (1 << (n + k)) + (1 << (n + sp1 - 1))
+
+
 def prove_ntt(gate, n, d, cols, roots=None, log_blowup=0):
-    """NTT ZeroCheck proof bytes and the quotient q (canonical, M*32 bytes)."""
+    """NTT ZeroCheck proof bytes and the quotient q (canonical, M*32 bytes).
+    log_blowup is the domain word (see domain_word); 0 selects the default."""
     C = _Cols(cols)
     rb, rp = _roots_buf(roots)
-    lb = log_blowup or (max(d, 1) - 1).bit_length()
-    M = 1 << (n + lb)
+    M = domain_size(n, d, log_blowup)
     cap = proof_size(2, gate, n, d)
     proof = np.zeros(cap, np.uint8)
     q = np.zeros(M * 32, np.uint8)
     ln = ctypes.c_size_t()
-    st = lib().zo_prove_ntt(gate, n, d, lb, C.p, rp, _ptr(proof), cap, ctypes.byref(ln), _ptr(q))
+    st = lib().zo_prove_ntt(gate, n, d, log_blowup, C.p, rp, _ptr(proof), cap, ctypes.byref(ln), _ptr(q))
     if st != 0:
         raise ValueError(f"oracle prove_ntt status {st}")
     return proof.tobytes()[: ln.value], q
@@ -206,7 +220,7 @@ def root(v) -> bytes:
     a = _buf(v)
     out = np.zeros(32, np.uint8)
     if lib().zo_root(_ptr(a), a.size // 32, _ptr(out)) != 0:
-        raise ValueError("root needs a power-of-two length")
+        raise ValueError("root needs a non-empty vector")
     return out.tobytes()
 
 

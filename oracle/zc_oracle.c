@@ -310,28 +310,33 @@ static void sha256(const uint8_t *m, size_t len, uint8_t out[32]) {
 /* ------------------------------------------------ commitment stand-in -- */
 /* The paper's commitments [g], [q] (Fig. side-by-side-zc, "Commit") are
  * stood in by a binary SHA-256 Merkle root over chunks of 64 canonical
- * elements: leaf = SHA-256(enc(v[64t]) || ... ), node = SHA-256(l || r),
- * root = SHA-256(le64(L) || top).  L must be a power of two. */
+ * elements: leaf t = SHA-256(enc(v[64t]) || ... || enc(v[min(64t+63, L-1)]))
+ * (the last leaf may be shorter), node = SHA-256(l || r), and at a level
+ * with an odd count the last node moves up unchanged; root =
+ * SHA-256(le64(L) || top).  For a power-of-two L every level is even. */
 #define LEAF_ELEMS 64
 
 static int root_of(const uint8_t *canon, size_t L, uint8_t out[32]) {
-    if (L == 0 || (L & (L - 1))) return 0;
-    size_t nl = L < LEAF_ELEMS ? 1 : L / LEAF_ELEMS;
-    size_t per = L < LEAF_ELEMS ? L : LEAF_ELEMS;
+    if (L == 0) return 0;
+    size_t nl = (L + LEAF_ELEMS - 1) / LEAF_ELEMS;
     uint8_t *nodes = (uint8_t *)malloc(nl * 32);
     if (!nodes) return 0;
     #pragma omp parallel for schedule(static)
-    for (long t = 0; t < (long)nl; t++)
-        sha256(canon + (size_t)t * per * 32, per * 32, nodes + (size_t)t * 32);
+    for (long t = 0; t < (long)nl; t++) {
+        size_t first = (size_t)t * LEAF_ELEMS;
+        size_t cnt = L - first < LEAF_ELEMS ? L - first : LEAF_ELEMS;
+        sha256(canon + first * 32, cnt * 32, nodes + (size_t)t * 32);
+    }
     /* each level is written to a fresh buffer: a parallel in-place update
      * would let node i be overwritten while node i/2 is still reading it */
     uint8_t *next = (uint8_t *)malloc((nl / 2 + 1) * 32);
     if (!next) { free(nodes); return 0; }
-    for (size_t cnt = nl; cnt > 1; cnt /= 2) {
+    for (size_t cnt = nl; cnt > 1; cnt = (cnt + 1) / 2) {
         #pragma omp parallel for schedule(static)
         for (long i = 0; i < (long)(cnt / 2); i++)
             sha256(nodes + (size_t)(2 * i) * 32, 64, next + (size_t)i * 32);
-        memcpy(nodes, next, (cnt / 2) * 32);
+        if (cnt & 1) memcpy(next + (cnt / 2) * 32, nodes + (cnt - 1) * 32, 32);
+        memcpy(nodes, next, ((cnt + 1) / 2) * 32);
     }
     free(next);
     uint8_t msg[40];
@@ -646,11 +651,55 @@ int zo_verify_sumcheck(uint32_t gate, uint32_t n, uint32_t d, const uint8_t *con
 
 /* ------------------------------------------------- NTT ZeroCheck ------- */
 /* Fig. side-by-side-zc (left), Sec. 3.2.  Column j holds g_j(w_N^i) at
- * index i.  D = {7 w_M^i}, M = 2^(log_blowup) N, by default next_pow2(d) N;
- * any M >= (d-1) N holds the quotient.
- * Proof = "ZCN1" | gate | n | d | logM | root(q) | g_j(z) ... | q(z). */
+ * index i.  The domain D is given by a domain word w:
+ *   - power of two (w < 256): D = {7 w_M^i}, M = 2^k N with k = w (0: the
+ *     default log2(next_pow2(d)));
+ *   - step radix (w = k | (s+1) << 8, s < k): D = D_big u D_small with
+ *     D_big = {7 w_Mb^i}, Mb = 2^k N, and D_small = {sigma w_Ms^i},
+ *     Ms = 2^s N, sigma = 7 w_{2 Mb}; M = Mb + Ms (Sec. 4, "Degree
+ *     scaling": a non-power-of-two transform, e.g. 3N = 2N + N, built from
+ *     power-of-two transforms plus element-wise work).
+ * Any M >= (d-1)N holds the quotient.  The header and the transcript carry
+ * log2 M (power of two) or log2 Mb | (log2 Ms + 1) << 8 (step radix).
+ * Proof = "ZCN1" | gate | n | d | domain | root(q) | g_j(z) ... | q(z). */
 
 static uint32_t default_blowup(uint32_t d) { return ilog2(d); }
+
+typedef struct { unsigned k, s; int step; size_t N, Mb, Ms, M; uint32_t word; } ntt_domain;
+
+/* The domain with big part 2^k N and, if step, small part 2^s N (s < k),
+ * for size n and degree d; 0 if it is invalid or cannot hold the quotient. */
+static int domain_make(uint32_t n, uint32_t d, unsigned k, int step, unsigned s, ntt_domain *D) {
+    D->k = k; D->s = step ? s : 0; D->step = step;
+    if (n + k > 32 || (step && s >= k)) return 0;
+    D->N = (size_t)1 << n;
+    D->Mb = D->N << k;
+    D->Ms = step ? D->N << s : 0;
+    D->M = D->Mb + D->Ms;
+    /* |D| must hold the quotient's (d-1)N - d + 1 coefficients (Sec. 4,
+     * degree scaling: the NTT size follows the degree of q) */
+    if (D->M < (size_t)(d - 1) * D->N - d + 1) return 0;
+    D->word = step ? (n + k) | ((n + s + 1) << 8) : n + k;
+    return 1;
+}
+
+/* From the caller's domain word (0: the default 2^log2(next_pow2(d)) N). */
+static int domain_of(uint32_t n, uint32_t d, uint32_t w, ntt_domain *D) {
+    if (w >> 16) return 0;
+    const unsigned k = w & 0xff, sp1 = (w >> 8) & 0xff;
+    if (sp1) return k > 0 && domain_make(n, d, k, 1, sp1 - 1, D);
+    return domain_make(n, d, k ? k : default_blowup(d), 0, 0, D);
+}
+
+/* From the proof header's word (log2 M, or log2 Mb | (log2 Ms + 1) << 8). */
+static int domain_of_header(uint32_t n, uint32_t d, uint32_t W, ntt_domain *D) {
+    if (W >> 16) return 0;
+    const unsigned lb = W & 0xff, sl = (W >> 8) & 0xff;
+    if (lb < n) return 0;
+    if (!sl) return domain_make(n, d, lb - n, 0, 0, D);
+    if (sl < n + 1) return 0;
+    return domain_make(n, d, lb - n, 1, sl - 1 - n, D);
+}
 
 /* coefficients of g from its values on H: N^{-1} sum_i e_i w_N^{-ik} */
 static void intt_h(fe *a, unsigned n) {
@@ -661,47 +710,31 @@ static void intt_h(fe *a, unsigned n) {
     for (long k = 0; k < (long)N; k++) a[k] = f_mul(a[k], ninv);
 }
 
-/* evaluations of the coefficient vector c (length N) on the coset 7 <w_M> */
-static void coset_lde(const fe *coef, unsigned n, unsigned logm, fe *out) {
+/* evaluations of the coefficient vector c (length N) on the coset
+ * shift <w_M>: out[i] = sum_k c[k] (shift w_M^i)^k */
+static void coset_lde_at(const fe *coef, unsigned n, unsigned logm, fe shift, fe *out) {
     size_t N = (size_t)1 << n, M = (size_t)1 << logm;
-    /* out[k] = coef[k] * 7^k for k < N, zero above */
-    powers(f_from_u64(7), N, out);
+    /* out[k] = coef[k] * shift^k for k < N, zero above */
+    powers(shift, N, out);
     #pragma omp parallel for schedule(static)
     for (long k = 0; k < (long)M; k++)
         out[k] = (size_t)k < N ? f_mul(coef[k], out[k]) : f_zero();
     ntt_inplace(out, logm, root_of_unity(logm));
 }
 
-int zo_prove_ntt(uint32_t gate, uint32_t n, uint32_t d, uint32_t log_blowup,
-                 const uint8_t *const *cols, const uint8_t *roots_in,
-                 uint8_t *proof, size_t cap, size_t *len, uint8_t *q_out) {
-    field_init();
-    int c = gate_cols(gate, d);
-    if (c < 0 || n < 1 || n > 28) return 1;
-    if (log_blowup == 0) log_blowup = default_blowup(d);
-    /* |D| must hold the quotient's (d-1)N - d + 1 coefficients (Sec. 4,
-     * degree scaling: the NTT size follows the degree of q) */
-    if ((1u << log_blowup) + 1 < d) return 1;
-    unsigned logm = n + log_blowup;
-    if (logm > 32) return 1;
-    size_t need; zo_proof_size(2, gate, n, d, &need);
-    if (cap < need) return 6;
+static void coset_lde(const fe *coef, unsigned n, unsigned logm, fe *out) {
+    coset_lde_at(coef, n, logm, f_from_u64(7), out);
+}
+
+/* f-hat / z_H at the M = 2^logm points x_i = shift w_M^i of a coset:
+ * evaluations of the g_j there (coset LDE), the gate pointwise, then the
+ * element-wise division by z_H(x_i) = x_i^N - 1.  fh, tmp: M entries. */
+static void quotient_evals(uint32_t gate, uint32_t d, int c, fe *const *G, unsigned n, unsigned logm,
+                           fe shift, fe *fh, fe *tmp) {
     size_t N = (size_t)1 << n, M = (size_t)1 << logm;
-
-    fe *G[65];
-    if (!load_cols(cols, c, N, G)) { free_cols(G, c); return 1; }
-    uint8_t *roots = (uint8_t *)malloc(32 * (size_t)c);
-    col_roots(cols, c, N, roots_in, roots);
-
-    /* 1. g_j <- INTT_H(evals g_j) */
-    for (int j = 0; j < c; j++) intt_h(G[j], n);
-
-    /* 2-4. evals of g_j on D, f-hat = gate(g-hat) pointwise */
-    fe *fh = (fe *)malloc(M * sizeof(fe));
-    fe *tmp = (fe *)malloc(M * sizeof(fe));
     if (gate == GATE_PLONK) {
         fe *L[8];
-        for (int j = 0; j < 8; j++) { L[j] = (fe *)malloc(M * sizeof(fe)); coset_lde(G[j], n, logm, L[j]); }
+        for (int j = 0; j < 8; j++) { L[j] = (fe *)malloc(M * sizeof(fe)); coset_lde_at(G[j], n, logm, shift, L[j]); }
         #pragma omp parallel for schedule(static)
         for (long i = 0; i < (long)M; i++) {
             fe x[8];
@@ -712,54 +745,115 @@ int zo_prove_ntt(uint32_t gate, uint32_t n, uint32_t d, uint32_t log_blowup,
     } else {
         /* running product of the first d columns, then minus o (product gate)
          * or plus the single columns (sum gate) */
-        coset_lde(G[0], n, logm, fh);
+        coset_lde_at(G[0], n, logm, shift, fh);
         for (uint32_t j = 1; j < d; j++) {
-            coset_lde(G[j], n, logm, tmp);
+            coset_lde_at(G[j], n, logm, shift, tmp);
             #pragma omp parallel for schedule(static)
             for (long i = 0; i < (long)M; i++) fh[i] = f_mul(fh[i], tmp[i]);
         }
         if ((gate & 0xff) == GATE_PRODUCT) {
-            coset_lde(G[d], n, logm, tmp);
+            coset_lde_at(G[d], n, logm, shift, tmp);
             #pragma omp parallel for schedule(static)
             for (long i = 0; i < (long)M; i++) fh[i] = f_sub(fh[i], tmp[i]);
         } else {
-            /* sum gate: plus g_{d+1} .. g_{d+m} */
             for (int j = (int)d; j < c; j++) {
-                coset_lde(G[j], n, logm, tmp);
+                coset_lde_at(G[j], n, logm, shift, tmp);
                 #pragma omp parallel for schedule(static)
                 for (long i = 0; i < (long)M; i++) fh[i] = f_add(fh[i], tmp[i]);
             }
         }
     }
-
-    /* evals of z_H = x^N - 1 on D, then element-wise division */
-    fe wM = root_of_unity(logm), seven = f_from_u64(7);
-    powers(wM, M, tmp);                                   /* w_M^i */
+    /* evals of z_H = x^N - 1 at x_i = shift w_M^i, then element-wise division */
+    powers(root_of_unity(logm), M, tmp);                  /* w_M^i */
     #pragma omp parallel for schedule(static)
     for (long i = 0; i < (long)M; i++) {
-        fe xi = f_mul(seven, tmp[i]);                     /* x_i = 7 w_M^i */
+        fe xi = f_mul(shift, tmp[i]);
         tmp[i] = f_sub(f_pow_u64(xi, N), f_one());
     }
     f_batch_inv(tmp, M);
     #pragma omp parallel for schedule(static)
     for (long i = 0; i < (long)M; i++) fh[i] = f_mul(fh[i], tmp[i]);
+}
 
-    /* 5. q <- INTT_D(evals q): q[k] = M^{-1} 7^{-k} sum_i qhat_i w_M^{-ik} */
-    ntt_inplace(fh, logm, f_inv(wM));
+/* INTT on a coset, in place: v[k] <- M^{-1} shift^{-k} sum_i v[i] w_M^{-ik},
+ * the coefficients of the degree < M polynomial with those values at the
+ * points shift w_M^i.  tmp: M entries. */
+static void coset_intt(fe *v, unsigned logm, fe shift, fe *tmp) {
+    size_t M = (size_t)1 << logm;
+    ntt_inplace(v, logm, f_inv(root_of_unity(logm)));
     fe minv = f_inv(f_from_u64(M));
-    powers(f_inv(seven), M, tmp);                         /* 7^{-k} */
+    powers(f_inv(shift), M, tmp);
     #pragma omp parallel for schedule(static)
-    for (long k = 0; k < (long)M; k++)
-        fh[k] = f_mul(fh[k], f_mul(minv, tmp[k]));
+    for (long k = 0; k < (long)M; k++) v[k] = f_mul(v[k], f_mul(minv, tmp[k]));
+}
+
+int zo_prove_ntt(uint32_t gate, uint32_t n, uint32_t d, uint32_t log_blowup,
+                 const uint8_t *const *cols, const uint8_t *roots_in,
+                 uint8_t *proof, size_t cap, size_t *len, uint8_t *q_out) {
+    field_init();
+    int c = gate_cols(gate, d);
+    if (c < 0 || n < 1 || n > 28) return 1;
+    ntt_domain D;
+    if (!domain_of(n, d, log_blowup, &D)) return 1;
+    size_t need; zo_proof_size(2, gate, n, d, &need);
+    if (cap < need) return 6;
+    size_t N = D.N, M = D.M, Mb = D.Mb, Ms = D.Ms;
+
+    fe *G[65];
+    if (!load_cols(cols, c, N, G)) { free_cols(G, c); return 1; }
+    uint8_t *roots = (uint8_t *)malloc(32 * (size_t)c);
+    col_roots(cols, c, N, roots_in, roots);
+
+    /* 1. g_j <- INTT_H(evals g_j) */
+    for (int j = 0; j < c; j++) intt_h(G[j], n);
+
+    /* 2-5 on D_big: qhat = gate(ghat) / z_H, then q_big <- INTT_D_big(qhat):
+     * the degree < Mb polynomial that matches q on D_big */
+    const fe seven = f_from_u64(7);
+    fe *q = (fe *)malloc(M * sizeof(fe));
+    fe *tmp = (fe *)malloc(Mb * sizeof(fe));
+    quotient_evals(gate, d, c, G, n, n + D.k, seven, q, tmp);
+    coset_intt(q, n + D.k, seven, tmp);
+    if (D.step) {
+        /* step radix: q = q_big + (x^Mb - 7^Mb) q_small with deg q_small < Ms.
+         * On D_small x^Mb = sigma^Mb, so q_small there is
+         * (qhat - q_big) / (sigma^Mb - 7^Mb): evaluate q_big on D_small
+         * (reduce it modulo x^Ms - sigma^Ms, then a coset NTT of Ms points),
+         * subtract, scale, and interpolate with a coset INTT of Ms points. */
+        const fe sigma = f_mul(seven, root_of_unity(n + D.k + 1));
+        fe *hs = (fe *)malloc(Ms * sizeof(fe)), *vs = (fe *)malloc(Ms * sizeof(fe));
+        fe *t2 = (fe *)malloc(Ms * sizeof(fe));
+        quotient_evals(gate, d, c, G, n, n + D.s, sigma, hs, t2);
+        const fe sms = f_pow_u64(sigma, Ms);
+        const size_t parts = Mb / Ms;
+        #pragma omp parallel for schedule(static)
+        for (long kk = 0; kk < (long)Ms; kk++) {
+            fe acc = f_zero();                            /* Horner in sigma^Ms */
+            for (size_t m = parts; m-- > 0;) acc = f_add(f_mul(acc, sms), q[(size_t)kk + m * Ms]);
+            t2[kk] = acc;
+        }
+        coset_lde_at(t2, n + D.s, n + D.s, sigma, vs);   /* q_big on D_small */
+        const fe s7mb = f_pow_u64(seven, Mb);
+        const fe kinv = f_inv(f_sub(f_pow_u64(sigma, Mb), s7mb));
+        #pragma omp parallel for schedule(static)
+        for (long i = 0; i < (long)Ms; i++) hs[i] = f_mul(f_sub(hs[i], vs[i]), kinv);
+        coset_intt(hs, n + D.s, sigma, t2);               /* q_small */
+        #pragma omp parallel for schedule(static)
+        for (long kk = 0; kk < (long)Ms; kk++) {
+            q[kk] = f_sub(q[kk], f_mul(s7mb, hs[kk]));
+            q[Mb + (size_t)kk] = hs[kk];
+        }
+        free(hs); free(vs); free(t2);
+    }
 
     uint8_t *qb = q_out ? q_out : (uint8_t *)malloc(M * 32);
     #pragma omp parallel for schedule(static)
-    for (long k = 0; k < (long)M; k++) f_to_bytes(fh[k], qb + (size_t)k * 32);
+    for (long k = 0; k < (long)M; k++) f_to_bytes(q[k], qb + (size_t)k * 32);
     uint8_t qroot[32];
     root_of(qb, M, qroot);
 
     /* 6. r <- Hash([g], [q]); re-squeeze while z lies in H */
-    transcript tr; tr_init(&tr, 2, gate, n, d, logm);
+    transcript tr; tr_init(&tr, 2, gate, n, d, D.word);
     for (int j = 0; j < c; j++) tr_absorb(&tr, roots + 32 * j, 32);
     tr_absorb(&tr, qroot, 32);
     fe z;
@@ -767,7 +861,7 @@ int zo_prove_ntt(uint32_t gate, uint32_t n, uint32_t d, uint32_t log_blowup,
 
     /* 7. open g_j(z), q(z) by Horner */
     memcpy(proof, "ZCN1", 4);
-    le32(proof + 4, gate); le32(proof + 8, n); le32(proof + 12, d); le32(proof + 16, logm);
+    le32(proof + 4, gate); le32(proof + 8, n); le32(proof + 12, d); le32(proof + 16, D.word);
     memcpy(proof + 20, qroot, 32);
     uint8_t *pp = proof + 52;
     for (int j = 0; j < c; j++) {
@@ -776,11 +870,11 @@ int zo_prove_ntt(uint32_t gate, uint32_t n, uint32_t d, uint32_t log_blowup,
         f_to_bytes(y, pp); pp += 32;
     }
     fe tq = f_zero();
-    for (size_t k = M; k-- > 0;) tq = f_add(f_mul(tq, z), fh[k]);
+    for (size_t k = M; k-- > 0;) tq = f_add(f_mul(tq, z), q[k]);
     f_to_bytes(tq, pp);
     *len = need;
     if (!q_out) free(qb);
-    free(fh); free(tmp); free(roots); free_cols(G, c);
+    free(q); free(tmp); free(roots); free_cols(G, c);
     return 0;
 }
 
@@ -796,13 +890,14 @@ int zo_verify_ntt(uint32_t gate, uint32_t n, uint32_t d, const uint8_t *const *c
     if (c < 0 || n < 1 || n > 28) return 1;
     size_t need; zo_proof_size(2, gate, n, d, &need);
     if (len != need || memcmp(proof, "ZCN1", 4) != 0) return 1;
-    uint32_t logm = 0;
-    for (int i = 3; i >= 0; i--) logm = (logm << 8) | proof[16 + i];
-    if (logm < n || logm > 32 || (1u << (logm - n)) + 1 < d) return 1;
+    uint32_t word = 0;
+    for (int i = 3; i >= 0; i--) word = (word << 8) | proof[16 + i];
+    ntt_domain D;
+    if (!domain_of_header(n, d, word, &D)) return 1;
     uint8_t hdr[20]; memcpy(hdr, "ZCN1", 4);
-    le32(hdr + 4, gate); le32(hdr + 8, n); le32(hdr + 12, d); le32(hdr + 16, logm);
+    le32(hdr + 4, gate); le32(hdr + 8, n); le32(hdr + 12, d); le32(hdr + 16, word);
     if (memcmp(hdr, proof, 20) != 0) return 1;
-    size_t N = (size_t)1 << n, M = (size_t)1 << logm;
+    size_t N = (size_t)1 << n, M = D.M;
     int ok = 1;
 
     uint8_t qroot[32];
@@ -811,7 +906,7 @@ int zo_verify_ntt(uint32_t gate, uint32_t n, uint32_t d, const uint8_t *const *c
 
     uint8_t *roots = (uint8_t *)malloc(32 * (size_t)c);
     col_roots(cols, c, N, roots_in, roots);
-    transcript tr; tr_init(&tr, 2, gate, n, d, logm);
+    transcript tr; tr_init(&tr, 2, gate, n, d, word);
     for (int j = 0; j < c; j++) tr_absorb(&tr, roots + 32 * j, 32);
     free(roots);
     tr_absorb(&tr, proof + 20, 32);

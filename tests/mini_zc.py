@@ -40,12 +40,15 @@ def sha(m: bytes) -> bytes:
 
 
 def merkle_root(vals) -> bytes:
+    """Leaves of 64 elements (the last may be shorter), pairwise SHA-256 up a
+    binary tree whose odd last node moves up unchanged, then the length."""
     L = len(vals)
-    assert L & (L - 1) == 0
-    per = min(L, 64)
-    nodes = [sha(b"".join(enc(v) for v in vals[i:i + per])) for i in range(0, L, per)]
+    nodes = [sha(b"".join(enc(v) for v in vals[i:i + 64])) for i in range(0, L, 64)]
     while len(nodes) > 1:
-        nodes = [sha(nodes[2 * i] + nodes[2 * i + 1]) for i in range(len(nodes) // 2)]
+        nxt = [sha(nodes[2 * i] + nodes[2 * i + 1]) for i in range(len(nodes) // 2)]
+        if len(nodes) % 2:
+            nxt.append(nodes[-1])
+        nodes = nxt
     return sha(L.to_bytes(8, "little") + nodes[0])
 
 
@@ -188,12 +191,43 @@ def divide_by_zh(f, N):
     return q, f[:N]
 
 
-def prove_ntt(gate, n, d, cols_int, logb=None):
-    N = 1 << n
+def ntt_domain(n, d, logb=None):
+    """Points of the NTT domain and its header word.  logb: None (default
+    2^ceil(log2 d) N), k (2^k N points), or (k, s): the step-radix domain
+    {7 w_{2^k N}^i} u {7 w_{2^(k+1) N} w_{2^s N}^i}."""
     if logb is None:
         logb = (d - 1).bit_length()
-    logm = n + logb
-    M = 1 << logm
+    if isinstance(logb, tuple):
+        k, s = logb
+        Mb, Ms = 1 << (n + k), 1 << (n + s)
+        sigma = 7 * omega(n + k + 1) % R
+        pts = [7 * pow(omega(n + k), i, R) % R for i in range(Mb)]
+        pts += [sigma * pow(omega(n + s), i, R) % R for i in range(Ms)]
+        return pts, (n + k) | ((n + s + 1) << 8)
+    M = 1 << (n + logb)
+    return [7 * pow(omega(n + logb), i, R) % R for i in range(M)], n + logb
+
+
+def interpolate(points, vals):
+    """Lagrange: the coefficients of the degree < len(points) polynomial."""
+    m = len(points)
+    out = [0] * m
+    for i, (xi, yi) in enumerate(zip(points, vals)):
+        num, den = [1], 1
+        for j, xj in enumerate(points):
+            if j != i:
+                num = pmul(num, [(-xj) % R, 1])
+                den = den * (xi - xj) % R
+        sc = yi * inv(den) % R
+        for t, cf in enumerate(num):
+            out[t] = (out[t] + cf * sc) % R
+    return out
+
+
+def prove_ntt(gate, n, d, cols_int, logb=None):
+    N = 1 << n
+    pts, word = ntt_domain(n, d, logb)
+    M = len(pts)
     coefs = [interpolate_h(c) for c in cols_int]
     f = gate_poly(gate, d, coefs)
     q, rem = divide_by_zh(f, N)
@@ -201,16 +235,11 @@ def prove_ntt(gate, n, d, cols_int, logb=None):
         q = (q + [0] * M)[:M]
     else:
         # f does not vanish on H: q is the degree < M interpolant of f / z_H
-        # on D = {7 w_M^i}, by the inverse DFT on the coset
-        w = omega(logm)
-        vals = []
-        for i in range(M):
-            x = 7 * pow(w, i, R) % R
-            vals.append(horner(f, x) * inv(pow(x, N, R) - 1) % R)
-        minv, sinv = inv(M), inv(7)
-        q = [c * minv * pow(sinv, k, R) % R for k, c in enumerate(dft(vals, inv(w)))]
+        # on the domain's points
+        vals = [horner(f, x) * inv(pow(x, N, R) - 1) % R for x in pts]
+        q = interpolate(pts, vals)
     qroot = merkle_root(q)
-    tr = Transcript(2, gate, n, d, logm)
+    tr = Transcript(2, gate, n, d, word)
     for col in cols_int:
         tr.absorb(merkle_root(col))
     tr.absorb(qroot)
@@ -218,7 +247,7 @@ def prove_ntt(gate, n, d, cols_int, logb=None):
         z = tr.squeeze()
         if pow(z, N, R) != 1:
             break
-    out = b"ZCN1" + b"".join(x.to_bytes(4, "little") for x in (gate, n, d, logm)) + qroot
+    out = b"ZCN1" + b"".join(x.to_bytes(4, "little") for x in (gate, n, d, word)) + qroot
     for cf in coefs:
         out += enc(horner(cf, z))
     out += enc(horner(q, z))

@@ -332,3 +332,75 @@ def test_edge_witness_covers_the_boundaries():
         assert v in vals, hex(v)
     mixed = _cols_int(witness.generate_edge(1, 8, 3, 1))
     assert any(v not in vals for c in mixed for v in c)
+
+
+# ---- step-radix NTT domain (Sec. 4, "Degree scaling": 3N = 2N + N, 5N = 4N + N)
+
+STEP_CASES = [(1, 3, 3, (1, 0)), (2, 3, 4, (1, 0)), (2, 2, 6, (2, 0)), (2, 3, 7, (2, 1)),
+              (2, 2, 3, (1, 0)), (witness.gate_sum(1), 3, 4, (1, 0)), (witness.gate_sum(0), 2, 4, (1, 0))]
+
+
+@pytest.mark.parametrize("gate,n,d,ks", STEP_CASES)
+def test_ntt_step_radix_matches_long_division(gate, n, d, ks):
+    """Honest witness on a 2^k N + 2^s N domain: the quotient is the long
+    division of f by x^N - 1, padded to M; proof bytes as the restatement."""
+    cols = witness.generate(gate, n, d, 500 + n * d)
+    w = oracle.domain_word(*ks)
+    pb, q = oracle.prove_ntt(gate, n, d, cols, log_blowup=w)
+    ref, qref, _ = mz.prove_ntt(gate, n, d, _cols_int(cols), logb=ks)
+    assert len(qref) == oracle.domain_size(n, d, w) == ((1 << ks[0]) + (1 << ks[1])) << n
+    assert mz.ints(q) == qref
+    assert pb == ref
+    assert oracle.verify_ntt(gate, n, d, cols, pb, q)
+
+
+@pytest.mark.parametrize("gate,n,d,ks", [(1, 2, 3, (1, 0)), (2, 2, 4, (1, 0)), (2, 1, 6, (2, 0)),
+                                         (2, 2, 5, (2, 1))])
+def test_ntt_step_radix_interpolates_nonvanishing(gate, n, d, ks):
+    """Witness that does not vanish on H: q is the degree < M interpolant of
+    f / z_H on the M explicit points of D_big u D_small (Lagrange)."""
+    cols = witness.generate_edge(gate, n, d, 77 + n)
+    w = oracle.domain_word(*ks)
+    pb, q = oracle.prove_ntt(gate, n, d, cols, log_blowup=w)
+    ref, qref, _ = mz.prove_ntt(gate, n, d, _cols_int(cols), logb=ks)
+    assert mz.ints(q) == qref
+    assert pb == ref
+
+
+def test_ntt_step_radix_identity_and_rejections():
+    gate, n, d = 2, 6, 4
+    cols = witness.generate(gate, n, d, 61)
+    w = oracle.domain_word(1, 0)                      # 3N
+    pb, q = oracle.prove_ntt(gate, n, d, cols, log_blowup=w)
+    qi = mz.ints(q)
+    N = 1 << n
+    qlen = (d - 1) * N - d + 1
+    assert len(qi) == 3 * N and all(x == 0 for x in qi[qlen:]) and qi[qlen - 1] != 0
+    coefs = [mz.interpolate_h(c) for c in _cols_int(cols)]
+    rng = random.Random(5)
+    for _ in range(3):
+        z = rng.randrange(R)
+        ys = [mz.horner(cf, z) for cf in coefs]
+        assert mz.gate_eval(gate, d, ys) == mz.horner(qi, z) * (pow(z, N, R) - 1) % R
+    # same quotient polynomial as the power-of-two 4N domain, other bytes
+    pb4, q4 = oracle.prove_ntt(gate, n, d, cols)
+    assert mz.ints(q4)[:3 * N] == qi and pb4 != pb
+    # tampered witness or quotient: rejected
+    bad = witness.generate(gate, n, d, 61, tamper=True)
+    pbb, qb = oracle.prove_ntt(gate, n, d, bad, log_blowup=w)
+    assert not oracle.verify_ntt(gate, n, d, bad, pbb, qb)
+    q2 = np.array(q, copy=True)
+    q2[32 * 5] ^= 1
+    assert not oracle.verify_ntt(gate, n, d, cols, pb, q2)
+    # domains that cannot hold q, or malformed words
+    with pytest.raises(ValueError):
+        oracle.prove_ntt(2, 4, 6, witness.generate(2, 4, 6, 1), log_blowup=oracle.domain_word(1, 0))
+    with pytest.raises(ValueError):
+        oracle.prove_ntt(gate, n, d, cols, log_blowup=oracle.domain_word(1, 1))   # s must be < k
+
+
+@pytest.mark.parametrize("L", [1, 3, 5, 63, 64, 65, 96, 100, 192, 200, 3 * 1024, 5 * 512 + 64])
+def test_merkle_root_any_length(L):
+    rng = random.Random(L)
+    vals = [rng.randrange(R) for _ in range(L)]
+    assert oracle.root(oracle.ints_to_bytes(vals)) == mz.merkle_root(vals)
