@@ -476,8 +476,12 @@ def cpu_sample_batched(inst, cols, forms):
                       f"all 64 by algorithmic mulmods (x{mm_all / mm_s:.1f})"}
 
 
+# (gate, n, d[, NTT domain word]): Plonk n = 12, 20, 22 and the product gate
+# at n = 22, then the other domains of Sec. 4's degree scaling: Plonk on the
+# quotient-sized 2N and the step-radix 3N = 2N + N; the product gate d = 4 on
+# 3N (against its default 4N) and d = 6 on 5N = 4N + N (against 8N).
 SWEEP = [(1, 12, 3), (1, 20, 3), (1, 22, 3), (2, 22, 2), (2, 22, 4), (2, 22, 8), (2, 22, 16), (2, 22, 32),
-         (1, 22, 3, 1)]   # last: Plonk with the quotient-sized 2N domain
+         (1, 22, 3, 1), (1, 22, 3, 0x101), (2, 22, 4, 0x101), (2, 22, 6), (2, 22, 6, 0x102)]
 
 
 def _time_shapes(local, shapes, K, W, seed_of, label_of):
@@ -536,7 +540,8 @@ def run_sweep(args, world, rank, local):
                              lambda g, d: "plonk" if g == 1 else "product")
     head = rows[2]
     config = {"workload": "sweep: one proof of each form at a time; Plonk n=12, 20, 22 and product gate "
-                          "n=22, d in {2, 4, 8, 16, 32}; column roots given (untimed)",
+                          "n=22, d in {2, 4, 8, 16, 32}; NTT domains 2N and 3N = 2N + N for Plonk n=22, "
+                          "3N for d=4 and 5N = 4N + N against 8N for d=6; column roots given (untimed)",
               "parallelism": f"replicas x{world}", "l2": "n >= 20 inputs larger than L2; no flush"}
     line = _base_line(args, world, head["sumcheck"]["ms"] + head["ntt"]["ms"], "ms", False, config)
     line["value_is"] = "Plonk n=22: SumCheck ms + NTT ms"

@@ -49,13 +49,17 @@
  *   SumCheck: "ZCS1" | u32 gate | u32 n | u32 d | G_i(t) for i = 1..n,
  *             t = 0..d+1 | v_j = the columns' MLEs at alpha, j = 1..c.
  *             Size 16 + 32 (n (d + 2) + c).
- *   NTT:      "ZCN1" | u32 gate | u32 n | u32 d | u32 log2 M | root(q) |
- *             g_j(z), j = 1..c | q(z).  Size 20 + 32 + 32 (c + 1).
+ *   NTT:      "ZCN1" | u32 gate | u32 n | u32 d | u32 domain | root(q) |
+ *             g_j(z), j = 1..c | q(z).  Size 20 + 32 + 32 (c + 1).  domain
+ *             is log2 M, or log2 Mb | (log2 Ms + 1) << 8 for a step-radix
+ *             domain of Mb + Ms points (see zc_params).
  * Transcript: S0 = SHA-256("zerocheck-gb300/v1" | u32 form | u32 gate |
- * u32 n | u32 d | u32 log2 M (0 for SumCheck)); absorb(m): S = SHA-256(S|m);
+ * u32 n | u32 d | u32 domain (0 for SumCheck)); absorb(m): S = SHA-256(S|m);
  * squeeze: S = SHA-256(S | 0x43), challenge = int_le(S) mod r.  The column
  * and quotient commitments are stood in by root(v): a binary SHA-256 Merkle
- * tree over leaves of 64 canonical elements, root = SHA-256(u64 len | top).
+ * tree over leaves of 64 canonical elements (the last leaf may be shorter;
+ * at a level with an odd count the last node moves up unchanged),
+ * root = SHA-256(u64 len | top).
  */
 #ifndef ZC_H
 #define ZC_H
@@ -83,10 +87,20 @@ typedef enum { ZC_GATE_PLONK = 1, ZC_GATE_PRODUCT = 2, ZC_GATE_SUM = 3 } zc_gate
 typedef enum { ZC_FORM_SUMCHECK = 1, ZC_FORM_NTT = 2 } zc_form;
 
 /* One ZeroCheck instance: gate word, n (N = 2^n, 1 <= n <= 28), degree d
- * (3 for Plonk, 2..64 for the product and sum gates) and log2(|D| / N) for the NTT
- * form (0 selects log2(next_pow2(d)); |D| = 2^log_blowup N must hold the
- * quotient, 2^log_blowup >= d - 1: Sec. 4 sizes the quotient transform by
- * the degree of q, e.g. 2N for degree 3).  SumCheck ignores log_blowup. */
+ * (3 for Plonk, 2..64 for the product and sum gates) and the NTT form's
+ * domain word log_blowup (SumCheck ignores it):
+ *   - 0: |D| = next_pow2(d) N, the coset 7 <w_|D|>;
+ *   - k (1..): |D| = 2^k N, the coset 7 <w_{2^k N}>;
+ *   - ZC_DOMAIN_STEP(k, s), s < k: the step-radix domain of 2^k N + 2^s N
+ *     points, 7 <w_{2^k N}> u sigma <w_{2^s N}> with sigma = 7 w_{2^{k+1} N}
+ *     (Sec. 4, "Degree scaling": a non-power-of-two transform such as
+ *     3N = 2N + N built from power-of-two transforms plus element-wise work).
+ *     The library proves s = 0 (2^k N + N: 3N, 5N, 9N, ...).
+ * |D| must hold the quotient's (d-1)N - d + 1 coefficients (Sec. 4 sizes the
+ * quotient transform by the degree of q: 2N for degree 3, 3N for degree 4).
+ * The NTT proof header and transcript carry log2 |D|, or for a step-radix
+ * domain log2(2^k N) | (log2(2^s N) + 1) << 8; q has |D| coefficients. */
+#define ZC_DOMAIN_STEP(k, s) ((uint32_t)(k) | (((uint32_t)(s) + 1u) << 8))
 typedef struct {
   uint32_t gate, n, d;
   uint32_t log_blowup;
@@ -129,9 +143,9 @@ zc_status zc_prove_sumcheck(zc_ctx* ctx, const zc_params* params, const void* co
 
 /* NTT-form ZeroCheck proof (Fig. side-by-side-zc left; Sec. 3.2).
  * Arguments as for zc_prove_sumcheck.  q_out: NULL, or M*32 bytes
- * (M = N 2^log_blowup) that receive the quotient coefficients q_0..q_{M-1},
- * canonical, device memory when q_on_device != 0.  Asynchronous when the
- * columns, proof and q_out are all device memory. */
+ * (M = |D| points of the domain, see zc_params) that receive the quotient coefficients q_0..q_{M-1},
+ * canonical, device memory when q_on_device != 0 (M = |D|, see zc_params).
+ * Asynchronous when the columns, proof and q_out are all device memory. */
 zc_status zc_prove_ntt(zc_ctx* ctx, const zc_params* params, const void* const* cols,
                        int cols_on_device, const uint8_t (*col_roots)[32], void* cuda_stream,
                        uint8_t* proof, size_t cap, size_t* len, void* q_out, int q_on_device);

@@ -14,7 +14,11 @@ NTTs of size N on the coset slices plus their coset scaling, the gate at M
 points, the quotient inverse NTT of size M, its scaling, and the openings
 (c N + (d - 1) N).  Bytes: columns in, coefficients out and back in, one
 slice pass per column and slice, q-hat out and in, q out, q read for the
-root and the opening.
+root and the opening.  A step-radix domain of Mb + N points (Mb = 2^k N)
+has s = 2^k + 1 slices; its quotient transform is the Mb-point inverse NTT
+with its scaling, the reduction of q_big (Mb multiplications), an N-point
+coset NTT of the reduced q_big and an N-point inverse NTT with their
+scalings, and the combination (2 N).
 """
 from __future__ import annotations
 
@@ -31,22 +35,37 @@ def blowup(d: int) -> int:
     return 1 << max(0, (d - 1).bit_length())
 
 
+def domain(n: int, d: int, log_blowup: int = 0) -> tuple[int, int]:
+    """(Mb, Ms): the power-of-two part and the step-radix part (0 if none)
+    of the NTT domain for a domain word (0: next_pow2(d) N)."""
+    N = 1 << n
+    k, sp1 = log_blowup & 0xFF, (log_blowup >> 8) & 0xFF
+    if not sp1:
+        return (1 << k if k else blowup(d)) * N, 0
+    return N << k, N << (sp1 - 1)
+
+
 def algorithmic_mulmods(form: str, n: int, d: int = 3, gate: int = 1, log_blowup: int = 0) -> float:
     N = 1 << n
     c = ncols(gate, d)
     g = 5 if gate == 1 else d - 1
-    s = 1 << log_blowup if log_blowup else blowup(d)
-    M = s * N
     if form == "sumcheck":
         return (N - 1) * ((d + 1) * (g + 1) + 1 + c)
+    Mb, Ms = domain(n, d, log_blowup)
+    M = Mb + Ms
+    s = M / N
+    q_transform = (Mb / 2) * math.log2(Mb) + Mb
+    if Ms:
+        q_transform += Mb + 2 * ((Ms / 2) * math.log2(Ms) + Ms) + 2 * Ms
     return (c * (N / 2) * n + c * s * (N + (N / 2) * n) + M * (g + 1)
-            + (M / 2) * math.log2(M) + M + c * N + (d - 1) * N)
+            + q_transform + c * N + (d - 1) * N)
 
 
 def algorithmic_bytes(form: str, n: int, d: int = 3, gate: int = 1, log_blowup: int = 0) -> float:
     N = 1 << n
     c = ncols(gate, d)
-    M = (1 << log_blowup if log_blowup else blowup(d)) * N
     if form == "sumcheck":
         return 128.0 * c * N
+    Mb, Ms = domain(n, d, log_blowup)
+    M = Mb + Ms
     return 32.0 * (2 * c * N + c * M + M + 2 * M + c * N + M)

@@ -26,6 +26,25 @@ static uint32_t default_log_blowup(uint32_t d) {
   return l;
 }
 
+bool ntt_domain(uint32_t n, uint32_t d, uint32_t w, NttDomain* D) {
+  if (w >> 16) return false;
+  const uint32_t sp1 = (w >> 8) & 0xffu;
+  D->step = sp1 != 0;
+  D->k = w & 0xffu;
+  if (!D->step && D->k == 0) D->k = default_log_blowup(d);
+  D->s = D->step ? sp1 - 1 : 0;
+  if (D->step && (D->k == 0 || D->s >= D->k)) return false;
+  if (n + D->k > 32) return false;
+  D->N = 1ull << n;
+  D->Mb = D->N << D->k;
+  D->Ms = D->step ? D->N << D->s : 0;
+  D->M = D->Mb + D->Ms;
+  // |D| must hold the quotient's (d-1) N - d + 1 coefficients
+  if (D->M + d < (uint64_t)(d - 1) * D->N + 1) return false;
+  D->word = D->step ? (n + D->k) | ((n + D->s + 1) << 8) : n + D->k;
+  return true;
+}
+
 zc_status check_params(zc_ctx* ctx, const zc_params* p, zc_form form) {
   if (!p) {
     if (ctx) ctx->err = "null params";
@@ -36,10 +55,9 @@ zc_status check_params(zc_ctx* ctx, const zc_params* p, zc_form form) {
     return ZC_ERR_ARG;
   }
   if (form == ZC_FORM_NTT) {
-    uint32_t lb = p->log_blowup ? p->log_blowup : default_log_blowup(p->d);
-    // |D| = 2^lb N must hold the quotient's (d-1) N - d + 1 coefficients
-    if ((1u << lb) + 1 < p->d || p->n + lb > (uint32_t)kMaxN + 2) {
-      if (ctx) ctx->err = "log_blowup too small for the degree, or domain too large";
+    NttDomain D;
+    if (!ntt_domain(p->n, p->d, p->log_blowup, &D) || p->n + D.k > (uint32_t)kMaxN + 2) {
+      if (ctx) ctx->err = "domain word malformed, too small for the degree, or domain too large";
       return ZC_ERR_ARG;
     }
   } else if (form != ZC_FORM_SUMCHECK) {
@@ -254,15 +272,20 @@ static void parallel_for(size_t n, F f) {
   for (auto& x : th) x.join();
 }
 
-// root(v) on the host (same definition as the device kernels)
+// root(v) on the host (same definition as the device kernels): leaves of
+// 64 elements (the last may be shorter), node = SHA-256(l | r), the odd last
+// node of a level moves up unchanged, root = SHA-256(le64(L) | top).
 static bool host_root(const uint8_t* v, uint64_t L, uint8_t out[32]) {
-  if (L == 0 || (L & (L - 1))) return false;
-  uint64_t per = L < 64 ? L : 64, nl = L / per;
+  if (L == 0) return false;
+  const uint64_t nl = (L + 63) / 64;
   std::vector<uint32_t> nodes(nl * 8);
   parallel_for(nl, [&](size_t lo, size_t hi, unsigned) {
-    for (size_t t = lo; t < hi; t++) sha256_host_mem(v + t * per * 32, per * 32, &nodes[8 * t]);
+    for (size_t t = lo; t < hi; t++) {
+      const uint64_t cnt = std::min<uint64_t>(64, L - 64 * t);
+      sha256_host_mem(v + t * 64 * 32, (uint32_t)(cnt * 32), &nodes[8 * t]);
+    }
   });
-  for (uint64_t cnt = nl; cnt > 1; cnt /= 2) {
+  for (uint64_t cnt = nl; cnt > 1; cnt = (cnt + 1) / 2) {
     for (uint64_t i = 0; i < cnt / 2; i++) {
       uint32_t w[16], h[8];
       for (int k = 0; k < 16; k++) w[k] = nodes[16 * i + k];
@@ -274,6 +297,8 @@ static bool host_root(const uint8_t* v, uint64_t L, uint8_t out[32]) {
       sha256_compress(h, w);
       for (int k = 0; k < 8; k++) nodes[8 * i + k] = h[k];
     }
+    if (cnt & 1)
+      for (int k = 0; k < 8; k++) nodes[8 * (cnt / 2) + k] = nodes[8 * (cnt - 1) + k];
   }
   uint8_t msg[40];
   for (int i = 0; i < 8; i++) msg[i] = (uint8_t)(L >> (8 * i));
@@ -450,10 +475,11 @@ static zc_status verify_ntt(const zc_params* p, const void* const* cols, const u
   if (len != need || std::memcmp(proof, "ZCN1", 4) != 0 || !qv) return ZC_ERR_ARG;
   uint32_t hdr[4];
   for (int q = 0; q < 4; q++) std::memcpy(&hdr[q], proof + 4 + 4 * q, 4);
-  uint32_t lb = p->log_blowup ? p->log_blowup : default_log_blowup(d);
-  if (hdr[0] != gate || hdr[1] != n || hdr[2] != d || hdr[3] != n + lb) return ZC_ERR_ARG;
-  const uint32_t logm = n + lb;
-  const uint64_t M = 1ull << logm;
+  NttDomain D;
+  if (!ntt_domain(n, d, p->log_blowup, &D)) return ZC_ERR_ARG;
+  if (hdr[0] != gate || hdr[1] != n || hdr[2] != d || hdr[3] != D.word) return ZC_ERR_ARG;
+  const uint32_t logm = D.word;
+  const uint64_t M = D.M;
   const uint8_t* q = static_cast<const uint8_t*>(qv);
   bool ok = true;
   uint8_t qroot[32];
@@ -645,8 +671,10 @@ void zc_destroy(zc_ctx* ctx) {
   if (ctx->up_fork) cudaEventDestroy(ctx->up_fork);
   if (ctx->up_stream) cudaStreamDestroy(ctx->up_stream);
   if (ctx->arena.base) cudaFree(ctx->arena.base);
-  for (auto& t : ctx->ntt_cache)
+  for (auto& t : ctx->ntt_cache) {
     if (t.mem) cudaFree(t.mem);
+    if (t.step_mem) cudaFree(t.step_mem);
+  }
   if (ctx->dconst) cudaFree(ctx->dconst);
   if (ctx->dtabs) cudaFree(ctx->dtabs);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);

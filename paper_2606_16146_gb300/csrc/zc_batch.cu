@@ -28,11 +28,10 @@ static double instance_cost(const zc_params& p, zc_form f) {
     const double g = p.gate == ZC_GATE_PLONK ? 5.0 : (double)p.d - 1;
     return N * ((p.d + 1) * (g + 1) + 1 + c);
   }
-  uint32_t lb = p.log_blowup;
-  if (!lb)
-    while ((1u << lb) < p.d) lb++;
-  const double s = std::ldexp(1.0, (int)lb), M = s * N;
-  return c * N / 2 * p.n + c * s * (N + N / 2 * p.n) + M * (p.n + lb) / 2 + M * p.d;
+  NttDomain D;
+  if (!ntt_domain(p.n, p.d, p.log_blowup, &D)) return 0.0;
+  const double M = (double)D.M, s = M / N;
+  return c * N / 2 * p.n + c * s * (N + N / 2 * p.n) + M * (p.n + D.k) / 2 + M * p.d;
 }
 
 zc_status make_lanes(zc_ctx* ctx, int K) {

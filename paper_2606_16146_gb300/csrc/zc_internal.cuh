@@ -118,6 +118,14 @@ struct zc_ctx {
     uint64_t stamp = 0;
     zc::fr *tw_fwd = nullptr, *tw_inv = nullptr, *coset = nullptr, *outer = nullptr, *fin = nullptr;
     zc::fr* zinv = nullptr;  // per slice: (7^N w_s^j - 1)^-1 M^-1, level 1
+    // step-radix domain 2^lb N + N (built on first use): the small part's
+    // coset factors sigma^k / N (level 2) and sigma^-k 7^k (level 1),
+    // k < N, sigma = 7 w_{2M}; constants: [0] the small part's z_H inverse
+    // times kappa^-1 N^-1, [1] 7^M (level 1), [8 + m] sigma^(mN) kappa^-1,
+    // m < 2^lb (level 1), kappa = sigma^M - 7^M.
+    void* step_mem = nullptr;
+    size_t step_bytes = 0;
+    zc::fr *step_coset = nullptr, *step_unscale = nullptr, *step_const = nullptr;
   };
   std::vector<NttSizeTables> ntt_cache;
   uint64_t ntt_cache_clock = 0;
@@ -168,6 +176,21 @@ void h_to_bytes(const fr& a, uint8_t* out);
 bool h_from_bytes(const uint8_t* in, fr* out);
 void transcript_init_words(uint32_t S[8], uint32_t form, uint32_t gate, uint32_t n, uint32_t d,
                            uint32_t logm);
+
+// The NTT form's domain (Sec. 3.2; Sec. 4 "Degree scaling"): the big part
+// 7 <w_Mb>, Mb = 2^k N, and for a step-radix domain the small part
+// sigma <w_Ms>, Ms = 2^s N, s < k, sigma = 7 w_{2 Mb}; M = Mb + Ms points.
+// word is what the proof header and the transcript carry: log2 Mb, or
+// log2 Mb | (log2 Ms + 1) << 8.
+struct NttDomain {
+  uint32_t k = 0, s = 0;
+  bool step = false;
+  uint64_t N = 0, Mb = 0, Ms = 0, M = 0;
+  uint32_t word = 0;
+};
+// From zc_params.log_blowup (0: 2^ceil(log2 d) N; k; or k | (s + 1) << 8);
+// false when the word is malformed or the domain cannot hold the quotient.
+bool ntt_domain(uint32_t n, uint32_t d, uint32_t log_blowup, NttDomain* D);
 
 // device roots: cols (device pointers), c columns of L elements -> roots
 // (device, c x 32 bytes).  Uses arena scratch.

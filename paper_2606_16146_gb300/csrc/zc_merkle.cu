@@ -3,11 +3,15 @@
 // The paper commits to [g] and [q] before the Fiat-Shamir challenge (Fig.
 // side-by-side-zc, "Commit"); the commitment scheme itself is outside its
 // comparison (Sec. 3.4).  Here root(v) is a binary SHA-256 Merkle tree:
-// leaf t = SHA-256 of the canonical bytes of v[64 t .. 64 t + 63] (all of v
-// when it has fewer than 64 elements), node = SHA-256(left | right),
-// root = SHA-256(le64(len) | top).  One thread hashes one 2 KB leaf; a CTA
-// reduces its 128 leaves to one node in shared memory; a second kernel
-// reduces the CTA nodes of each column.
+// leaf t = SHA-256 of the canonical bytes of v[64 t .. min(64 t + 63, L-1)]
+// (the last leaf is shorter when 64 does not divide L), node =
+// SHA-256(left | right), and at a level with an odd count the last node
+// moves up unchanged; root = SHA-256(le64(len) | top).  One thread hashes
+// one 2 KB leaf; a CTA reduces its 128 leaves to one node in shared memory;
+// a second kernel reduces the CTA nodes of each column.  The CTAs' leaf
+// ranges start at multiples of 128, so their subtrees are the global tree's
+// first seven levels (a ragged last CTA's node arrives at level 7 unchanged,
+// as the odd last node of every level above it).
 #include "zc_internal.cuh"
 
 namespace zc {
@@ -18,7 +22,7 @@ constexpr int kLeafCta = 128;
 struct RootLeafArgs {
   const fr* col[kMaxCols];
   uint64_t L;
-  uint32_t per;        // elements per leaf
+  uint32_t per;        // elements per leaf (the last leaf may have fewer)
   uint64_t nleaves;
   uint32_t ctas;       // CTAs per column
   uint32_t* nodes;     // [c][ctas][8] digest words
@@ -97,15 +101,22 @@ __global__ void __launch_bounds__(kLeafCta) k_root_leaves(RootLeafArgs A) {
   uint32_t h[8];
   if (threadIdx.x < cnt) {
     const uint8_t* p = reinterpret_cast<const uint8_t*>(A.col[c] + leaf * A.per);
-    sha256_device_mem(p, A.per * 32, h);
+    const uint64_t left = A.L - leaf * A.per;
+    const uint32_t elems = left < A.per ? (uint32_t)left : A.per;
+    sha256_device_mem(p, elems * 32, h);
 #pragma unroll
     for (int i = 0; i < 8; i++) dig[threadIdx.x][i] = h[i];
   }
-  for (uint32_t w = cnt; w > 1; w >>= 1) {
+  for (uint32_t w = cnt; w > 1; w = (w + 1) / 2) {
     __syncthreads();
-    if (threadIdx.x < w / 2) sha256_node(dig[2 * threadIdx.x], dig[2 * threadIdx.x + 1], h);
+    const bool pair = threadIdx.x < w / 2, carry = (w & 1) && threadIdx.x == w / 2;
+    if (pair) sha256_node(dig[2 * threadIdx.x], dig[2 * threadIdx.x + 1], h);
+    if (carry) {
+#pragma unroll
+      for (int i = 0; i < 8; i++) h[i] = dig[w - 1][i];
+    }
     __syncthreads();
-    if (threadIdx.x < w / 2) {
+    if (pair || carry) {
 #pragma unroll
       for (int i = 0; i < 8; i++) dig[threadIdx.x][i] = h[i];
     }
@@ -122,13 +133,15 @@ __global__ void __launch_bounds__(256) k_root_top(RootTopArgs A) {
   const int c = blockIdx.x;
   uint32_t* a = A.nodes + (size_t)c * A.ctas * 8;
   uint32_t* b = A.tmp + (size_t)c * A.ctas * 8;
-  for (uint32_t w = A.ctas; w > 1; w >>= 1) {
+  for (uint32_t w = A.ctas; w > 1; w = (w + 1) / 2) {
     for (uint32_t t = threadIdx.x; t < w / 2; t += blockDim.x) {
       uint32_t h[8];
       sha256_node(a + 16 * t, a + 16 * t + 8, h);
 #pragma unroll
       for (int i = 0; i < 8; i++) b[8 * t + i] = h[i];
     }
+    if ((w & 1) && threadIdx.x == 0)  // the odd last node moves up unchanged
+      for (int i = 0; i < 8; i++) b[8 * (w / 2) + i] = a[8 * (w - 1) + i];
     __syncthreads();
     uint32_t* x = a;
     a = b;
@@ -161,15 +174,15 @@ __global__ void __launch_bounds__(256) k_root_top(RootTopArgs A) {
 
 zc_status launch_roots(zc_ctx* ctx, const fr* const* dcols, int c, uint64_t L, uint8_t* droots,
                        cudaStream_t st) {
-  if (L == 0 || (L & (L - 1)) || c < 1 || c > kMaxCols) {
-    ctx->err = "root: length must be a power of two";
+  if (L == 0 || c < 1 || c > kMaxCols) {
+    ctx->err = "root: empty vector or too many columns";
     return ZC_ERR_ARG;
   }
   RootLeafArgs la{};
   for (int j = 0; j < c; j++) la.col[j] = dcols[j];
   la.L = L;
   la.per = L < (uint64_t)kLeafElems ? (uint32_t)L : (uint32_t)kLeafElems;
-  la.nleaves = L / la.per;
+  la.nleaves = (L + la.per - 1) / la.per;
   la.ctas = (uint32_t)((la.nleaves + kLeafCta - 1) / kLeafCta);
   size_t words = (size_t)c * la.ctas * 8;
   uint32_t* nodes = ctx->arena.take<uint32_t>(words);
@@ -196,7 +209,7 @@ zc_status launch_roots(zc_ctx* ctx, const fr* const* dcols, int c, uint64_t L, u
 
 size_t root_scratch_bytes(int c, uint64_t L) {
   uint64_t per = L < (uint64_t)kLeafElems ? L : (uint64_t)kLeafElems;
-  uint64_t nl = L / per;
+  uint64_t nl = (L + per - 1) / per;
   uint64_t ctas = (nl + kLeafCta - 1) / kLeafCta;
   return 2 * ((size_t)c * ctas * 32 + 256);
 }

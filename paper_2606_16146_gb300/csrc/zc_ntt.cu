@@ -423,6 +423,7 @@ struct NttGateArgs {
   const fr* col[kMaxCols];  // slice evaluations, level 1
   fr* qhat;                 // slice output
   const fr* zinv;           // constant of this slice
+  const fr* sub;            // nullptr, or values subtracted after the scaling (level 1)
   uint64_t N;
   uint32_t gate, d, c;       // gate word, degree, columns
 };
@@ -448,7 +449,73 @@ __global__ void __launch_bounds__(256) k_ntt_gate(NttGateArgs A) {
       else
         for (uint32_t j = A.d; j < A.c; j++) f = fr_add(f, ld_fr(A.col[j] + p));
     }
-    st_fr(A.qhat + p, fr_mul(f, zi));
+    f = fr_mul(f, zi);
+    if (A.sub) f = fr_sub(f, ld_fr(A.sub + p));
+    st_fr(A.qhat + p, f);
+  }
+}
+
+// ------------------------------------------------ step-radix domain --
+// D = D_big u D_small, D_big = 7 <w_M> (M = 2^lb N), D_small = sigma H with
+// sigma = 7 w_{2M} (Sec. 4, degree scaling: a transform of M + N points
+// from power-of-two transforms plus element-wise work).  q = q_big +
+// (x^M - 7^M) q_small: q_big is the INTT over D_big of qhat there; on
+// D_small, x^M = sigma^M, so q_small = INTT over D_small of
+// (qhat - q_big) / kappa, kappa = sigma^M - 7^M.
+
+struct NttStepTabArgs {
+  fr* coset;      // [k] sigma^k / N, level 2
+  fr* unscale;    // [k] w_{2M}^-k, level 1
+  uint32_t n, shift2m;  // exponent shift of w_{2M} in the 2^30 tables: 30 - log2(2M)
+  fr ninv_l2;
+  NttTables T;
+};
+
+__global__ void k_ntt_step_tables(NttStepTabArgs A) {
+  const uint64_t N = 1ull << A.n;
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t ex = (uint32_t)((k << A.shift2m) & ((1ull << kLog30) - 1));
+    const fr p7 = fr_mul(ld_fr(A.T.p7_hi + (k >> kLoBits)), ld_fr(A.T.p7_lo + (k & kLoMask)));  // 7^k
+    st_fr(A.coset + k, fr_mul(fr_mul(p7, root_pow(A.T.wf_lo, A.T.wf_hi, ex)), A.ninv_l2));
+    st_fr(A.unscale + k, root_pow(A.T.wi_lo, A.T.wi_hi, ex));
+  }
+}
+
+// q_big evaluated on D_small starts with its reduction modulo x^N - sigma^N,
+// scaled by 1/kappa: rho[k] = sum_m q[k + m N] sigma^(mN) / kappa.
+struct NttStepReduceArgs {
+  const fr* q;       // q_big, M canonical coefficients
+  fr* rho;           // N outputs, level 0
+  const fr* cm;      // 2^lb constants sigma^(mN) / kappa, level 1
+  uint64_t N;
+  uint32_t parts;    // M / N
+};
+
+__global__ void k_ntt_step_reduce(NttStepReduceArgs A) {
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < A.N;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    fr acc = fr_mul(ld_fr(A.q + k), ld_fr(A.cm));
+    for (uint32_t m = 1; m < A.parts; m++) acc = fr_add(acc, fr_mul(ld_fr(A.q + k + m * A.N), ld_fr(A.cm + m)));
+    st_fr(A.rho + k, acc);
+  }
+}
+
+// q_small[k] = w_{2M}^-k x[k] (x: the small part's INTT, which carried the
+// factor 7^-k); q[M + k] = q_small[k], q[k] -= 7^M q_small[k].
+struct NttStepCombineArgs {
+  fr* q;             // M + N coefficients; x in q[M .. M + N)
+  const fr* unscale;
+  const fr* s7m;     // 7^M, level 1
+  uint64_t N, M;
+};
+
+__global__ void k_ntt_step_combine(NttStepCombineArgs A) {
+  const fr c = ld_fr(A.s7m);
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < A.N;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    const fr t = fr_mul(ld_fr(A.q + A.M + k), ld_fr(A.unscale + k));
+    st_fr(A.q + A.M + k, t);
+    st_fr(A.q + k, fr_sub(ld_fr(A.q + k), fr_mul(t, c)));
   }
 }
 
@@ -720,14 +787,15 @@ static zc_ctx::NttSizeTables* size_tables(zc_ctx* user, const NttTables* T, uint
   const size_t bytes = sizeof(fr) * (2 * N + 3 * M + s);
   if (ctx->ntt_cache_frozen || bytes > ctx->ntt_cache_budget) return nullptr;
   size_t used = 0;
-  for (auto& e : ctx->ntt_cache) used += e.bytes;
+  for (auto& e : ctx->ntt_cache) used += e.bytes + e.step_bytes;
   while (!ctx->ntt_cache.empty() && used + bytes > ctx->ntt_cache_budget) {
     size_t old = 0;
     for (size_t i = 1; i < ctx->ntt_cache.size(); i++)
       if (ctx->ntt_cache[i].stamp < ctx->ntt_cache[old].stamp) old = i;
     cudaStreamSynchronize(st);
     cudaFree(ctx->ntt_cache[old].mem);
-    used -= ctx->ntt_cache[old].bytes;
+    if (ctx->ntt_cache[old].step_mem) cudaFree(ctx->ntt_cache[old].step_mem);
+    used -= ctx->ntt_cache[old].bytes + ctx->ntt_cache[old].step_bytes;
     ctx->ntt_cache.erase(ctx->ntt_cache.begin() + old);
   }
   zc_ctx::NttSizeTables e;
@@ -793,28 +861,30 @@ static void pass_defaults(NttPassArgs& a) {
   a.out_lbdiv = 63;
 }
 
-static uint32_t ntt_log_blowup(const zc_params* p) {
-  uint32_t lb = p->log_blowup;
-  if (!lb)
-    while ((1u << lb) < p->d) lb++;
-  return lb;
+static NttDomain domain_of(const zc_params* p) {
+  NttDomain D;
+  ntt_domain(p->n, p->d, p->log_blowup, &D);  // validated by check_params
+  return D;
 }
 
 size_t ntt_scratch_bytes(const zc_params* p, int sm_count, bool q_direct) {
-  const uint32_t n = p->n, lb = ntt_log_blowup(p);
+  const NttDomain D = domain_of(p);
+  const uint32_t n = p->n, lb = D.k;
   const int c = gate_ncols(p->gate, p->d);
-  const uint64_t N = 1ull << n, M = N << lb, s = 1ull << lb;
+  const uint64_t N = 1ull << n, Mb = N << lb, s = 1ull << lb, M = D.M;
   const uint32_t hbits = (n + 1) / 2;
   const uint32_t nlo = 1u << hbits, nhi = 1u << (n - hbits);
   const uint32_t nblk_open = 2 * (uint32_t)sm_count;
   const size_t psize = 20 + 32 + 32 * ((size_t)c + 1);
   size_t need = 2 * align_up(sizeof(fr) * N, 256) * c;  // coefficients + slice buffer
-  need += align_up(sizeof(fr) * M, 256);                  // qhat
+  need += align_up(sizeof(fr) * M, 256);                  // qhat (both parts)
   if (!q_direct) need += align_up(sizeof(fr) * M, 256);   // q
+  if (D.step) need += 2 * align_up(sizeof(fr) * N, 256);  // q_big reduced, and its LDE
   need += align_up(sizeof(fr) * s * (nlo + nhi), 256) + align_up(sizeof(fr) * s, 256);
   need += align_up(sizeof(fr) * (c + 1) * nblk_open, 256) + align_up(sizeof(fr) * 32, 256);
   need += align_up(sizeof(NttState), 256) + align_up(psize, 256) + align_up(32 * (size_t)(c + 1), 256);
   need += root_scratch_bytes(c, N) + root_scratch_bytes(1, M) + 8192;
+  (void)Mb;
   return need;
 }
 
@@ -851,14 +921,83 @@ static bool ntt_two_pass(const zc_ctx* ctx, uint32_t n) {
   return n >= (uint32_t)(t > 0 ? t : 12) && n >= 2;
 }
 
+// The step-radix tables of a cache entry (lb = k): built once, with the
+// host-computed constants of the small part.  False if they cannot be made.
+static bool step_tables(zc_ctx* user, zc_ctx::NttSizeTables* e, const NttTables* T, cudaStream_t st) {
+  if (e->step_mem) return true;
+  zc_ctx* ctx = user->table_owner ? user->table_owner : user;
+  if (ctx->ntt_cache_frozen) return false;
+  const uint32_t n = e->n, lb = e->lb;
+  const uint64_t N = 1ull << n, M = N << lb, parts = 1ull << lb;
+  if (n + lb + 1 > (uint32_t)kLog30 || parts > 64) return false;
+  const size_t nconst = 8 + parts;
+  const size_t bytes = sizeof(fr) * (2 * N + nconst);
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  fr* q = static_cast<fr*>(mem);
+  fr* coset = q;
+  fr* unscale = q + N;
+  fr* cst = q + 2 * N;
+  const DevConst& C = ctx->hconst;
+  // sigma = 7 w_{2M}; kappa = sigma^M - 7^M; z_H on D_small = sigma^N - 1
+  const fr w2m = h_pow(T->w32h, (1ull << 32) >> (n + lb + 1), C);
+  const fr seven = h_from_u64(7), one = h_from_u64(1);
+  const fr sigma = h_canon_mul(seven, w2m, C);
+  const fr s7m = h_pow(seven, M, C);
+  const fr kinv = h_inv(fr_sub_g(h_pow(sigma, M, C), s7m), C);
+  const fr ninv = h_inv(h_from_u64(N), C);
+  const fr sn = h_pow(sigma, N, C);
+  std::vector<fr> hc(nconst, fr_zero());
+  hc[0] = h_canon_mul(h_canon_mul(h_canon_mul(h_inv(fr_sub_g(sn, one), C), kinv, C), ninv, C), C.one, C);
+  hc[1] = h_canon_mul(s7m, C.one, C);
+  fr pm = one;
+  for (uint64_t m = 0; m < parts; m++) {
+    hc[8 + m] = h_canon_mul(h_canon_mul(pm, kinv, C), C.one, C);  // level 1
+    pm = h_canon_mul(pm, sn, C);
+  }
+  if (cudaMemcpyAsync(cst, hc.data(), sizeof(fr) * nconst, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(mem);
+    return false;
+  }
+  NttStepTabArgs a{};
+  a.coset = coset;
+  a.unscale = unscale;
+  a.n = n;
+  a.shift2m = kLog30 - (n + lb + 1);
+  a.ninv_l2 = fr_mul_g(fr_mul_g(ninv, C.r2), C.r2);
+  a.T = *T;
+  k_ntt_step_tables<<<(unsigned)std::min<uint64_t>((N + 255) / 256, (uint64_t)ctx->sm_count * 16), 256, 0, st>>>(a);
+  if (cudaGetLastError() != cudaSuccess) {
+    cudaFree(mem);
+    return false;
+  }
+  e->step_mem = mem;
+  e->step_bytes = bytes;
+  e->step_coset = coset;
+  e->step_unscale = unscale;
+  e->step_const = cst;
+  user->launches++;
+  return true;
+}
+
 zc_status ntt_prepare(zc_ctx* ctx, const zc_params* p, cudaStream_t st) {
   ensure_pass_attributes(ctx->device);
   NttTables* T = nullptr;
   zc_status s0 = ensure_tables(ctx, st, &T);
   if (s0 != ZC_OK) return s0;
-  const uint32_t n = p->n, lb = ntt_log_blowup(p);
+  const NttDomain D = domain_of(p);
+  const uint32_t n = p->n, lb = D.k;
   const bool two = ntt_two_pass(ctx, n);
-  size_tables(ctx, T, n, lb, two ? (n + 1) / 2 : n, two ? n / 2 : 0, st);
+  zc_ctx::NttSizeTables* ST = size_tables(ctx, T, n, lb, two ? (n + 1) / 2 : n, two ? n / 2 : 0, st);
+  if (D.step && (!ST || !step_tables(ctx, ST, T, st))) {
+    ctx->err = "step-radix domain: tables unavailable";
+    return ZC_ERR_OOM;
+  }
   return cudaStreamSynchronize(st) == cudaSuccess ? ZC_OK : ZC_ERR_CUDA;
 }
 
@@ -871,15 +1010,20 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
     ctx->err = "NTT form supports n <= 24";
     return ZC_ERR_UNSUPPORTED;
   }
-  uint32_t lb = p->log_blowup;
-  if (!lb) while ((1u << lb) < d) lb++;
-  const uint32_t logm = n + lb;
-  if (logm > (uint32_t)kLog30) {
+  const NttDomain D = domain_of(p);
+  if (D.step && D.s != 0) {
+    ctx->err = "step-radix domains take a small part of N points (s = 0)";
+    return ZC_ERR_UNSUPPORTED;
+  }
+  const uint32_t lb = D.k;          // the big part 7 <w_Mb>, Mb = 2^lb N
+  const uint32_t logm = n + lb;     // log2 Mb
+  if (logm + (D.step ? 1 : 0) > (uint32_t)kLog30) {
     ctx->err = "domain larger than 2^30";
     return ZC_ERR_UNSUPPORTED;
   }
   const int c = gate_ncols(gate, d);
-  const uint64_t N = 1ull << n, M = 1ull << logm, s = 1ull << lb;
+  const uint64_t N = 1ull << n, Mb = 1ull << logm, s = 1ull << lb;
+  const uint64_t M = D.M;           // Mb, or Mb + N (step radix)
   const size_t psize = 20 + 32 + 32 * ((size_t)c + 1);
   ensure_pass_attributes(ctx->device);
   NttTables* T = nullptr;
@@ -900,6 +1044,8 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
   for (int j = 0; j < c; j++) slb[j] = ar.take<fr>(N);
   fr* qhat = ar.take<fr>(M);
   fr* qv = q_direct ? static_cast<fr*>(q_out) : ar.take<fr>(M);
+  fr* rho = D.step ? ar.take<fr>(N) : nullptr;   // q_big reduced mod x^N - sigma^N
+  fr* vsm = D.step ? ar.take<fr>(N) : nullptr;   // its values on D_small
   fr* tlo = ar.take<fr>(s * nlo);
   fr* thi = ar.take<fr>(s * nhi);
   fr* zinv = ar.take<fr>(s);
@@ -921,6 +1067,10 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
   const uint64_t L1 = 1ull << l1, L2 = 1ull << l2;
   zc_status rs;
   zc_ctx::NttSizeTables* ST = size_tables(ctx, T, n, lb, l1, l2, st);
+  if (D.step && (!ST || !step_tables(ctx, ST, T, st))) {
+    ctx->err = "step-radix domain: per-size tables unavailable";
+    return ZC_ERR_OOM;
+  }
 
   // N1's first pass (rows over i2, twiddled) for the columns [j0, j1)
   auto n1_first = [&](const fr* const* in, int j0, int j1) -> zc_status {
@@ -1043,13 +1193,17 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
   }
   ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[2], st));
 
-  // ---- N2: per slice, coset NTT of every column, gate, divide by z_H
-  for (uint64_t j = 0; j < s; j++) {
+  // ---- N2: per slice, coset NTT of every column, gate, divide by z_H.
+  // slice_lde: the coset NTT of the `items` coefficient vectors in[] into
+  // out[] on one slice, with the coset factor table pre (per-size tables)
+  // or slice j's two-level tables (without them).
+  auto slice_lde = [&](const fr* const* in, fr* const* out, int items, const fr* pre, uint64_t j,
+                       bool mark) -> zc_status {
     NttPassArgs a;
     pass_defaults(a);
-    for (int i = 0; i < c; i++) {
-      a.in[i] = coef[i];
-      a.out[i] = slb[i];
+    for (int i = 0; i < items; i++) {
+      a.in[i] = in[i];
+      a.out[i] = out[i];
     }
     a.pre = PRE_COSET;
     a.pre_lo = tlo + j * nlo;
@@ -1064,37 +1218,42 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
       a.post = POST_TW; a.tw_lo = T->wf_lo; a.tw_hi = T->wf_hi;
       a.tw_lbmod = l2; a.tw_shift = kLog30 - n;
       if (ST) {  // coset factor of k = k2 + L2 k1; twiddle w_N^(k2 i1) = tw_fwd[k2 L1 + i1]
-        a.pre = PRE_TAB; a.pre_tab = ST->coset + j * N;
+        a.pre = PRE_TAB; a.pre_tab = pre;
         a.post = POST_TAB; a.post_tab = ST->tw_fwd;
         a.p_lbdiv = 63; a.p_ls = L1; a.p_ts = 1;
       }
-      if ((rs = run_pass(ctx, st, a, c, L2)) != ZC_OK) return rs;
-      if (j == 0) ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[7], st));
+      if ((rs = run_pass(ctx, st, a, items, L2)) != ZC_OK) return rs;
+      if (mark) ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[7], st));
       pass_defaults(a);
-      for (int i = 0; i < c; i++) {
-        a.in[i] = slb[i];
-        a.out[i] = slb[i];
+      for (int i = 0; i < items; i++) {
+        a.in[i] = out[i];
+        a.out[i] = out[i];
       }
       a.logL = l2;                     // rows over k2
       a.in_bs_lo = L2; a.in_ts = 1;
       a.out_bs_lo = L2; a.out_ts = 1;
       a.dft = T->dft_fwd;
-      if ((rs = run_pass(ctx, st, a, c, L1)) != ZC_OK) return rs;
+      if ((rs = run_pass(ctx, st, a, items, L1)) != ZC_OK) return rs;
     } else {
       a.logL = n;
       a.in_bs_lo = 0; a.in_ts = 1;
       a.out_bs_lo = 0; a.out_ts = 1;
       a.pre_kb = 0; a.pre_kt = 1;
       if (ST) {
-        a.pre = PRE_TAB; a.pre_tab = ST->coset + j * N;
+        a.pre = PRE_TAB; a.pre_tab = pre;
       }
-      if ((rs = run_pass(ctx, st, a, c, 1)) != ZC_OK) return rs;
-      if (j == 0) ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[7], st));
+      if ((rs = run_pass(ctx, st, a, items, 1)) != ZC_OK) return rs;
+      if (mark) ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[7], st));
     }
+    return ZC_OK;
+  };
+  // gate and division by z_H (constant zi on the slice), minus sub if given
+  auto slice_gate = [&](fr* out, const fr* zi, const fr* sub) {
     NttGateArgs ga{};
     for (int i = 0; i < c; i++) ga.col[i] = slb[i];
-    ga.qhat = qhat + j * N;
-    ga.zinv = (ST ? ST->zinv : zinv) + j;
+    ga.qhat = out;
+    ga.zinv = zi;
+    ga.sub = sub;
     ga.N = N;
     ga.gate = gate;
     ga.d = d;
@@ -1102,15 +1261,22 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
     uint32_t gb = (uint32_t)std::min<uint64_t>((N + 255) / 256, (uint64_t)ctx->sm_count * 8);
     k_ntt_gate<<<gb, 256, 0, st>>>(ga);
     ctx->launches++;
+  };
+  for (uint64_t j = 0; j < s; j++) {
+    if ((rs = slice_lde(coef, slb, c, ST ? ST->coset + j * N : nullptr, j, j == 0)) != ZC_OK) return rs;
+    slice_gate(qhat + j * N, (ST ? ST->zinv : zinv) + j, nullptr);
   }
   ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[3], st));
 
-  // ---- N3: q = 7^-k M^-1 DFT_M^-1(qhat), digits (s, L1, L2) or (s, N)
+  // ---- N3: q = 7^-k M^-1 DFT_M^-1(qhat), digits (s, L1, L2) or (s, N).
+  // inverse: the INTT of ns = 2^lbs slices qin[] into qout[] (natural
+  // order, with the factor 7^-k; M^-1 came with the slice constants).
+  auto inverse = [&](fr* qin, fr* qout, uint64_t s, uint32_t lb, uint32_t logm) -> zc_status {
   {
     NttPassArgs a;
     if (two) {
       pass_defaults(a);
-      a.in[0] = qhat; a.out[0] = qhat;
+      a.in[0] = qin; a.out[0] = qin;
       a.logL = l2;                     // rows (j, i2) over i3
       a.in_bs_lo = L2; a.in_ts = 1;
       a.out_bs_lo = L2; a.out_ts = 1;
@@ -1123,7 +1289,7 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
       }
       if ((rs = run_pass(ctx, st, a, 1, s * L1)) != ZC_OK) return rs;
       pass_defaults(a);
-      a.in[0] = qhat; a.out[0] = qhat;
+      a.in[0] = qin; a.out[0] = qin;
       a.logL = l1;                     // columns (j, k3) over i2 within a slice
       a.in_lbdiv = l2; a.in_bs_hi = N; a.in_bs_lo = 1; a.in_ts = L2;
       a.out_lbdiv = l2; a.out_bs_hi = N; a.out_bs_lo = 1; a.out_ts = L2;
@@ -1137,7 +1303,7 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
       if ((rs = run_pass(ctx, st, a, 1, s * L2)) != ZC_OK) return rs;
     } else {
       pass_defaults(a);
-      a.in[0] = qhat; a.out[0] = qhat;
+      a.in[0] = qin; a.out[0] = qin;
       a.logL = n;                      // one row per slice
       a.in_bs_lo = N; a.in_ts = 1;
       a.out_bs_lo = N; a.out_ts = 1;
@@ -1151,7 +1317,7 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
       if ((rs = run_pass(ctx, st, a, 1, s)) != ZC_OK) return rs;
     }
     pass_defaults(a);
-    a.in[0] = qhat; a.out[0] = qv;
+    a.in[0] = qin; a.out[0] = qout;
     a.logL = lb;                       // across slices
     a.in_bs_lo = 1; a.in_ts = N;
     a.out_bs_lo = 1; a.out_ts = N;
@@ -1163,6 +1329,37 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
       a.p_lbdiv = 63; a.p_ls = 1; a.p_ts = N;
     }
     if ((rs = run_pass(ctx, st, a, 1, N)) != ZC_OK) return rs;
+  }
+    return ZC_OK;
+  };
+  if ((rs = inverse(qhat, qv, s, lb, logm)) != ZC_OK) return rs;
+  if (D.step) {
+    // q_big on D_small (reduce, then the slice LDE with sigma's factors),
+    // the small part's gate minus it, its INTT, and q = q_big + (x^Mb -
+    // 7^Mb) q_small.
+    NttStepReduceArgs ra{};
+    ra.q = qv;
+    ra.rho = rho;
+    ra.cm = ST->step_const + 8;
+    ra.N = N;
+    ra.parts = (uint32_t)s;
+    const unsigned eg = (unsigned)std::min<uint64_t>((N + 255) / 256, (uint64_t)ctx->sm_count * 8);
+    k_ntt_step_reduce<<<eg, 256, 0, st>>>(ra);
+    ctx->launches++;
+    const fr* rin[1] = {rho};
+    fr* rout[1] = {vsm};
+    if ((rs = slice_lde(rin, rout, 1, ST->step_coset, 0, false)) != ZC_OK) return rs;
+    if ((rs = slice_lde(coef, slb, c, ST->step_coset, 0, false)) != ZC_OK) return rs;
+    slice_gate(qhat + Mb, ST->step_const, vsm);
+    if ((rs = inverse(qhat + Mb, qv + Mb, 1, 0, n)) != ZC_OK) return rs;
+    NttStepCombineArgs ca{};
+    ca.q = qv;
+    ca.unscale = ST->step_unscale;
+    ca.s7m = ST->step_const + 1;
+    ca.N = N;
+    ca.M = Mb;
+    k_ntt_step_combine<<<eg, 256, 0, st>>>(ca);
+    ctx->launches++;
   }
   ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[4], st));
   // a host q leaves on the side stream while the root and the openings run
@@ -1184,7 +1381,7 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
     za.roots = droots;
     za.c = c;
     za.n = n;
-    transcript_init_words(za.S0, ZC_FORM_NTT, gate, n, d, logm);
+    transcript_init_words(za.S0, ZC_FORM_NTT, gate, n, d, D.word);
     za.zpow = zpow;
     za.C = ctx->dconst;
     k_ntt_z<<<1, 32, 0, st>>>(za);
@@ -1214,7 +1411,7 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
     fa.gate = gate;
     fa.n = n;
     fa.d = d;
-    fa.logm = logm;
+    fa.logm = D.word;
     fa.ninv_l1 = fr_mul_g(ninv, C.r2);
     fa.qroot = droots + 32 * (size_t)c;
     fa.st = dstate;

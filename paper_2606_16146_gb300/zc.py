@@ -164,6 +164,20 @@ def _stream_ptr(stream):
     return getattr(stream, "cuda_stream", stream)
 
 
+def domain_word(k: int, s: int | None = None) -> int:
+    """zc_params.log_blowup for 2^k N points, or with s (< k) the step-radix
+    domain of 2^k N + 2^s N points (ZC_DOMAIN_STEP(k, s))."""
+    return k if s is None else k | ((s + 1) << 8)
+
+
+def domain_size(n: int, d: int, log_blowup: int = 0) -> int:
+    """Points M of the NTT domain (the quotient has M coefficients)."""
+    k, sp1 = log_blowup & 0xFF, (log_blowup >> 8) & 0xFF
+    if not sp1:
+        return 1 << (n + (k or (d - 1).bit_length()))
+    return (1 << (n + k)) + (1 << (n + sp1 - 1))
+
+
 def proof_size(gate, n, d, form, log_blowup=0) -> int:
     p = zc_params(gate, n, d, log_blowup)
     out = ctypes.c_size_t()
@@ -230,8 +244,7 @@ class Context:
         P, on_dev = self._cols(cols)
         rb, rp = _roots_arg(roots)
         cap = proof_size(gate, n, d, ZC_FORM_NTT, log_blowup)
-        lb = log_blowup or (d - 1).bit_length()
-        M = 1 << (n + lb)
+        M = domain_size(n, d, log_blowup)
         out = proof_out if proof_out is not None else np.zeros(cap, np.uint8)
         q = q_out if q_out is not None else (np.zeros(M * 32, np.uint8) if want_q else None)
         q_dev = 1 if (q is None or (_is_torch(q) and q.is_cuda)) else 0

@@ -77,3 +77,21 @@ def test_host_verifier_agrees_with_oracle(gate, n, d):
     assert not zc.verify(gate, n, d, 2, cols, pn, q=q2)
     roots = [oracle.root(c) for c in cols]
     assert zc.verify(gate, n, d, 1, cols, ps, roots=roots)
+
+
+@pytest.mark.parametrize("gate,n,d,ks", [(2, 5, 4, (1, 0)), (1, 7, 3, (1, 0)), (2, 3, 6, (2, 0)),
+                                         (2, 4, 7, (2, 1)), (zc.gate_sum(1), 6, 3, (1, 0))])
+def test_host_verifier_step_radix_domain(gate, n, d, ks):
+    """The library's host verifier (its own Merkle root over 2^k N + 2^s N
+    coefficients and its own header decoding) accepts the oracle's step-radix
+    proofs and rejects a flipped quotient coefficient or a wrong domain word."""
+    w = zc.domain_word(*ks)
+    assert zc.domain_size(n, d, w) == oracle.domain_size(n, d, w)
+    cols = witness.generate(gate, n, d, 60 + n)
+    pn, q = oracle.prove_ntt(gate, n, d, cols, log_blowup=w)
+    assert zc.verify(gate, n, d, 2, cols, pn, q=q, log_blowup=w)
+    q2 = np.array(q, copy=True)
+    q2[32 * 3] ^= 1
+    assert not zc.verify(gate, n, d, 2, cols, pn, q=q2, log_blowup=w)
+    # the header names another domain than the caller's: malformed, not accepted
+    assert not zc.verify(gate, n, d, 2, cols, pn, q=q, log_blowup=ks[0] + 1)
