@@ -53,6 +53,9 @@ def lib():
             u32, sz, p = ctypes.c_uint32, ctypes.c_size_t, ctypes.c_void_p
             L.zo_prove_sumcheck.argtypes = [u32, u32, u32, p, p, p, sz, ctypes.POINTER(sz), p, p]
             L.zo_verify_sumcheck.argtypes = [u32, u32, u32, p, p, p, sz, ctypes.POINTER(ctypes.c_int)]
+            L.zo_prove_sumcheck_eq.argtypes = [u32, u32, u32, p, p, p, sz, ctypes.POINTER(sz), p, p]
+            L.zo_verify_sumcheck_eq.argtypes = [u32, u32, u32, p, p, p, sz, ctypes.POINTER(ctypes.c_int)]
+            L.zo_proof_size_eq.argtypes = [u32, u32, u32, ctypes.POINTER(sz)]
             L.zo_prove_ntt.argtypes = [u32, u32, u32, u32, p, p, p, sz, ctypes.POINTER(sz), p]
             L.zo_verify_ntt.argtypes = [u32, u32, u32, p, p, p, sz, p, ctypes.POINTER(ctypes.c_int)]
             L.zo_proof_size.argtypes = [u32, u32, u32, u32, ctypes.POINTER(sz)]
@@ -126,6 +129,45 @@ def prove_sumcheck(gate, n, d, cols, roots=None, with_challenges=False):
         return pb, [r_out[32 * i:32 * i + 32].tobytes() for i in range(n)], \
             [a_out[32 * i:32 * i + 32].tobytes() for i in range(n)]
     return pb
+
+
+def proof_size_eq(gate: int, n: int, d: int) -> int:
+    out = ctypes.c_size_t()
+    if lib().zo_proof_size_eq(gate, n, d, ctypes.byref(out)) != 0:
+        raise ValueError("bad gate/degree")
+    return out.value
+
+
+def prove_sumcheck_eq(gate, n, d, cols, roots=None, with_challenges=False):
+    """Eq-factored SumCheck proof ("ZCS2", transcript v2): rounds carry
+    H_i(0..d); optionally also r and alpha as canonical bytes."""
+    C = _Cols(cols)
+    rb, rp = _roots_buf(roots)
+    cap = proof_size_eq(gate, n, d)
+    proof = np.zeros(cap, np.uint8)
+    ln = ctypes.c_size_t()
+    r_out = np.zeros(32 * n, np.uint8)
+    a_out = np.zeros(32 * n, np.uint8)
+    st = lib().zo_prove_sumcheck_eq(gate, n, d, C.p, rp, _ptr(proof), cap, ctypes.byref(ln),
+                                    _ptr(r_out), _ptr(a_out))
+    if st != 0:
+        raise ValueError(f"oracle prove_sumcheck_eq status {st}")
+    pb = proof.tobytes()[: ln.value]
+    if with_challenges:
+        return pb, [r_out[32 * i:32 * i + 32].tobytes() for i in range(n)], \
+            [a_out[32 * i:32 * i + 32].tobytes() for i in range(n)]
+    return pb
+
+
+def verify_sumcheck_eq(gate, n, d, cols, proof, roots=None) -> bool:
+    C = _Cols(cols)
+    rb, rp = _roots_buf(roots)
+    pr = _buf(proof)
+    acc = ctypes.c_int(0)
+    st = lib().zo_verify_sumcheck_eq(gate, n, d, C.p, rp, _ptr(pr), pr.size, ctypes.byref(acc))
+    if st != 0:
+        return False
+    return bool(acc.value)
 
 
 def verify_sumcheck(gate, n, d, cols, proof, roots=None) -> bool:

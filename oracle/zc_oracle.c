@@ -355,13 +355,17 @@ typedef struct { uint8_t s[32]; } transcript;
 
 static void le32(uint8_t *b, uint32_t v) { for (int i = 0; i < 4; i++) b[i] = (uint8_t)(v >> (8 * i)); }
 
-static void tr_init(transcript *t, uint32_t form, uint32_t gate, uint32_t n, uint32_t d, uint32_t logm) {
-    const char *tag = "zerocheck-gb300/v1";
+static void tr_init_tag(transcript *t, const char *tag, uint32_t form, uint32_t gate, uint32_t n,
+                        uint32_t d, uint32_t logm) {
     uint8_t msg[64]; size_t tl = strlen(tag);
     memcpy(msg, tag, tl);
     le32(msg + tl, form); le32(msg + tl + 4, gate); le32(msg + tl + 8, n);
     le32(msg + tl + 12, d); le32(msg + tl + 16, logm);
     sha256(msg, tl + 20, t->s);
+}
+
+static void tr_init(transcript *t, uint32_t form, uint32_t gate, uint32_t n, uint32_t d, uint32_t logm) {
+    tr_init_tag(t, "zerocheck-gb300/v1", form, gate, n, d, logm);
 }
 
 static void tr_absorb(transcript *t, const uint8_t *m, size_t len) {
@@ -623,6 +627,166 @@ int zo_verify_sumcheck(uint32_t gate, uint32_t n, uint32_t d, const uint8_t *con
                                  f_mul(f_sub(f_one(), r[i]), f_sub(f_one(), alpha[i]))));
     if (!f_eq(claim, f_mul(gate_eval(gate, d, v), eqra))) ok = 0;
     /* oracle access to the columns: v_j = sum_b col_j[b] eq_alpha(b) */
+    fe *T[65];
+    if (!load_cols(cols, c, N, T)) { free_cols(T, c); return 1; }
+    for (int j = 0; j < c && ok; j++) {
+        fe tot = f_zero();
+        #pragma omp parallel
+        {
+            fe part = f_zero();
+            #pragma omp for schedule(static)
+            for (long k = 0; k < (long)N; k++) {
+                fe e = f_one();
+                for (uint32_t i = 0; i < n; i++) {
+                    int b = (int)(((size_t)k >> (n - 1 - i)) & 1);
+                    e = f_mul(e, b ? alpha[i] : f_sub(f_one(), alpha[i]));
+                }
+                part = f_add(part, f_mul(T[j][k], e));
+            }
+            #pragma omp critical
+            tot = f_add(tot, part);
+        }
+        if (!f_eq(tot, v[j])) ok = 0;
+    }
+    free_cols(T, c);
+    *accept = ok;
+    return 0;
+}
+
+/* ------------------------------- eq-factored SumCheck (transcript v2) -- */
+/* Sec. 3.3 with the eq factor split off, as in the faster SumCheck provers
+ * the paper cites for Build MLE: G_i(X) = c_i l_i(X) H_i(X), where
+ *   c_i = prod_{j<i} eq(alpha_j, r_j),  l_i(X) = (1 - r_i)(1 - X) + r_i X,
+ *   H_i(X) = sum over x in {0,1}^{n-i} of f_M(alpha_<i, X, x) eq_{r_>i}(x).
+ * c_i and l_i are known to the verifier, so a round sends H_i, of degree d,
+ * at X = 0..d (d + 1 values instead of G_i's d + 2).  The verifier checks
+ * c_i ((1 - r_i) H_i(0) + r_i H_i(1)) = claim, then claim <- c_i l_i(alpha_i)
+ * H_i(alpha_i) and c_{i+1} = c_i l_i(alpha_i).  Transcript tag
+ * "zerocheck-gb300/v2" (form word 3); absorbs enc(H_i(0..d)).
+ * Proof = "ZCS2" | gate | n | d | H_1..H_n | v_1..v_c. */
+int zo_proof_size_eq(uint32_t gate, uint32_t n, uint32_t d, size_t *bytes) {
+    int c = gate_cols(gate, d);
+    if (c < 0) return 1;
+    *bytes = 16 + 32 * ((size_t)n * (d + 1) + c);
+    return 0;
+}
+
+int zo_prove_sumcheck_eq(uint32_t gate, uint32_t n, uint32_t d, const uint8_t *const *cols,
+                         const uint8_t *roots_in, uint8_t *proof, size_t cap, size_t *len,
+                         uint8_t *r_out, uint8_t *alpha_out) {
+    field_init();
+    int c = gate_cols(gate, d);
+    if (c < 0 || n < 1 || n > 30) return 1;
+    size_t need; zo_proof_size_eq(gate, n, d, &need);
+    if (cap < need) return 6;
+    size_t N = (size_t)1 << n;
+    fe *T[65];
+    if (!load_cols(cols, c, N, T)) { free_cols(T, c); return 1; }
+    uint8_t *roots = (uint8_t *)malloc(32 * (size_t)c);
+    col_roots(cols, c, N, roots_in, roots);
+
+    transcript tr; tr_init_tag(&tr, "zerocheck-gb300/v2", 3, gate, n, d, 0);
+    for (int j = 0; j < c; j++) tr_absorb(&tr, roots + 32 * j, 32);
+    fe r[64];
+    for (uint32_t i = 0; i < n; i++) r[i] = tr_squeeze(&tr);
+
+    memcpy(proof, "ZCS2", 4);
+    le32(proof + 4, gate); le32(proof + 8, n); le32(proof + 12, d);
+    uint8_t *pp = proof + 16;
+    fe *E = (fe *)malloc((N / 2 + 1) * sizeof(fe));
+    fe tpt[70];
+    for (uint32_t t = 0; t <= d; t++) tpt[t] = f_from_u64(t);
+    size_t size = N;
+    for (uint32_t i = 0; i < n; i++) {
+        size_t h = size / 2;
+        /* eq_{r_>i}(x) over the remaining n - i - 1 variables, x MSB first */
+        const uint32_t m = n - i - 1;
+        #pragma omp parallel for schedule(static)
+        for (long k = 0; k < (long)h; k++) {
+            fe e = f_one();
+            for (uint32_t l = 0; l < m; l++) {
+                int b = (int)(((size_t)k >> (m - 1 - l)) & 1);
+                fe rl = r[i + 1 + l];
+                e = f_mul(e, b ? rl : f_sub(f_one(), rl));
+            }
+            E[k] = e;
+        }
+        fe H[70];
+        for (uint32_t t = 0; t <= d; t++) {
+            fe tot = f_zero();
+            #pragma omp parallel
+            {
+                fe part = f_zero();
+                fe x[65];
+                #pragma omp for schedule(static)
+                for (long k = 0; k < (long)h; k++) {
+                    for (int j = 0; j < c; j++)
+                        x[j] = f_add(T[j][k], f_mul(tpt[t], f_sub(T[j][k + h], T[j][k])));
+                    part = f_add(part, f_mul(gate_eval(gate, d, x), E[k]));
+                }
+                #pragma omp critical
+                tot = f_add(tot, part);
+            }
+            H[t] = tot;
+        }
+        uint8_t msg[70 * 32];
+        for (uint32_t t = 0; t <= d; t++) f_to_bytes(H[t], msg + 32 * t);
+        memcpy(pp, msg, 32 * (size_t)(d + 1)); pp += 32 * (size_t)(d + 1);
+        tr_absorb(&tr, msg, 32 * (size_t)(d + 1));
+        fe alpha = tr_squeeze(&tr);
+        if (alpha_out) f_to_bytes(alpha, alpha_out + 32 * i);
+        for (int j = 0; j < c; j++) {
+            fe *Tj = T[j];
+            #pragma omp parallel for schedule(static)
+            for (long k = 0; k < (long)h; k++)
+                Tj[k] = f_add(Tj[k], f_mul(alpha, f_sub(Tj[k + h], Tj[k])));
+        }
+        size = h;
+    }
+    for (int j = 0; j < c; j++) { f_to_bytes(T[j][0], pp); pp += 32; }
+    if (r_out) for (uint32_t i = 0; i < n; i++) f_to_bytes(r[i], r_out + 32 * i);
+    *len = need;
+    free(E); free(roots); free_cols(T, c);
+    return 0;
+}
+
+int zo_verify_sumcheck_eq(uint32_t gate, uint32_t n, uint32_t d, const uint8_t *const *cols,
+                          const uint8_t *roots_in, const uint8_t *proof, size_t len, int *accept) {
+    field_init();
+    *accept = 0;
+    int c = gate_cols(gate, d);
+    if (c < 0 || n < 1 || n > 30) return 1;
+    size_t need; zo_proof_size_eq(gate, n, d, &need);
+    if (len != need) return 1;
+    uint8_t hdr[16]; memcpy(hdr, "ZCS2", 4); le32(hdr + 4, gate); le32(hdr + 8, n); le32(hdr + 12, d);
+    if (memcmp(hdr, proof, 16) != 0) return 1;
+    size_t N = (size_t)1 << n;
+    uint8_t *roots = (uint8_t *)malloc(32 * (size_t)c);
+    col_roots(cols, c, N, roots_in, roots);
+    transcript tr; tr_init_tag(&tr, "zerocheck-gb300/v2", 3, gate, n, d, 0);
+    for (int j = 0; j < c; j++) tr_absorb(&tr, roots + 32 * j, 32);
+    free(roots);
+    fe r[64], alpha[64];
+    for (uint32_t i = 0; i < n; i++) r[i] = tr_squeeze(&tr);
+    const uint8_t *pp = proof + 16;
+    fe claim = f_zero(), ci = f_one();
+    int ok = 1;
+    for (uint32_t i = 0; i < n; i++) {
+        fe H[70];
+        for (uint32_t t = 0; t <= d; t++)
+            if (!f_from_bytes(pp + 32 * t, &H[t])) return 1;
+        fe sum = f_add(f_mul(f_sub(f_one(), r[i]), H[0]), f_mul(r[i], H[1]));
+        if (!f_eq(f_mul(ci, sum), claim)) ok = 0;
+        tr_absorb(&tr, pp, 32 * (size_t)(d + 1));
+        pp += 32 * (size_t)(d + 1);
+        alpha[i] = tr_squeeze(&tr);
+        fe li = f_add(f_mul(f_sub(f_one(), r[i]), f_sub(f_one(), alpha[i])), f_mul(r[i], alpha[i]));
+        ci = f_mul(ci, li);
+        claim = f_mul(ci, lagrange_at(H, d + 1, alpha[i]));
+    }
+    fe v[65];
+    for (int j = 0; j < c; j++) if (!f_from_bytes(pp + 32 * j, &v[j])) return 1;
+    if (!f_eq(claim, f_mul(gate_eval(gate, d, v), ci))) ok = 0;
     fe *T[65];
     if (!load_cols(cols, c, N, T)) { free_cols(T, c); return 1; }
     for (int j = 0; j < c && ok; j++) {

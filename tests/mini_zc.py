@@ -53,8 +53,8 @@ def merkle_root(vals) -> bytes:
 
 
 class Transcript:
-    def __init__(self, form, gate, n, d, logm):
-        self.s = sha(TAG + b"".join(x.to_bytes(4, "little") for x in (form, gate, n, d, logm)))
+    def __init__(self, form, gate, n, d, logm, tag=TAG):
+        self.s = sha(tag + b"".join(x.to_bytes(4, "little") for x in (form, gate, n, d, logm)))
 
     def absorb(self, m: bytes):
         self.s = sha(self.s + m)
@@ -115,6 +115,37 @@ def prove_sumcheck(gate, n, d, cols_int):
     for i in range(n):
         G = [sumcheck_round_poly(gate, d, cols_int, r, alphas, i, t) for t in range(d + 2)]
         msg = b"".join(enc(g) for g in G)
+        out += msg
+        tr.absorb(msg)
+        alphas.append(tr.squeeze())
+    for col in cols_int:
+        out += enc(mle(col, alphas))
+    return out, r, alphas
+
+
+def sumcheck_round_h(gate, d, cols, r, alphas, i, t):
+    """H_i(t) = sum over x_{i+1..n} of f_M(a, t, x) eq_{r_{>i}}(x): G_i with the
+    eq factors of the bound variables and of x_i itself divided out."""
+    n = len(r)
+    tot = 0
+    for rest in itertools.product((0, 1), repeat=n - i - 1):
+        pt = list(alphas[:i]) + [t] + list(rest)
+        vals = [mle(c, pt) for c in cols]
+        tot += gate_eval(gate, d, vals) * eq(r[i + 1:], rest)
+    return tot % R
+
+
+def prove_sumcheck_eq(gate, n, d, cols_int):
+    """Eq-factored rounds ("ZCS2", tag v2): H_i at t = 0..d."""
+    tr = Transcript(3, gate, n, d, 0, tag=b"zerocheck-gb300/v2")
+    for col in cols_int:
+        tr.absorb(merkle_root(col))
+    r = [tr.squeeze() for _ in range(n)]
+    out = b"ZCS2" + b"".join(x.to_bytes(4, "little") for x in (gate, n, d))
+    alphas = []
+    for i in range(n):
+        H = [sumcheck_round_h(gate, d, cols_int, r, alphas, i, t) for t in range(d + 1)]
+        msg = b"".join(enc(h) for h in H)
         out += msg
         tr.absorb(msg)
         alphas.append(tr.squeeze())

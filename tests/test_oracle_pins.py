@@ -404,3 +404,55 @@ def test_merkle_root_any_length(L):
     rng = random.Random(L)
     vals = [rng.randrange(R) for _ in range(L)]
     assert oracle.root(oracle.ints_to_bytes(vals)) == mz.merkle_root(vals)
+
+
+# ---- eq-factored SumCheck, transcript v2 (rounds carry H_i(0..d))
+
+EQ_CASES = [(1, 1, 3), (1, 3, 3), (2, 3, 2), (2, 2, 5), (2, 3, 4), (witness.gate_sum(1), 3, 2),
+            (witness.gate_sum(0), 2, 3)]
+
+
+@pytest.mark.parametrize("gate,n,d", EQ_CASES)
+def test_sumcheck_eq_matches_bruteforce(gate, n, d):
+    cols = witness.generate(gate, n, d, 700 + n + d)
+    pb, r, al = oracle.prove_sumcheck_eq(gate, n, d, cols, with_challenges=True)
+    ref, r2, al2 = mz.prove_sumcheck_eq(gate, n, d, _cols_int(cols))
+    assert [int.from_bytes(x, "little") for x in r] == r2
+    assert [int.from_bytes(x, "little") for x in al] == al2
+    assert pb == ref
+    assert len(pb) == oracle.proof_size_eq(gate, n, d) == 16 + 32 * (n * (d + 1) + len(cols))
+
+
+def test_sumcheck_eq_is_g_with_the_eq_factor_split_off():
+    """G_i(t) (brute force, v1 definition) = c_i l_i(t) H_i(t) at the v2
+    proof's own challenges, c_i = prod_{j<i} eq(alpha_j, r_j)."""
+    gate, n, d = 2, 3, 3
+    cols = witness.generate(gate, n, d, 17)
+    ci = _cols_int(cols)
+    pb, r, al = oracle.prove_sumcheck_eq(gate, n, d, cols, with_challenges=True)
+    r = [int.from_bytes(x, "little") for x in r]
+    al = [int.from_bytes(x, "little") for x in al]
+    H = mz.ints(pb[16:16 + 32 * n * (d + 1)])
+    for i in range(n):
+        c = 1
+        for j in range(i):
+            c = c * ((1 - r[j]) * (1 - al[j]) + r[j] * al[j]) % R
+        for t in range(d + 2):
+            li = ((1 - r[i]) * (1 - t) + r[i] * t) % R
+            g = mz.sumcheck_round_poly(gate, d, ci, r, al, i, t)
+            h = H[i * (d + 1) + t] if t <= d else mz.sumcheck_round_h(gate, d, ci, r, al, i, t)
+            assert g == c * li * h % R
+
+
+@pytest.mark.parametrize("gate,n,d", [(1, 6, 3), (2, 5, 4), (witness.gate_sum(2), 5, 2)])
+def test_sumcheck_eq_verifier(gate, n, d):
+    cols = witness.generate(gate, n, d, 800 + n)
+    pb = oracle.prove_sumcheck_eq(gate, n, d, cols)
+    assert oracle.verify_sumcheck_eq(gate, n, d, cols, pb)
+    assert not oracle.verify_sumcheck(gate, n, d, cols, pb)          # not a v1 proof
+    bad = witness.generate(gate, n, d, 800 + n, tamper=True)
+    assert not oracle.verify_sumcheck_eq(gate, n, d, bad, oracle.prove_sumcheck_eq(gate, n, d, bad))
+    for off in (16, 16 + 32 * (d + 1) + 5, len(pb) - 3):
+        x = bytearray(pb)
+        x[off] ^= 2
+        assert not oracle.verify_sumcheck_eq(gate, n, d, cols, bytes(x))
