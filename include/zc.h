@@ -49,13 +49,17 @@
  *   SumCheck: "ZCS1" | u32 gate | u32 n | u32 d | G_i(t) for i = 1..n,
  *             t = 0..d+1 | v_j = the columns' MLEs at alpha, j = 1..c.
  *             Size 16 + 32 (n (d + 2) + c).
+ *   SumCheck, eq-factored (ZC_FORM_SUMCHECK_EQ): "ZCS2" | u32 gate | u32 n |
+ *             u32 d | H_i(t) for i = 1..n, t = 0..d | v_j, j = 1..c.  Size
+ *             16 + 32 (n (d + 1) + c).
  *   NTT:      "ZCN1" | u32 gate | u32 n | u32 d | u32 domain | root(q) |
  *             g_j(z), j = 1..c | q(z).  Size 20 + 32 + 32 (c + 1).  domain
  *             is log2 M, or log2 Mb | (log2 Ms + 1) << 8 for a step-radix
  *             domain of Mb + Ms points (see zc_params).
- * Transcript: S0 = SHA-256("zerocheck-gb300/v1" | u32 form | u32 gate |
+ * Transcript: S0 = SHA-256(tag | u32 form | u32 gate |
  * u32 n | u32 d | u32 domain (0 for SumCheck)); absorb(m): S = SHA-256(S|m);
- * squeeze: S = SHA-256(S | 0x43), challenge = int_le(S) mod r.  The column
+ * squeeze: S = SHA-256(S | 0x43), challenge = int_le(S) mod r; tag is
+ * "zerocheck-gb300/v1", or "zerocheck-gb300/v2" for ZC_FORM_SUMCHECK_EQ.  The column
  * and quotient commitments are stood in by root(v): a binary SHA-256 Merkle
  * tree over leaves of 64 canonical elements (the last leaf may be shorter;
  * at a level with an odd count the last node moves up unchanged),
@@ -84,7 +88,9 @@ typedef enum {
 typedef enum { ZC_GATE_PLONK = 1, ZC_GATE_PRODUCT = 2, ZC_GATE_SUM = 3 } zc_gate;
 /* Gate word of the sum gate with m single columns (m in bits 8..15). */
 #define ZC_GATE_SUM_OF(m) ((uint32_t)ZC_GATE_SUM | ((uint32_t)(m) << 8))
-typedef enum { ZC_FORM_SUMCHECK = 1, ZC_FORM_NTT = 2 } zc_form;
+/* ZC_FORM_SUMCHECK_EQ: the SumCheck form with eq-factored round messages
+ * (see zc_prove_sumcheck_eq). */
+typedef enum { ZC_FORM_SUMCHECK = 1, ZC_FORM_NTT = 2, ZC_FORM_SUMCHECK_EQ = 3 } zc_form;
 
 /* One ZeroCheck instance: gate word, n (N = 2^n, 1 <= n <= 28), degree d
  * (3 for Plonk, 2..64 for the product and sum gates) and the NTT form's
@@ -140,6 +146,20 @@ zc_status zc_proof_size(const zc_params* params, zc_form form, size_t* bytes);
 zc_status zc_prove_sumcheck(zc_ctx* ctx, const zc_params* params, const void* const* cols,
                             int cols_on_device, const uint8_t (*col_roots)[32],
                             void* cuda_stream, uint8_t* proof, size_t cap, size_t* len);
+
+/* SumCheck-form proof with eq-factored round messages (Sec. 3.3 with the
+ * eq factor split off, the faster-prover formulation the paper cites with
+ * Build MLE): round i's polynomial is G_i(X) = c_i l_i(X) H_i(X), with
+ * c_i = prod_{j<i} eq(alpha_j, r_j) and l_i(X) = (1 - r_i)(1 - X) + r_i X
+ * known to the verifier, so the round sends H_i (degree d) at X = 0..d:
+ * d + 1 values instead of G_i's d + 2, and one SHA-256 block less per
+ * round for low degrees.  The verifier checks c_i ((1 - r_i) H_i(0) +
+ * r_i H_i(1)) against the claim.  Proof format "ZCS2" (above), transcript
+ * tag v2 with form word ZC_FORM_SUMCHECK_EQ.  Arguments, asynchrony and
+ * errors as for zc_prove_sumcheck. */
+zc_status zc_prove_sumcheck_eq(zc_ctx* ctx, const zc_params* params, const void* const* cols,
+                               int cols_on_device, const uint8_t (*col_roots)[32],
+                               void* cuda_stream, uint8_t* proof, size_t cap, size_t* len);
 
 /* NTT-form ZeroCheck proof (Fig. side-by-side-zc left; Sec. 3.2).
  * Arguments as for zc_prove_sumcheck.  q_out: NULL, or M*32 bytes

@@ -60,7 +60,7 @@ zc_status check_params(zc_ctx* ctx, const zc_params* p, zc_form form) {
       if (ctx) ctx->err = "domain word malformed, too small for the degree, or domain too large";
       return ZC_ERR_ARG;
     }
-  } else if (form != ZC_FORM_SUMCHECK) {
+  } else if (form != ZC_FORM_SUMCHECK && form != ZC_FORM_SUMCHECK_EQ) {
     if (ctx) ctx->err = "unknown form";
     return ZC_ERR_ARG;
   }
@@ -164,7 +164,8 @@ static fr h_signed(int64_t x) {  // canonical residue of a small signed integer
 
 void transcript_init_words(uint32_t S[8], uint32_t form, uint32_t gate, uint32_t n, uint32_t d,
                            uint32_t logm) {
-  const char* tag = "zerocheck-gb300/v1";
+  // the eq-factored SumCheck has its own transcript version
+  const char* tag = form == ZC_FORM_SUMCHECK_EQ ? "zerocheck-gb300/v2" : "zerocheck-gb300/v1";
   uint8_t msg[64];
   size_t tl = std::strlen(tag);
   std::memcpy(msg, tag, tl);
@@ -383,19 +384,25 @@ static fr host_lagrange(const fr* y, int m, const fr& x, const DevConst& C) {
   return acc;
 }
 
+// SumCheck proofs: v1 rounds carry G_i(0..d+1) (check G(0) + G(1) = claim,
+// claim <- G(alpha)); eq-factored v2 rounds carry H_i(0..d) with G_i =
+// c_i l_i H_i (check c_i ((1 - r_i) H(0) + r_i H(1)) = claim, then
+// c_{i+1} = c_i l_i(alpha), claim <- c_{i+1} H(alpha)).  Both end with
+// claim = gate(v) eq(r, alpha) and v_j = MLE_j(alpha).
 static zc_status verify_sumcheck(const zc_params* p, const void* const* cols,
                                  const uint8_t (*roots)[32], const uint8_t* proof, size_t len,
-                                 int* accept, const DevConst& C) {
+                                 int* accept, const DevConst& C, bool v2) {
   const uint32_t n = p->n, d = p->d, gate = p->gate;
   const int c = gate_ncols(gate, d);
   const uint64_t N = 1ull << n;
-  size_t need = 16 + 32 * ((size_t)n * (d + 2) + c);
-  if (len != need || std::memcmp(proof, "ZCS1", 4) != 0) return ZC_ERR_ARG;
+  const uint32_t per = v2 ? d + 1 : d + 2;  // values per round
+  size_t need = 16 + 32 * ((size_t)n * per + c);
+  if (len != need || std::memcmp(proof, v2 ? "ZCS2" : "ZCS1", 4) != 0) return ZC_ERR_ARG;
   uint32_t hdr[3];
   for (int q = 0; q < 3; q++) std::memcpy(&hdr[q], proof + 4 + 4 * q, 4);
   if (hdr[0] != gate || hdr[1] != n || hdr[2] != d) return ZC_ERR_ARG;
   HostTranscript tr;
-  tr.init(ZC_FORM_SUMCHECK, gate, n, d, 0);
+  tr.init(v2 ? ZC_FORM_SUMCHECK_EQ : ZC_FORM_SUMCHECK, gate, n, d, 0);
   for (int j = 0; j < c; j++) {
     uint8_t rt[32];
     if (roots) std::memcpy(rt, roots[j], 32);
@@ -405,17 +412,29 @@ static zc_status verify_sumcheck(const zc_params* p, const void* const* cols,
   std::vector<fr> r(n), al(n);
   for (uint32_t i = 0; i < n; i++) r[i] = tr.squeeze();
   bool ok = true;
-  fr claim = fr_zero();
+  fr claim = fr_zero(), ci = h_from_u64(1);
+  const fr one1 = h_from_u64(1);
   const uint8_t* pp = proof + 16;
-  std::vector<fr> G(d + 2);
+  std::vector<fr> G(per);
   for (uint32_t i = 0; i < n; i++) {
-    for (uint32_t t = 0; t <= d + 1; t++)
+    for (uint32_t t = 0; t < per; t++)
       if (!h_from_bytes(pp + 32 * t, &G[t])) return ZC_ERR_ARG;
-    if (!fr_equal(fr_add_g(G[0], G[1]), claim)) ok = false;
-    tr.absorb(pp, 32 * (size_t)(d + 2));
-    pp += 32 * (size_t)(d + 2);
+    if (v2) {
+      const fr s = fr_add_g(h_canon_mul(fr_sub_g(one1, r[i]), G[0], C), h_canon_mul(r[i], G[1], C));
+      if (!fr_equal(h_canon_mul(ci, s, C), claim)) ok = false;
+    } else if (!fr_equal(fr_add_g(G[0], G[1]), claim)) {
+      ok = false;
+    }
+    tr.absorb(pp, 32 * (size_t)per);
+    pp += 32 * (size_t)per;
     al[i] = tr.squeeze();
-    claim = host_lagrange(G.data(), (int)d + 2, al[i], C);
+    claim = host_lagrange(G.data(), (int)per, al[i], C);
+    if (v2) {
+      const fr li = fr_add_g(h_canon_mul(fr_sub_g(one1, r[i]), fr_sub_g(one1, al[i]), C),
+                             h_canon_mul(r[i], al[i], C));
+      ci = h_canon_mul(ci, li, C);
+      claim = h_canon_mul(ci, claim, C);
+    }
   }
   std::vector<fr> v(c);
   for (int j = 0; j < c; j++)
@@ -689,17 +708,19 @@ zc_status zc_proof_size(const zc_params* params, zc_form form, size_t* bytes) {
   if (s != ZC_OK) return s;
   int c = gate_ncols(params->gate, params->d);
   if (form == ZC_FORM_SUMCHECK) *bytes = 16 + 32 * ((size_t)params->n * (params->d + 2) + c);
+  else if (form == ZC_FORM_SUMCHECK_EQ) *bytes = 16 + 32 * ((size_t)params->n * (params->d + 1) + c);
   else *bytes = 20 + 32 + 32 * ((size_t)c + 1);
   return ZC_OK;
 }
 
-zc_status zc_prove_sumcheck(zc_ctx* ctx, const zc_params* params, const void* const* cols,
-                            int cols_on_device, const uint8_t (*col_roots)[32], void* cuda_stream,
-                            uint8_t* proof, size_t cap, size_t* len) {
+static zc_status prove_sumcheck_form(zc_ctx* ctx, zc_form form, const zc_params* params,
+                                     const void* const* cols, int cols_on_device,
+                                     const uint8_t (*col_roots)[32], void* cuda_stream, uint8_t* proof,
+                                     size_t cap, size_t* len) {
   if (!ctx) return ZC_ERR_ARG;
   std::lock_guard<std::mutex> lk(ctx->mu);
   ctx->err.clear();
-  zc_status s = check_params(ctx, params, ZC_FORM_SUMCHECK);
+  zc_status s = check_params(ctx, params, form);
   if (s != ZC_OK) return s;
   if (!cols || !proof || !len) {
     ctx->err = "null argument";
@@ -712,7 +733,7 @@ zc_status zc_prove_sumcheck(zc_ctx* ctx, const zc_params* params, const void* co
       return ZC_ERR_ARG;
     }
   size_t need;
-  zc_proof_size(params, ZC_FORM_SUMCHECK, &need);
+  zc_proof_size(params, form, &need);
   *len = need;
   if (cap < need) {
     ctx->err = "proof buffer too small";
@@ -721,7 +742,21 @@ zc_status zc_prove_sumcheck(zc_ctx* ctx, const zc_params* params, const void* co
   ZC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   bool pdev = is_device_ptr(proof);
   return sumcheck_prove(ctx, params, cols, cols_on_device, col_roots,
-                        static_cast<cudaStream_t>(cuda_stream), proof, pdev);
+                        static_cast<cudaStream_t>(cuda_stream), proof, pdev, form == ZC_FORM_SUMCHECK_EQ);
+}
+
+zc_status zc_prove_sumcheck(zc_ctx* ctx, const zc_params* params, const void* const* cols,
+                            int cols_on_device, const uint8_t (*col_roots)[32], void* cuda_stream,
+                            uint8_t* proof, size_t cap, size_t* len) {
+  return prove_sumcheck_form(ctx, ZC_FORM_SUMCHECK, params, cols, cols_on_device, col_roots, cuda_stream,
+                             proof, cap, len);
+}
+
+zc_status zc_prove_sumcheck_eq(zc_ctx* ctx, const zc_params* params, const void* const* cols,
+                               int cols_on_device, const uint8_t (*col_roots)[32], void* cuda_stream,
+                               uint8_t* proof, size_t cap, size_t* len) {
+  return prove_sumcheck_form(ctx, ZC_FORM_SUMCHECK_EQ, params, cols, cols_on_device, col_roots, cuda_stream,
+                             proof, cap, len);
 }
 
 zc_status zc_prove_ntt(zc_ctx* ctx, const zc_params* params, const void* const* cols,
@@ -767,7 +802,8 @@ zc_status zc_verify(const zc_params* params, zc_form form, const void* const* co
   for (int j = 0; j < c; j++)
     if (!cols[j]) return ZC_ERR_ARG;
   const DevConst& C = host_constants();
-  if (form == ZC_FORM_SUMCHECK) return verify_sumcheck(params, cols, col_roots, proof, len, accept, C);
+  if (form == ZC_FORM_SUMCHECK || form == ZC_FORM_SUMCHECK_EQ)
+    return verify_sumcheck(params, cols, col_roots, proof, len, accept, C, form == ZC_FORM_SUMCHECK_EQ);
   return verify_ntt(params, cols, col_roots, proof, len, q, accept, C);
 }
 

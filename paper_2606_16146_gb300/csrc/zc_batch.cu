@@ -24,7 +24,7 @@ constexpr int kMaxLanes = 64;
 static double instance_cost(const zc_params& p, zc_form f) {
   const double N = std::ldexp(1.0, (int)p.n);
   const int c = gate_ncols(p.gate, p.d);
-  if (f == ZC_FORM_SUMCHECK) {
+  if (f != ZC_FORM_NTT) {
     const double g = p.gate == ZC_GATE_PLONK ? 5.0 : (double)p.d - 1;
     return N * ((p.d + 1) * (g + 1) + 1 + c);
   }
@@ -107,7 +107,7 @@ zc_status batch_prepare(zc_ctx* ctx, uint32_t count, const zc_form* forms, const
   const std::vector<int> lane = assign_lanes(count, forms, params, K);
   std::vector<size_t> need(K, 0);
   for (uint32_t i = 0; i < count; i++) {
-    const size_t b = forms[i] == ZC_FORM_SUMCHECK
+    const size_t b = forms[i] != ZC_FORM_NTT
                          ? sumcheck_scratch_bytes(ctx, &params[i])
                          : ntt_scratch_bytes(&params[i], ctx->sm_count, q_direct ? q_direct[i] : false);
     need[lane[i]] = std::max(need[lane[i]], b);
@@ -150,8 +150,9 @@ zc_status batch_enqueue(zc_ctx* ctx, uint32_t count, const zc_form* forms, const
     for (uint32_t i = 0; i < count; i++) {
       if (lane[i] != k) continue;
       zc_status s;
-      if (forms[i] == ZC_FORM_SUMCHECK)
-        s = sumcheck_prove(L, &params[i], cols[i], 1, nullptr, ctx->lane_streams[k], proofs[i], true);
+      if (forms[i] != ZC_FORM_NTT)
+        s = sumcheck_prove(L, &params[i], cols[i], 1, nullptr, ctx->lane_streams[k], proofs[i], true,
+                           forms[i] == ZC_FORM_SUMCHECK_EQ);
       else
         s = ntt_prove(L, &params[i], cols[i], 1, nullptr, ctx->lane_streams[k], proofs[i], true,
                       q_outs ? q_outs[i] : nullptr, 1);
@@ -205,7 +206,8 @@ static zc_status check_batch_args(zc_ctx* ctx, uint32_t count, const zc_form* fo
                                   uint8_t* const* proofs) {
   if (!ctx || !forms || !params || !cols || !proofs || count == 0) return ZC_ERR_ARG;
   for (uint32_t i = 0; i < count; i++) {
-    if (forms[i] != ZC_FORM_SUMCHECK && forms[i] != ZC_FORM_NTT) return ZC_ERR_ARG;
+    if (forms[i] != ZC_FORM_SUMCHECK && forms[i] != ZC_FORM_NTT && forms[i] != ZC_FORM_SUMCHECK_EQ)
+      return ZC_ERR_ARG;
     const int c = gate_ncols(params[i].gate, params[i].d);
     if (c < 0 || !cols[i] || !proofs[i]) return ZC_ERR_ARG;
     for (int j = 0; j < c; j++)

@@ -199,9 +199,10 @@ zc_status launch_roots(zc_ctx* ctx, const fr* const* dcols, int c, uint64_t L, u
 size_t root_scratch_bytes(int c, uint64_t L);
 void static_constants(DevConst* C, std::vector<fr>* tabs);
 
+// v2: the eq-factored form (rounds carry H_i(0..d), transcript v2)
 zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, int on_dev,
                          const uint8_t (*roots)[32], cudaStream_t st, uint8_t* proof,
-                         bool proof_on_dev);
+                         bool proof_on_dev, bool v2 = false);
 zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, int on_dev,
                     const uint8_t (*roots)[32], cudaStream_t st, uint8_t* proof,
                     bool proof_on_dev, void* q_out, int q_on_dev);

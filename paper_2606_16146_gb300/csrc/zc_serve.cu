@@ -72,8 +72,7 @@ void destroy_serve_pool(zc_ctx* ctx) {
 static zc_status proof_scratch(zc_ctx* ctx, const zc_params* p, zc_form form, bool q_dev, size_t* out) {
   zc_status s = check_params(ctx, p, form);
   if (s != ZC_OK) return s;
-  *out = form == ZC_FORM_SUMCHECK ? sumcheck_scratch_bytes(ctx, p)
-                                  : ntt_scratch_bytes(p, ctx->sm_count, q_dev);
+  *out = form != ZC_FORM_NTT ? sumcheck_scratch_bytes(ctx, p) : ntt_scratch_bytes(p, ctx->sm_count, q_dev);
   return ZC_OK;
 }
 
@@ -251,8 +250,9 @@ zc_status zc_serve(zc_ctx* ctx, const zc_request* reqs, uint32_t count, const zc
       res[i].scratch_bytes = fp[i];
       res[i].slot = (uint32_t)k;
       zc_status ps;
-      if (r.form == ZC_FORM_SUMCHECK)
-        ps = sumcheck_prove(L, &r.params, r.cols, 1, nullptr, ctx->lane_streams[k], r.proof, true);
+      if (r.form != ZC_FORM_NTT)
+        ps = sumcheck_prove(L, &r.params, r.cols, 1, nullptr, ctx->lane_streams[k], r.proof, true,
+                            r.form == ZC_FORM_SUMCHECK_EQ);
       else
         ps = ntt_prove(L, &r.params, r.cols, 1, nullptr, ctx->lane_streams[k], r.proof, true, r.q_out, 1);
       launches += L->launches;

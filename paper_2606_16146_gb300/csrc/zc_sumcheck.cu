@@ -97,6 +97,7 @@ struct ScRoundArgs {
   uint32_t nwork;      // CTAs that evaluate pairs (round 1 may add one for the inverses)
   uint32_t full;       // evaluate H at all of 0..d-1 (no point derived from the claim)
   uint32_t next_derives;  // the next round derives a point: keep the claim
+  uint32_t v2;         // eq-factored proof: rounds carry H_i(0..d), not G_i(0..d+1)
   ScState* st;
   fr* partials;
   uint8_t* proof;
@@ -185,12 +186,13 @@ static_assert(2 * kMaxPts >= 32, "tmp holds one partial sum per warp of a 1024-t
 // Finish round `i` from the sums Hc (shared memory, np values): either all
 // of H(0..d-1) and H(inf) (np = d + 1) or H(p0), H(2..d-1), H(inf) (np = d,
 // the other of H(0), H(1) derived from the claim); extrapolate, G_i(t) =
-// c_i l_i(t) H_i(t) into the proof, absorb, squeeze alpha_i, update c_i and,
-// when the next round derives a point, the claim H_i(alpha_i).  All threads
-// of the CTA (at least 128).  Independent steps run on different warps so the
-// serial chain is eight multiplications and the hash.
+// c_i l_i(t) H_i(t) into the proof (v2: H_i(0..d) itself, the eq-factored
+// message), absorb, squeeze alpha_i, update c_i and, when the next round
+// derives a point, the claim H_i(alpha_i).  All threads of the CTA (at least
+// 128).  Independent steps run on different warps so the serial chain is
+// eight multiplications and the hash.
 __device__ void sc_challenge(ChalSmem& S, int np, int d, int i, ScState* st, uint8_t* proof,
-                             const DevConst* C, const fr* tabs, bool need_claim) {
+                             const DevConst* C, const fr* tabs, bool need_claim, bool v2) {
   const bool full = np == d + 1;
   const fr r = st->r[i];
   const fr two_r_m1 = fr_sub(fr_add(r, r), C->one);
@@ -198,7 +200,7 @@ __device__ void sc_challenge(ChalSmem& S, int np, int d, int i, ScState* st, uin
   const int t = threadIdx.x;
   const int hs = (d + 2 + 31) / 32 * 32;  // first thread of the warp after the c_i l_i(t) threads
   if (t < d + 2) {  // c_i l_i(t)
-    S.cl[t] = fr_mul(st->ci, fr_add(one_m_r, fr_mul(C->small[t], two_r_m1)));
+    if (!v2) S.cl[t] = fr_mul(st->ci, fr_add(one_m_r, fr_mul(C->small[t], two_r_m1)));
   } else if (t == hs) {  // another warp: H(0..d-1), H(inf)
     S.Hinf = S.Hc[np - 1];
     if (full) {
@@ -231,10 +233,12 @@ __device__ void sc_challenge(ChalSmem& S, int np, int d, int i, ScState* st, uin
     S.H[d + t] = v;
   }
   __syncthreads();
-  // G(t) = c_i l_i(t) H(t), level 0 = canonical
-  if (t < d + 2) {
-    const fr g = fr_mul(S.H[t], S.cl[t]);
-    uint8_t* pout = proof + 16 + 32 * ((size_t)i * (d + 2) + t);
+  // G(t) = c_i l_i(t) H(t) at t = 0..d+1, or (v2) H(t) at t = 0..d; H is
+  // at level 0 = canonical
+  const int per = v2 ? d + 1 : d + 2;
+  if (t < per) {
+    const fr g = v2 ? S.H[t] : fr_mul(S.H[t], S.cl[t]);
+    uint8_t* pout = proof + 16 + 32 * ((size_t)i * per + t);
     for (int q = 0; q < 8; q++) {
       S.msg[8 + 8 * t + q] = sha_bswap(g.v[q]);
       for (int b = 0; b < 4; b++) pout[4 * q + b] = (uint8_t)(g.v[q] >> (8 * b));
@@ -243,7 +247,7 @@ __device__ void sc_challenge(ChalSmem& S, int np, int d, int i, ScState* st, uin
   __syncthreads();
   if (t == 0) {
     uint32_t Sn[8];
-    sha256_words(S.msg, 8 + 8 * (d + 2), Sn);
+    sha256_words(S.msg, 8 + 8 * per, Sn);
     const fr a = fr_mul(tr_squeeze(Sn), C->r2);
     for (int q = 0; q < 8; q++) st->S[q] = Sn[q];
     st->alpha[i] = a;
@@ -313,7 +317,7 @@ __device__ void sc_finish_round(const ScRoundArgs& A, int np) {
     }
     __syncthreads();
   }
-  sc_challenge(S, np, (int)A.d, A.round, A.st, A.proof, A.C, A.tabs, A.next_derives != 0);
+  sc_challenge(S, np, (int)A.d, A.round, A.st, A.proof, A.C, A.tabs, A.next_derives != 0, A.v2 != 0);
 }
 
 // ------------------------------------------------------- per-pair work --
@@ -936,12 +940,12 @@ __global__ void __launch_bounds__(PLONK ? kTailThreads : 256, 1) k_sc_tail(ScRou
     }
     for (int p = threadIdx.x; p < np; p += blockDim.x) S.Hc[p] = pg[p];
     __syncthreads();
-    sc_challenge(S, np, d, i, A.st, A.proof, C, A.tabs, false);
+    sc_challenge(S, np, d, i, A.st, A.proof, C, A.tabs, false, A.v2 != 0);
   }
   if (bad) atomicOr(&A.st->err, 1u);
   __syncthreads();
   // final values v_j = T_j[0] + alpha_n (T_j[1] - T_j[0]); Plonk wires are at level 1
-  uint8_t* pv = A.proof + 16 + 32 * ((size_t)n * (d + 2));
+  uint8_t* pv = A.proof + 16 + 32 * ((size_t)n * (A.v2 ? d + 1 : d + 2));
   if (threadIdx.x < (unsigned)c) {
     const int j = threadIdx.x;
     const fr alpha = A.st->alpha[n - 1];
@@ -952,7 +956,7 @@ __global__ void __launch_bounds__(PLONK ? kTailThreads : 256, 1) k_sc_tail(ScRou
       for (int b = 0; b < 4; b++) pv[32 * j + 4 * q + b] = (uint8_t)(v.v[q] >> (8 * b));
   }
   if (threadIdx.x == 0) {
-    const char* mg = A.st->err ? "ZCE!" : "ZCS1";
+    const char* mg = A.st->err ? "ZCE!" : (A.v2 ? "ZCS2" : "ZCS1");
     for (int b = 0; b < 4; b++) A.proof[b] = (uint8_t)mg[b];
     const uint32_t hv[3] = {A.gate, (uint32_t)n, A.d};
     for (int q = 0; q < 3; q++)
@@ -1104,7 +1108,7 @@ static bool sc_carve(Arena& ar, const ScPlan& P, uint64_t N, size_t psize, ScBuf
 static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const* src,
                             const ScBuffers& B, const DevConst* dC, const fr* dtabs,
                             const DevConst& hC, int skip_point, cudaStream_t st,
-                            uint32_t* launches, cudaEvent_t* ev) {
+                            uint32_t* launches, cudaEvent_t* ev, bool v2 = false) {
   const uint32_t gate = p->gate, n = p->n, d = p->d;
   const int c = P.c;
   const uint64_t N = 1ull << n;
@@ -1112,7 +1116,7 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
   ScSetupArgs sa{};
   sa.st = B.st;
   sa.roots = B.roots;
-  transcript_init_words(sa.S0, ZC_FORM_SUMCHECK, gate, n, d, 0);
+  transcript_init_words(sa.S0, v2 ? ZC_FORM_SUMCHECK_EQ : ZC_FORM_SUMCHECK, gate, n, d, 0);
   sa.c = c;
   sa.n = (int)n;
   sa.C = dC;
@@ -1148,6 +1152,7 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
   R.kcomp = hC.rnegpow[d - 2];
   R.C = dC;
   R.tabs = dtabs;
+  R.v2 = v2 ? 1u : 0u;
   const uint64_t tail_pairs = P.tail_pairs;
   const fr* cur[kMaxCols];
   for (int j = 0; j < c; j++) cur[j] = src[j];
@@ -1283,7 +1288,7 @@ size_t sumcheck_scratch_bytes(const zc_ctx* ctx, const zc_params* p) {
 
 zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, int on_dev,
                          const uint8_t (*roots)[32], cudaStream_t st, uint8_t* proof,
-                         bool proof_on_dev) {
+                         bool proof_on_dev, bool v2) {
   const uint32_t n = p->n, d = p->d;
   const ScPlan P = sc_plan(p, ctx->sm_count, ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_GRID),
                            ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_TAIL_LOG),
@@ -1295,7 +1300,7 @@ zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* col
                            ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_PROD_FUSE));
   const int c = P.c;
   const uint64_t N = 1ull << n;
-  const size_t psize = 16 + 32 * ((size_t)n * (d + 2) + c);
+  const size_t psize = 16 + 32 * ((size_t)n * (v2 ? d + 1 : d + 2) + c);
   zc_status s = ensure_arena(ctx, sumcheck_scratch_bytes(ctx, p));
   if (s != ZC_OK) return s;
   Arena& ar = ctx->arena;
@@ -1333,7 +1338,7 @@ zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* col
   ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[1], st));
   uint32_t launches = 0;
   s = sc_enqueue(p, P, src, B, ctx->dconst, ctx->dtabs, ctx->hconst, ctx->skip_point, st, &launches,
-                 ctx->ev);
+                 ctx->ev, v2);
   ctx->launches += launches;
   if (s != ZC_OK) {
     ctx->err = "kernel launch failed";

@@ -29,7 +29,7 @@ def gate_sum(m: int) -> int:
     return ZC_GATE_SUM | (m << 8)
 
 
-ZC_FORM_SUMCHECK, ZC_FORM_NTT = 1, 2
+ZC_FORM_SUMCHECK, ZC_FORM_NTT, ZC_FORM_SUMCHECK_EQ = 1, 2, 3
 ZC_TUNE_SC_GRID, ZC_TUNE_SC_TAIL_LOG, ZC_TUNE_NTT_TILE_LOG, ZC_TUNE_NTT_MINB = 1, 2, 3, 4
 ZC_TUNE_SC_SMALL_LOG, ZC_TUNE_SC_MINB, ZC_TUNE_SC_PROD_PPT, ZC_TUNE_SC_CHUNK_LOG = 5, 6, 7, 8
 ZC_TUNE_BATCH_LANES, ZC_TUNE_SC_QUAD_LOG, ZC_TUNE_SC_PROD_FUSE, ZC_TUNE_NTT_TWO_LOG = 9, 10, 11, 12
@@ -88,6 +88,8 @@ def lib(path: str | None = None):
         L.zc_proof_size.restype = ctypes.c_int
         L.zc_prove_sumcheck.argtypes = [vp, P(zc_params), vp, ctypes.c_int, vp, vp, u8p, sz, P(sz)]
         L.zc_prove_sumcheck.restype = ctypes.c_int
+        L.zc_prove_sumcheck_eq.argtypes = [vp, P(zc_params), vp, ctypes.c_int, vp, vp, u8p, sz, P(sz)]
+        L.zc_prove_sumcheck_eq.restype = ctypes.c_int
         L.zc_prove_ntt.argtypes = [vp, P(zc_params), vp, ctypes.c_int, vp, vp, u8p, sz, P(sz), vp,
                                    ctypes.c_int]
         L.zc_prove_ntt.restype = ctypes.c_int
@@ -221,18 +223,20 @@ class Context:
             cols = [_host_array(c) for c in cols]
         return _Ptrs(cols), 1 if on_dev else 0
 
-    def prove_sumcheck(self, gate, n, d, cols, roots=None, stream=None, proof_out=None):
+    def prove_sumcheck(self, gate, n, d, cols, roots=None, stream=None, proof_out=None, eq_factored=False):
         """SumCheck-form proof.  Returns the proof (numpy uint8) unless proof_out
-        (a device tensor) is given, in which case the call is asynchronous."""
+        (a device tensor) is given, in which case the call is asynchronous.
+        eq_factored: zc_prove_sumcheck_eq (rounds carry H_i(0..d), "ZCS2")."""
         p = zc_params(gate, n, d, 0)
         P, on_dev = self._cols(cols)
         rb, rp = _roots_arg(roots)
-        cap = proof_size(gate, n, d, ZC_FORM_SUMCHECK)
+        form = ZC_FORM_SUMCHECK_EQ if eq_factored else ZC_FORM_SUMCHECK
+        cap = proof_size(gate, n, d, form)
         out = proof_out if proof_out is not None else np.zeros(cap, np.uint8)
         ln = ctypes.c_size_t()
-        st = lib().zc_prove_sumcheck(self.h, ctypes.byref(p), P.p, on_dev, rp, _stream_ptr(stream),
-                                     _addr(out), cap, ctypes.byref(ln))
-        self._check(st, "zc_prove_sumcheck")
+        fn = lib().zc_prove_sumcheck_eq if eq_factored else lib().zc_prove_sumcheck
+        st = fn(self.h, ctypes.byref(p), P.p, on_dev, rp, _stream_ptr(stream), _addr(out), cap, ctypes.byref(ln))
+        self._check(st, "zc_prove_sumcheck_eq" if eq_factored else "zc_prove_sumcheck")
         return out
 
     def prove_ntt(self, gate, n, d, cols, roots=None, stream=None, proof_out=None, q_out=None,

@@ -95,3 +95,19 @@ def test_host_verifier_step_radix_domain(gate, n, d, ks):
     assert not zc.verify(gate, n, d, 2, cols, pn, q=q2, log_blowup=w)
     # the header names another domain than the caller's: malformed, not accepted
     assert not zc.verify(gate, n, d, 2, cols, pn, q=q, log_blowup=ks[0] + 1)
+
+
+@pytest.mark.parametrize("gate,n,d", [(1, 6, 3), (2, 5, 4), (2, 1, 2), (zc.gate_sum(2), 4, 3)])
+def test_host_verifier_eq_factored(gate, n, d):
+    """ZC_FORM_SUMCHECK_EQ: the library's host verifier accepts the oracle's
+    eq-factored proofs, rejects tampered ones, and sizes them as the oracle."""
+    assert zc.proof_size(gate, n, d, zc.ZC_FORM_SUMCHECK_EQ) == oracle.proof_size_eq(gate, n, d)
+    cols = witness.generate(gate, n, d, 90 + n)
+    pb = oracle.prove_sumcheck_eq(gate, n, d, cols)
+    assert zc.verify(gate, n, d, zc.ZC_FORM_SUMCHECK_EQ, cols, pb)
+    assert not zc.verify(gate, n, d, zc.ZC_FORM_SUMCHECK, cols, pb)
+    bad = witness.generate(gate, n, d, 90 + n, tamper=True)
+    assert not zc.verify(gate, n, d, zc.ZC_FORM_SUMCHECK_EQ, bad, oracle.prove_sumcheck_eq(gate, n, d, bad))
+    x = bytearray(pb)
+    x[16 + 32 * (d + 1) + 1] ^= 8
+    assert not zc.verify(gate, n, d, zc.ZC_FORM_SUMCHECK_EQ, cols, bytes(x))

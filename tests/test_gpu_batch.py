@@ -113,6 +113,6 @@ def test_batch_bad_arguments(ctx):
     insts = _setup([(1, 1, 4, 3)], 7400)
     forms, params, cols, proofs, qs = _args(insts)
     with pytest.raises(zc.ZCError):
-        ctx.prove_batch([3], params, cols, proofs, qs)
+        ctx.prove_batch([9], params, cols, proofs, qs)      # no such form
     with pytest.raises(zc.ZCError):
         ctx.prove_batch(forms, [(1, 30, 3, 0)], cols, proofs, qs)
