@@ -599,16 +599,20 @@ def run_served(args, world, rank, local):
     torch.cuda.set_device(local)
     ctx = zc.Context(local, max_n=24, max_d=16)
     model = CostModel()
-    model.calibrate(ctx, [(1, 3), (2, 8), (2, 16)], ns=[12, 14, 16, 18, 20], reps=3)
+    # measured over the whole served range of n (no extrapolation past n = 24)
+    model.calibrate(ctx, [(1, 3), (2, 8), (2, 16)], ns=[12, 14, 16, 18, 20, 22, 24], reps=3)
     rates = [float(r) for r in args.rates.split(",")]
     lists = {r: workloads.served_requests(r, args.requests) for r in rates}
     budget = 180 * 10**9
-    srv = serve.Server(ctx, model=model, slots=8, hbm_budget_bytes=budget)
+    prio_bytes = 1 << 30   # requests with >= 1 GiB of scratch (the n >= 22 shapes) get the priority slot
+    srv = serve.Server(ctx, model=model, slots=8, hbm_budget_bytes=budget, priority_bytes=prio_bytes)
+    flat = serve.Server(ctx, model=model, slots=8, hbm_budget_bytes=budget)
     one = serve.Server(ctx, model=model, slots=1, hbm_budget_bytes=budget, in_order=True)
     t_pool = time.perf_counter()
     srv.load_pool([s for lst in lists.values() for _, s in lst])
     t_pool = time.perf_counter() - t_pool
     one.pool = srv.pool
+    flat.pool = srv.pool
     # warm-up: every shape once through the loop (tables, lanes, pool allocation)
     warm = [(0.0, s) for s in sorted(srv.pool, key=lambda s: (s.n, s.d))]
     srv.run(srv.build(warm))
@@ -625,16 +629,20 @@ def run_served(args, world, rank, local):
         rep = serve.report(reqs, res)
         base_reqs = one.build(lst)
         base = serve.report(base_reqs, one.run(base_reqs))
+        flat_reqs = flat.build(lst)
+        flat_rep = serve.report(flat_reqs, flat.run(flat_reqs))
         exact = all(a["proof"].cpu().numpy().tobytes() == b["proof"].cpu().numpy().tobytes()
-                    for a, b in zip(reqs, base_reqs))
-        rows[str(int(r))] = {"served": rep, "one_at_a_time": base, "exact_vs_one_at_a_time": exact}
+                    == c["proof"].cpu().numpy().tobytes() for a, b, c in zip(reqs, base_reqs, flat_reqs))
+        rows[str(int(r))] = {"served": rep, "one_at_a_time": base, "served_no_priority_slot": flat_rep,
+                             "exact_vs_one_at_a_time": exact}
     clk = clocks.stop()
     mid = rows[str(int(rates[len(rates) // 2]))]["served"]
     config = {"workload": "served: Poisson arrivals, n uniform 12..24, d in {3 (Plonk), 8, 16 (product)}, "
                           "witness pool per shape on the device, admission by scratch footprint against "
-                          "a 180 GB pool, 8 slots, cost-model routing; baseline: the same requests one "
-                          "at a time (1 slot)",
-              "rates_req_s": rates, "requests_per_rate": args.requests, "slots": 8,
+                          "a 180 GB pool, 8 slots (requests with >= 1 GiB of scratch one at a time on a "
+                          "high-priority slot), cost-model routing calibrated at n = 12..24; baselines: "
+                          "the same requests one at a time (1 slot) and on 8 equal slots",
+              "rates_req_s": rates, "requests_per_rate": args.requests, "slots": 8, "priority_bytes": prio_bytes,
               "hbm_budget_bytes": budget, "parallelism": f"replicas x{world}",
               "l2": "pool witnesses (tens of GB) larger than L2; no flush"}
     line = _base_line(args, world, mid["p99_ms"], "ms", False, config)

@@ -317,6 +317,11 @@ typedef struct {
   uint32_t in_order;          /* 1: admit strictly by arrival; 0: a request that
                                  does not fit yet lets later ones that fit pass */
   double timeout_s;           /* ZC_ERR_TIMEOUT if the run lasts longer (0: none) */
+  uint64_t priority_bytes;    /* 0: every slot alike.  Otherwise requests whose
+                                 scratch is at least this many bytes run on slot 0,
+                                 a stream of the device's greatest priority, one at
+                                 a time in arrival order, and smaller requests use
+                                 the other slots around them */
 } zc_serve_opts;
 
 /* Run the loop until every request completed; results[i] for reqs[i].

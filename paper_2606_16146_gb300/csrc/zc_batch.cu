@@ -58,7 +58,14 @@ zc_status make_lanes(zc_ctx* ctx, int K) {
     for (int i = 0; i < 8; i++) cudaEventCreate(&L->ev[i]);
     cudaStream_t s;
     cudaEvent_t e;
-    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    // lane 0 runs at the device's greatest stream priority: in a batch it
+    // gets the longest instance (longest-first assignment), in serving the
+    // large requests (zc_serve_opts.priority_bytes)
+    int lo = 0, hi = 0;
+    if (ctx->lanes.empty() && cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess)
+      cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, hi);
+    else
+      cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
     ctx->lanes.push_back(L);
     ctx->lane_streams.push_back(s);

@@ -228,12 +228,24 @@ zc_status zc_serve(zc_ctx* ctx, const zc_request* reqs, uint32_t count, const zc
       completed++;
       progress = true;
     }
-    // admissions
+    // admissions: with priority_bytes set, a request whose scratch is at
+    // least that large runs on slot 0 (the greatest stream priority), one
+    // such request at a time in arrival order, and the others use slots
+    // 1..K-1, so small proofs fill the GPU around a large one instead of
+    // waiting behind it or slowing it down
+    const bool prio = o->priority_bytes > 0 && K > 1;
     for (auto it = waiting.begin(); it != waiting.end();) {
-      int k = 0;
-      while (k < K && slot_req[k] >= 0) k++;
-      if (k == K) break;
       const uint32_t i = *it;
+      const bool big = prio && fp[i] >= o->priority_bytes;
+      int k = prio && !big ? 1 : 0;
+      if (big) k = slot_req[0] >= 0 ? K : 0;
+      else
+        while (k < K && slot_req[k] >= 0) k++;
+      if (k == K) {
+        if (o->in_order || !prio) break;
+        ++it;
+        continue;
+      }
       const size_t off = pool.take(fp[i]);
       if (off == SIZE_MAX) {
         res[i].waited_for_memory = 1;

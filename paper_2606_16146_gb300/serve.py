@@ -17,12 +17,13 @@ from .router import CostModel
 
 class Server:
     def __init__(self, ctx: "zc.Context", model: CostModel | None = None, slots: int = 8,
-                 hbm_budget_bytes: int = 180 << 30, in_order: bool = False):
+                 hbm_budget_bytes: int = 180 << 30, in_order: bool = False, priority_bytes: int = 0):
         self.ctx = ctx
         self.model = model
         self.slots = slots
         self.budget = hbm_budget_bytes
         self.in_order = in_order
+        self.priority_bytes = priority_bytes
         self.pool: dict[workloads.Shape, list] = {}
 
     def load_pool(self, shapes, seed_of=workloads.shape_seed) -> None:
@@ -55,7 +56,7 @@ class Server:
 
     def run(self, reqs: list[dict], timeout_s: float = 0.0) -> list[dict]:
         return self.ctx.serve(reqs, slots=self.slots, hbm_budget_bytes=self.budget,
-                              in_order=self.in_order, timeout_s=timeout_s)
+                              in_order=self.in_order, timeout_s=timeout_s, priority_bytes=self.priority_bytes)
 
 
 def report(reqs: list[dict], results: list[dict]) -> dict:

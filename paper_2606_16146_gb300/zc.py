@@ -64,7 +64,8 @@ class zc_result(ctypes.Structure):
 
 class zc_serve_opts(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_uint32), ("hbm_budget_bytes", ctypes.c_uint64),
-                ("in_order", ctypes.c_uint32), ("timeout_s", ctypes.c_double)]
+                ("in_order", ctypes.c_uint32), ("timeout_s", ctypes.c_double),
+                ("priority_bytes", ctypes.c_uint64)]
 
 
 _lib = None
@@ -310,10 +311,13 @@ class Context:
                                            ctypes.byref(out)), "zc_scratch_bytes")
         return int(out.value)
 
-    def serve(self, requests, slots=8, hbm_budget_bytes=180 << 30, in_order=False, timeout_s=0.0):
+    def serve(self, requests, slots=8, hbm_budget_bytes=180 << 30, in_order=False, timeout_s=0.0,
+              priority_bytes=0):
         """Run the request loop.  requests: dicts with arrival_s, gate, n, d, form, cols
         (device tensors), proof (device tensor) and optional q (device tensor).  Returns one
-        dict per request: admit_s, done_s, scratch_bytes, slot, waited_for_memory, status."""
+        dict per request: admit_s, done_s, scratch_bytes, slot, waited_for_memory, status.
+        priority_bytes > 0: requests with at least that much scratch run one at a time on
+        the high-priority slot 0, the others on slots 1.."""
         cnt = len(requests)
         R = (zc_request * max(1, cnt))()
         keep = []
@@ -327,7 +331,7 @@ class Context:
             R[i].proof = _addr(r["proof"])
             R[i].q_out = _addr(r["q"]) if r.get("q") is not None else None
         out = (zc_result * max(1, cnt))()
-        o = zc_serve_opts(slots, hbm_budget_bytes, 1 if in_order else 0, timeout_s)
+        o = zc_serve_opts(slots, hbm_budget_bytes, 1 if in_order else 0, timeout_s, priority_bytes)
         st = lib().zc_serve(self.h, R, cnt, ctypes.byref(o), out)
         res = [{"admit_s": out[i].admit_s, "done_s": out[i].done_s,
                 "scratch_bytes": int(out[i].scratch_bytes), "slot": int(out[i].slot),

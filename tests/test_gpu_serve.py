@@ -125,3 +125,43 @@ def test_routed_by_measured_cost(ctx, expected):
         assert q["form"] == want
     results = srv.run(reqs, timeout_s=60)
     _check(reqs, results, expected)
+
+
+def test_distinct_witnesses_equal_alone(ctx):
+    """Every request has its own witness (seed 4000 + i), so no two requests
+    share inputs; served concurrently with arrivals that overlap, each proof
+    equals the oracle's proof of that request alone."""
+    import torch
+    from paper_2606_16146_gb300 import witness
+    shapes = [Shape(1, 10, 3), Shape(2, 9, 8), Shape(1, 14, 3), Shape(2, 11, 4), Shape(2, 8, 16),
+              Shape(1, 11, 3), Shape(2, 13, 8), Shape(1, 9, 3)]
+    reqs, want = [], []
+    for i in range(24):
+        s = shapes[(5 * i + 2) % len(shapes)]
+        form = zc.ZC_FORM_NTT if i % 4 == 1 else (zc.ZC_FORM_SUMCHECK_EQ if i % 4 == 3 else zc.ZC_FORM_SUMCHECK)
+        cols = witness.generate(s.gate, s.n, s.d, 4000 + i)
+        if form == zc.ZC_FORM_NTT:
+            want.append(oracle.prove_ntt(s.gate, s.n, s.d, cols)[0])
+        elif form == zc.ZC_FORM_SUMCHECK_EQ:
+            want.append(oracle.prove_sumcheck_eq(s.gate, s.n, s.d, cols))
+        else:
+            want.append(oracle.prove_sumcheck(s.gate, s.n, s.d, cols))
+        reqs.append({"arrival_s": 0.00005 * i, "gate": s.gate, "n": s.n, "d": s.d, "form": form,
+                     "cols": [torch.from_numpy(c).cuda() for c in cols],
+                     "proof": torch.zeros(zc.proof_size(s.gate, s.n, s.d, form), dtype=torch.uint8,
+                                          device="cuda")})
+    # footprints are admitted in 2 MiB granules: the threshold is the second
+    # smallest granule count, so both classes of request occur
+    gran = 2 << 20
+    fps = sorted({-(-ctx.scratch_bytes(q["gate"], q["n"], q["d"], q["form"]) // gran) * gran for q in reqs})
+    assert len(fps) >= 2
+    for prio in (0, fps[1]):
+        for q in reqs:
+            q["proof"].zero_()
+        res = ctx.serve(reqs, slots=6, hbm_budget_bytes=2 << 30, timeout_s=120, priority_bytes=prio)
+        assert all(r["status"] == 0 for r in res)
+        assert max(r["slot"] for r in res) >= 2            # requests overlapped on several slots
+        for q, r, w in zip(reqs, res, want):
+            assert proof_bytes(q["proof"]) == w
+            if prio:                                     # large requests only on slot 0, small ones never
+                assert (r["slot"] == 0) == (r["scratch_bytes"] >= prio)
