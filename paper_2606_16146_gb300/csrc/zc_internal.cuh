@@ -48,8 +48,9 @@ struct ScState {        // SumCheck per-proof device state
   fr claim;              // H_{i-1}(alpha_{i-1}), level 0
   fr ci;                 // prod_{j<i} eq(alpha_j, r_j), level 1
   uint32_t counter[kMaxN];  // CTAs that finished round i (last one runs the challenge)
-  uint32_t err;
-  uint32_t pad[7];
+  uint32_t err;          // bit 0: a column value >= r; bit 1: a bounded device wait gave up
+  uint32_t go;           // persistent round kernel: rounds whose challenge is out
+  uint32_t pad[6];
 };
 
 struct NttState {       // NTT per-proof device state

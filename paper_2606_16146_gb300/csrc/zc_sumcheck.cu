@@ -98,6 +98,8 @@ struct ScRoundArgs {
   uint32_t full;       // evaluate H at all of 0..d-1 (no point derived from the claim)
   uint32_t next_derives;  // the next round derives a point: keep the claim
   uint32_t v2;         // eq-factored proof: rounds carry H_i(0..d), not G_i(0..d+1)
+  int round_end;       // persistent round kernel: rounds [round, round_end)
+  uint32_t spin_limit; // persistent round kernel: polls of a hand-off before giving up
   ScState* st;
   fr* partials;
   uint8_t* proof;
@@ -275,6 +277,41 @@ __device__ void sc_challenge(ChalSmem& S, int np, int d, int i, ScState* st, uin
   __syncthreads();
 }
 
+// S.Hc[p] = sum of the np per-CTA partial sums of nwork CTAs.  G warps
+// share each point; every lane issues its L2 loads four at a time, so the
+// sum costs a few L2 round trips however many CTAs wrote partials.  All
+// threads of the CTA.
+__device__ void sc_sum_partials(ChalSmem& S, const fr* partials, uint32_t nwork, int np) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+  const int G = np < nw ? nw / np : 1, per_pass = nw / G;
+  fr* W = &S.tmp[0][0];  // nw <= 2 kMaxPts partial sums, free until the challenge
+  for (int base = 0; base < np; base += per_pass) {
+    const int p = base + warp / G, g = warp % G;
+    fr s = fr_zero();
+    if (warp / G < per_pass && p < np) {
+      const uint32_t stride = 32u * G;
+      uint32_t b = lane + 32u * g;
+      for (; b + 3 * stride < nwork; b += 4 * stride) {
+        const fr x0 = ld_fr_l2(partials + (size_t)b * np + p);
+        const fr x1 = ld_fr_l2(partials + (size_t)(b + stride) * np + p);
+        const fr x2 = ld_fr_l2(partials + (size_t)(b + 2 * stride) * np + p);
+        const fr x3 = ld_fr_l2(partials + (size_t)(b + 3 * stride) * np + p);
+        s = fr_add(s, fr_add(fr_add(x0, x1), fr_add(x2, x3)));
+      }
+      for (; b < nwork; b += stride) s = fr_add(s, ld_fr_l2(partials + (size_t)b * np + p));
+    }
+    s = warp_sum(s);
+    if (lane == 0) W[warp] = s;
+    __syncthreads();
+    if (t < per_pass && base + t < np) {
+      fr v = W[t * G];
+      for (int q = 1; q < G; q++) v = fr_add(v, W[t * G + q]);
+      S.Hc[base + t] = v;
+    }
+    __syncthreads();
+  }
+}
+
 // The last CTA to arrive reduces the per-CTA sums and runs the challenge.
 __device__ void sc_finish_round(const ScRoundArgs& A, int np) {
   __shared__ bool am_last;
@@ -287,36 +324,7 @@ __device__ void sc_finish_round(const ScRoundArgs& A, int np) {
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  // G warps share each point; every lane issues its L2 loads four at a time,
-  // so the sum costs a few L2 round trips however many CTAs wrote partials.
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
-  const int G = np < nw ? nw / np : 1, per_pass = nw / G;
-  fr* W = &S.tmp[0][0];  // nw <= 2 kMaxPts partial sums, free until the challenge
-  for (int base = 0; base < np; base += per_pass) {
-    const int p = base + warp / G, g = warp % G;
-    fr s = fr_zero();
-    if (warp / G < per_pass && p < np) {
-      const uint32_t stride = 32u * G;
-      uint32_t b = lane + 32u * g;
-      for (; b + 3 * stride < A.nwork; b += 4 * stride) {
-        const fr x0 = ld_fr_l2(A.partials + (size_t)b * np + p);
-        const fr x1 = ld_fr_l2(A.partials + (size_t)(b + stride) * np + p);
-        const fr x2 = ld_fr_l2(A.partials + (size_t)(b + 2 * stride) * np + p);
-        const fr x3 = ld_fr_l2(A.partials + (size_t)(b + 3 * stride) * np + p);
-        s = fr_add(s, fr_add(fr_add(x0, x1), fr_add(x2, x3)));
-      }
-      for (; b < A.nwork; b += stride) s = fr_add(s, ld_fr_l2(A.partials + (size_t)b * np + p));
-    }
-    s = warp_sum(s);
-    if (lane == 0) W[warp] = s;
-    __syncthreads();
-    if (t < per_pass && base + t < np) {
-      fr v = W[t * G];
-      for (int q = 1; q < G; q++) v = fr_add(v, W[t * G + q]);
-      S.Hc[base + t] = v;
-    }
-    __syncthreads();
-  }
+  sc_sum_partials(S, A.partials, A.nwork, np);
   sc_challenge(S, np, (int)A.d, A.round, A.st, A.proof, A.C, A.tabs, A.next_derives != 0, A.v2 != 0);
 }
 
@@ -597,6 +605,7 @@ __global__ void k_sc_setup(ScSetupArgs A) {
     A.st->claim = fr_zero();
     A.st->ci = A.C->one;
     A.st->err = 0;
+    A.st->go = 0;
   }
   __syncthreads();
   if ((int)threadIdx.x < A.n) A.st->r[threadIdx.x] = fr_mul(raw[threadIdx.x], A.C->r2);
@@ -729,6 +738,75 @@ __global__ void __launch_bounds__(TPP * PB) k_sc_plonk_chunk(ScRoundArgs A) {
   if (threadIdx.x < NPT) st_fr(A.partials + (size_t)blockIdx.x * NPT + threadIdx.x, part[threadIdx.x]);
   __syncthreads();
   sc_finish_round(A, NPT);
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Plonk rounds [A.round, A.round_end) (16 threads per pair, every point
+// evaluated) in one cooperative launch, so the latency-bound rounds pay no
+// launch between them.  Each CTA folds and evaluates its chunks of a round
+// and writes its partial sums; the last CTA to arrive sums them, runs the
+// challenge and releases the next round through st->go.  The other CTAs poll
+// st->go at most A.spin_limit times; a CTA that gives up sets bit 1 of
+// st->err and returns, after which every later hand-off also gives up, so
+// the launch always ends and the proof reports the timeout.  Tables are read
+// through L2: other CTAs rewrote them in the previous round.
+__global__ void __launch_bounds__(16 * kSmallPB) k_sc_plonk_rounds(ScRoundArgs A) {
+  __shared__ PlonkChunkSmem<kSmallPB> S;
+  __shared__ fr part[4];
+  __shared__ ChalSmem CS;
+  __shared__ int flag;  // 1: this CTA runs the challenge; 2: a wait gave up
+  const uint32_t G = gridDim.x;
+  const uint64_t N = 1ull << A.n;
+  for (int i = A.round; i < A.round_end; i++) {
+    const uint64_t h = N >> (i + 1);
+    const uint32_t nwork = (uint32_t)min((h + kSmallPB - 1) / kSmallPB, (uint64_t)G);
+    const fr alpha = ld_fr_l2(&A.st->alpha[i - 1]);
+    fr acc = fr_zero();
+    if (blockIdx.x < nwork)
+      for (uint64_t kb = (uint64_t)blockIdx.x * kSmallPB; kb < h; kb += (uint64_t)nwork * kSmallPB)
+        plonk_chunk<kSmallPB, 16, true, true>(
+            S, i == A.round ? (const fr* const*)A.src : (const fr* const*)A.dst, A.dst, h, kb, alpha, 0u,
+            A.E + A.eq_hi[i], A.E + A.eq_lo[i], A.m_lo[i], acc);
+    plonk_chunk_reduce<kSmallPB, 4>(acc, part);
+    if (blockIdx.x < nwork && threadIdx.x < 4)
+      st_fr(A.partials + (size_t)blockIdx.x * 4 + threadIdx.x, part[threadIdx.x]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned prev = atomicAdd(&A.st->counter[i], 1u);
+      flag = prev == G - 1 ? 1 : 0;
+    }
+    __syncthreads();
+    if (flag == 1) {
+      __threadfence();
+      sc_sum_partials(CS, A.partials, nwork, 4);
+      sc_challenge(CS, 4, 3, i, A.st, A.proof, A.C, A.tabs, false, A.v2 != 0);
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(&A.st->go, (uint32_t)(i + 1));
+      }
+    } else {
+      if (threadIdx.x == 0) {
+        uint32_t polls = 0;
+        while (ld_acquire_u32(&A.st->go) < (uint32_t)(i + 1)) {
+          if (++polls > A.spin_limit) {
+            atomicOr(&A.st->err, 2u);
+            flag = 2;
+            break;
+          }
+          __nanosleep(256);
+        }
+      }
+      __syncthreads();
+      if (flag == 2) return;
+    }
+    __syncthreads();
+  }
 }
 
 // MLE update by alpha_{round-1}: dst[j][k] = src[j][k] + alpha (src[j][k+h] - src[j][k])
@@ -956,7 +1034,8 @@ __global__ void __launch_bounds__(PLONK ? kTailThreads : 256, 1) k_sc_tail(ScRou
       for (int b = 0; b < 4; b++) pv[32 * j + 4 * q + b] = (uint8_t)(v.v[q] >> (8 * b));
   }
   if (threadIdx.x == 0) {
-    const char* mg = A.st->err ? "ZCE!" : (A.v2 ? "ZCS2" : "ZCS1");
+    const uint32_t e = A.st->err;
+    const char* mg = (e & 2u) ? "ZCT!" : (e ? "ZCE!" : (A.v2 ? "ZCS2" : "ZCS1"));
     for (int b = 0; b < 4; b++) A.proof[b] = (uint8_t)mg[b];
     const uint32_t hv[3] = {A.gate, (uint32_t)n, A.d};
     for (int q = 0; q < 3; q++)
@@ -988,6 +1067,7 @@ struct ScPlan {
   int c, G, grid_plonk, grid_prod, npmax;
   uint64_t tail_pairs, small_pairs, chunk_pairs;
   int grid_chunk, grid_quad;
+  int grid_rounds;      // co-resident CTAs of the persistent round kernel
   uint64_t quad_pairs;  // Plonk rounds 2.. in (chunk_pairs, quad_pairs]: 4 threads per pair
   int minb;  // Plonk round kernels: resident CTAs per SM they are compiled for
   int ppt;   // product round kernel: points per thread (1 or kPP; 0: by round, prod_ppt)
@@ -1068,6 +1148,7 @@ static ScPlan sc_plan(const zc_params* p, int SMs, int grid = 0, int tail_log = 
   P.small_pairs = small_log > 0 ? 1ull << small_log : kSmallPairsPlonk;
   P.chunk_pairs = chunk_log > 0 ? 1ull << chunk_log : kChunkPairsPlonk;
   P.grid_chunk = SMs * resident_ctas(reinterpret_cast<const void*>(k_sc_plonk_chunk<16, kSmallPB, false>));
+  P.grid_rounds = SMs * resident_ctas(reinterpret_cast<const void*>(k_sc_plonk_rounds), 16 * kSmallPB);
   P.quad_pairs = quad_log > 0 ? 1ull << quad_log : kQuadPairsPlonk;
   P.grid_quad = SMs * resident_ctas(reinterpret_cast<const void*>(k_sc_plonk_chunk<4, kQuadPB, false>), 4 * kQuadPB);
   P.minb = minb == 1 ? 1 : 2;
@@ -1102,13 +1183,38 @@ static bool sc_carve(Arena& ar, const ScPlan& P, uint64_t N, size_t psize, ScBuf
   return B.tab[P.c - 1] && B.partials && B.E && B.st && B.roots && B.proof;
 }
 
+// Polls of a persistent round kernel's hand-off before it gives up (about a
+// second); ZC_SPIN_LIMIT overrides it (tests make the wait run out).
+static uint32_t persistent_spin_limit() {
+  const char* e = std::getenv("ZC_SPIN_LIMIT");
+  if (e && *e) return (uint32_t)std::strtoul(e, nullptr, 10);
+  return 1u << 22;
+}
+
+// Whether a proof on this context may use the persistent round kernel: not
+// on batch or serving lanes (their kernels share the GPU with other
+// instances' kernels, and a batch is captured into a graph), and not when
+// ZC_SC_PERSISTENT=0.
+static bool persistent_allowed(const zc_ctx* ctx, cudaStream_t st) {
+  const char* e = std::getenv("ZC_SC_PERSISTENT");
+  if (e && e[0] == '0') return false;
+  if (ctx->table_owner) return false;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return cs == cudaStreamCaptureStatusNone;
+}
+
 // Queue every kernel of one proof on st (B.roots must hold the column roots
 // by the time the queue runs).  ev: optional events; [2] and [3] bracket the
 // round-1 launch.
 static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const* src,
                             const ScBuffers& B, const DevConst* dC, const fr* dtabs,
                             const DevConst& hC, int skip_point, cudaStream_t st,
-                            uint32_t* launches, cudaEvent_t* ev, bool v2 = false) {
+                            uint32_t* launches, cudaEvent_t* ev, bool v2 = false,
+                            bool persistent = false) {
   const uint32_t gate = p->gate, n = p->n, d = p->d;
   const int c = P.c;
   const uint64_t N = 1ull << n;
@@ -1183,6 +1289,26 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
     for (int j = 0; j < c; j++) {
       R.src[j] = cur[j];
       R.dst[j] = B.tab[j];
+    }
+    if (plonk && i > 0 && h <= P.chunk_pairs && persistent && R.full && h / 2 > tail_pairs) {
+      // every remaining round before the tail in one cooperative launch
+      // (all of them evaluate every point: h only shrinks)
+      uint32_t end = i;
+      while (end < n && (N >> (end + 1)) > tail_pairs) end++;
+      R.round_end = (int)end;
+      R.spin_limit = persistent_spin_limit();
+      const uint32_t G = (uint32_t)std::min<uint64_t>(
+          std::min<uint64_t>((h + kSmallPB - 1) / kSmallPB, (uint64_t)P.grid_chunk), (uint64_t)P.grid_rounds);
+      R.nwork = G;
+      void* kargs[] = {&R};
+      if (G >= 2 && cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_sc_plonk_rounds), dim3(G),
+                                                dim3(16 * kSmallPB), kargs, 0, st) == cudaSuccess) {
+        for (int j = 0; j < 8; j++) cur[j] = B.tab[j];
+        *launches += 1;
+        i = end;
+        break;
+      }
+      cudaGetLastError();  // not co-resident here: the per-round kernels below
     }
     if (plonk && i > 0 && h <= P.chunk_pairs) {
       R.nwork = (uint32_t)std::min<uint64_t>((h + kSmallPB - 1) / kSmallPB, (uint64_t)P.grid_chunk);
@@ -1338,7 +1464,7 @@ zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* col
   ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[1], st));
   uint32_t launches = 0;
   s = sc_enqueue(p, P, src, B, ctx->dconst, ctx->dtabs, ctx->hconst, ctx->skip_point, st, &launches,
-                 ctx->ev, v2);
+                 ctx->ev, v2, persistent_allowed(ctx, st));
   ctx->launches += launches;
   if (s != ZC_OK) {
     ctx->err = "kernel launch failed";
@@ -1353,6 +1479,10 @@ zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* col
     if (std::memcmp(proof, "ZCE!", 4) == 0) {
       ctx->err = "column value >= r";
       return ZC_ERR_ARG;
+    }
+    if (std::memcmp(proof, "ZCT!", 4) == 0) {
+      ctx->err = "a bounded device wait gave up (persistent round kernel)";
+      return ZC_ERR_TIMEOUT;
     }
   }
   return ZC_OK;
