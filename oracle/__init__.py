@@ -56,6 +56,10 @@ def lib():
             L.zo_prove_sumcheck_eq.argtypes = [u32, u32, u32, p, p, p, sz, ctypes.POINTER(sz), p, p]
             L.zo_verify_sumcheck_eq.argtypes = [u32, u32, u32, p, p, p, sz, ctypes.POINTER(ctypes.c_int)]
             L.zo_proof_size_eq.argtypes = [u32, u32, u32, ctypes.POINTER(sz)]
+            L.zo_pcs_proof_size.argtypes = [u32, u32, u32, u32, ctypes.POINTER(sz)]
+            L.zo_pcs_commit.argtypes = [u32, u32, u32, p, p]
+            L.zo_pcs_open.argtypes = [u32, u32, u32, u32, p, p, p, p, sz, ctypes.POINTER(sz)]
+            L.zo_pcs_verify.argtypes = [u32, u32, u32, u32, p, p, p, p, sz, ctypes.POINTER(ctypes.c_int)]
             L.zo_prove_ntt.argtypes = [u32, u32, u32, u32, p, p, p, sz, ctypes.POINTER(sz), p]
             L.zo_verify_ntt.argtypes = [u32, u32, u32, p, p, p, sz, p, ctypes.POINTER(ctypes.c_int)]
             L.zo_proof_size.argtypes = [u32, u32, u32, u32, ctypes.POINTER(sz)]
@@ -168,6 +172,55 @@ def verify_sumcheck_eq(gate, n, d, cols, proof, roots=None) -> bool:
     if st != 0:
         return False
     return bool(acc.value)
+
+
+# ---- hash-based PCS around the ZeroCheck (Ligero-style; see zc_oracle.c)
+
+def pcs_default_nc(n: int) -> int:
+    return min(n, 12)
+
+
+def pcs_proof_size(n: int, c: int, t: int, nc: int | None = None) -> int:
+    out = ctypes.c_size_t()
+    if lib().zo_pcs_proof_size(n, nc or pcs_default_nc(n), c, t, ctypes.byref(out)) != 0:
+        raise ValueError("bad PCS shape")
+    return out.value
+
+
+def pcs_commit(n: int, cols, nc: int | None = None) -> bytes:
+    """Merkle root over the rate-1/4 row encodings of the c columns."""
+    C = _Cols(cols)
+    root = np.zeros(32, np.uint8)
+    if lib().zo_pcs_commit(n, nc or pcs_default_nc(n), len(cols), C.p, _ptr(root)) != 0:
+        raise ValueError("pcs_commit rejected its input")
+    return root.tobytes()
+
+
+def pcs_open(n: int, cols, alpha, values, t: int, nc: int | None = None) -> bytes:
+    """Opening of every column at alpha (canonical bytes, n of them) with the
+    claimed values (canonical bytes, one per column), t queried columns."""
+    C = _Cols(cols)
+    a = np.frombuffer(b"".join(bytes(x) for x in alpha), dtype=np.uint8).copy()
+    v = np.frombuffer(b"".join(bytes(x) for x in values), dtype=np.uint8).copy()
+    cap = pcs_proof_size(n, len(cols), t, nc)
+    out = np.zeros(cap, np.uint8)
+    ln = ctypes.c_size_t()
+    st = lib().zo_pcs_open(n, nc or pcs_default_nc(n), len(cols), t, C.p, _ptr(a), _ptr(v), _ptr(out), cap,
+                           ctypes.byref(ln))
+    if st != 0:
+        raise ValueError(f"oracle pcs_open status {st}")
+    return out.tobytes()[: ln.value]
+
+
+def pcs_verify(n: int, c: int, t: int, root: bytes, alpha, values, proof, nc: int | None = None) -> bool:
+    a = np.frombuffer(b"".join(bytes(x) for x in alpha), dtype=np.uint8).copy()
+    v = np.frombuffer(b"".join(bytes(x) for x in values), dtype=np.uint8).copy()
+    r = np.frombuffer(bytes(root), dtype=np.uint8).copy()
+    pr = _buf(proof)
+    acc = ctypes.c_int(0)
+    st = lib().zo_pcs_verify(n, nc or pcs_default_nc(n), c, t, _ptr(r), _ptr(a), _ptr(v), _ptr(pr), pr.size,
+                             ctypes.byref(acc))
+    return st == 0 and bool(acc.value)
 
 
 def verify_sumcheck(gate, n, d, cols, proof, roots=None) -> bool:

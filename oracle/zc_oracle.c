@@ -1125,6 +1125,283 @@ int zo_verify_ntt(uint32_t gate, uint32_t n, uint32_t d, const uint8_t *const *c
     return 0;
 }
 
+/* ------------------------------- hash-based PCS around the ZeroCheck -- */
+/* Stages (1) and (3) of the prover workflow (Sec. 3.1): commit to the
+ * witness columns, then open them at the point the ZeroCheck's SumCheck
+ * ends in, with the lightweight hash-based commitment the paper points to
+ * (Ligero, Sec. 3.1).  The c columns (MLE tables of N = 2^n values, x_1 the
+ * most significant index bit) are m x w matrices, w = 2^nc (1 <= nc <= n;
+ * the library's default is min(n, 12)), m = 2^(n - nc), row i holding
+ * entries i w .. i w + w - 1.
+ *   Commit: every row is Reed-Solomon encoded at rate 1/4, as the values of
+ *   the polynomial with the row as coefficients at the W = 4w points
+ *   x_k = 7 w_W^k: E[i][k] = sum_l M[i][l] x_k^l.  Column digest
+ *   D_kj = SHA-256(enc(E_j[0][k]) | ... | enc(E_j[m-1][k])), leaf
+ *   L_k = SHA-256(D_k0 | ... | D_k,c-1), binary Merkle tree over the W
+ *   leaves, root = SHA-256(le64(W) | top).
+ *   Open at alpha with values v_j: transcript S = SHA-256(
+ *   "zerocheck-gb300/pcs-v1" | u32 n | u32 nc | u32 c | u32 t | root | enc(alpha_i)
+ *   | enc(v_j)); u_j = sum_i eq(alpha_1..nr, i) M_j[i] (so that
+ *   v_j = <u_j, eq(alpha_nr+1..n, .)>); absorb enc(u_0..u_c-1); gamma =
+ *   squeeze; u' = sum_j,i gamma^(j m + i) M_j[i] (proximity); absorb
+ *   enc(u'); t queries k_s = squeeze mod W.  Proof = "ZCP1" | u32 n | u32 nc
+ *   | u32 c | u32 t | u_j | u' | per query: enc(E_j[i][k_s]) for j, i, then the
+ *   log2 W sibling digests from the leaf up.
+ *   Verify: <u_j, eq_lo> = v_j; each queried column hashes up to the root;
+ *   its entries combine to the encodings of u_j (with eq_hi) and of u'
+ *   (with the gamma powers) at x_k. */
+typedef struct { unsigned n, nc, nr; size_t m, w, W; unsigned logW; } pcs_shape;
+
+static int pcs_shape_of(unsigned n, unsigned nc, pcs_shape *P) {
+    if (n < 1 || n > 24 || nc < 1 || nc > n) return 0;
+    P->n = n; P->nc = nc; P->nr = n - P->nc;
+    P->m = (size_t)1 << P->nr; P->w = (size_t)1 << P->nc; P->W = P->w * 4; P->logW = P->nc + 2;
+    return 1;
+}
+
+int zo_pcs_proof_size(uint32_t n, uint32_t nc, uint32_t c, uint32_t t, size_t *bytes) {
+    pcs_shape P;
+    if (!pcs_shape_of(n, nc, &P) || c < 1 || c > 65 || t < 1) return 1;
+    *bytes = 20 + 32 * (c * P.w + P.w + (size_t)t * c * P.m + (size_t)t * P.logW);
+    return 0;
+}
+
+/* E_j[i][k] for all i < m, k < W (row-major by i), canonical fe */
+static void pcs_encode(const fe *M, const pcs_shape *P, fe *E) {
+    fe *row = (fe *)malloc(P->W * sizeof(fe));
+    for (size_t i = 0; i < P->m; i++) {
+        coset_lde(M + i * P->w, P->nc, P->logW, row);          /* values at 7 w_W^k */
+        memcpy(E + i * P->W, row, P->W * sizeof(fe));
+    }
+    free(row);
+}
+
+/* leaf digests of all W columns of the c encoded matrices */
+static void pcs_leaves(fe *const *E, uint32_t c, const pcs_shape *P, uint8_t *leaves) {
+    #pragma omp parallel
+    {
+        uint8_t *buf = (uint8_t *)malloc(P->m * 32), *dg = (uint8_t *)malloc(32 * (size_t)c);
+        #pragma omp for schedule(static)
+        for (long k = 0; k < (long)P->W; k++) {
+            for (uint32_t j = 0; j < c; j++) {
+                for (size_t i = 0; i < P->m; i++) f_to_bytes(E[j][i * P->W + (size_t)k], buf + 32 * i);
+                sha256(buf, P->m * 32, dg + 32 * j);
+            }
+            sha256(dg, 32 * (size_t)c, leaves + 32 * (size_t)k);
+        }
+        free(buf); free(dg);
+    }
+}
+
+/* all levels of the tree: level 0 = leaves (W), level l has W >> l nodes */
+static uint8_t *pcs_tree(const uint8_t *leaves, const pcs_shape *P, uint8_t root[32]) {
+    uint8_t *T = (uint8_t *)malloc(2 * P->W * 32);
+    memcpy(T, leaves, P->W * 32);
+    size_t off = 0, cnt = P->W;
+    while (cnt > 1) {
+        for (size_t u = 0; u < cnt / 2; u++) sha256(T + (off + 2 * u) * 32, 64, T + (off + cnt + u) * 32);
+        off += cnt; cnt /= 2;
+    }
+    uint8_t msg[40];
+    for (int i = 0; i < 8; i++) msg[i] = (uint8_t)((uint64_t)P->W >> (8 * i));
+    memcpy(msg + 8, T + off * 32, 32);
+    sha256(msg, 40, root);
+    return T;
+}
+
+static int pcs_load(const uint8_t *const *cols, uint32_t c, const pcs_shape *P, fe **M, fe **E) {
+    if (!load_cols(cols, (int)c, P->m * P->w, M)) return 0;
+    for (uint32_t j = 0; j < c; j++) {
+        E[j] = (fe *)malloc(P->m * P->W * sizeof(fe));
+        pcs_encode(M[j], P, E[j]);
+    }
+    return 1;
+}
+
+int zo_pcs_commit(uint32_t n, uint32_t nc, uint32_t c, const uint8_t *const *cols, uint8_t *root) {
+    field_init();
+    pcs_shape P;
+    if (!pcs_shape_of(n, nc, &P) || c < 1 || c > 65) return 1;
+    fe *M[65], *E[65];
+    if (!pcs_load(cols, c, &P, M, E)) { free_cols(M, (int)c); return 1; }
+    uint8_t *leaves = (uint8_t *)malloc(P.W * 32);
+    pcs_leaves(E, c, &P, leaves);
+    free(pcs_tree(leaves, &P, root));
+    free(leaves); free_cols(M, (int)c); free_cols(E, (int)c);
+    return 0;
+}
+
+/* eq(x, b) over the variables x[0..k) for every b < 2^k, b_1 the MSB */
+static void eq_table(const fe *x, unsigned k, fe *out) {
+    for (size_t b = 0; b < ((size_t)1 << k); b++) {
+        fe e = f_one();
+        for (unsigned l = 0; l < k; l++) {
+            int bit = (int)((b >> (k - 1 - l)) & 1);
+            e = f_mul(e, bit ? x[l] : f_sub(f_one(), x[l]));
+        }
+        out[b] = e;
+    }
+}
+
+static void pcs_transcript(transcript *tr, uint32_t n, uint32_t nc, uint32_t c, uint32_t t,
+                           const uint8_t root[32], const fe *alpha, const fe *v) {
+    sha_ctx s; sha_init(&s);
+    const char *tag = "zerocheck-gb300/pcs-v1";
+    sha_update(&s, (const uint8_t *)tag, strlen(tag));
+    uint8_t b4[4], b32[32];
+    le32(b4, n); sha_update(&s, b4, 4);
+    le32(b4, nc); sha_update(&s, b4, 4);
+    le32(b4, c); sha_update(&s, b4, 4);
+    le32(b4, t); sha_update(&s, b4, 4);
+    sha_update(&s, root, 32);
+    for (uint32_t i = 0; i < n; i++) { f_to_bytes(alpha[i], b32); sha_update(&s, b32, 32); }
+    for (uint32_t j = 0; j < c; j++) { f_to_bytes(v[j], b32); sha_update(&s, b32, 32); }
+    sha_final(&s, tr->s);
+}
+
+static int load_fes(const uint8_t *b, size_t cnt, fe *out) {
+    for (size_t i = 0; i < cnt; i++) if (!f_from_bytes(b + 32 * i, &out[i])) return 0;
+    return 1;
+}
+
+static size_t query_index(transcript *tr, const pcs_shape *P) {
+    fe q = tr_squeeze(tr);
+    uint8_t b[32]; f_to_bytes(q, b);
+    uint64_t x = 0;
+    for (int i = 7; i >= 0; i--) x = (x << 8) | b[i];
+    return (size_t)(x & (P->W - 1));
+}
+
+int zo_pcs_open(uint32_t n, uint32_t nc, uint32_t c, uint32_t t, const uint8_t *const *cols,
+                const uint8_t *alpha_b, const uint8_t *values_b, uint8_t *proof, size_t cap, size_t *len) {
+    field_init();
+    size_t need;
+    if (zo_pcs_proof_size(n, nc, c, t, &need)) return 1;
+    if (cap < need) return 6;
+    pcs_shape P; pcs_shape_of(n, nc, &P);
+    fe alpha[64], v[65];
+    if (!load_fes(alpha_b, n, alpha) || !load_fes(values_b, c, v)) return 1;
+    fe *M[65], *E[65];
+    if (!pcs_load(cols, c, &P, M, E)) { free_cols(M, (int)c); return 1; }
+    uint8_t *leaves = (uint8_t *)malloc(P.W * 32), root[32];
+    pcs_leaves(E, c, &P, leaves);
+    uint8_t *tree = pcs_tree(leaves, &P, root);
+    transcript tr; pcs_transcript(&tr, n, nc, c, t, root, alpha, v);
+    memcpy(proof, "ZCP1", 4); le32(proof + 4, n); le32(proof + 8, nc); le32(proof + 12, c); le32(proof + 16, t);
+    uint8_t *pp = proof + 20;
+    /* u_j = sum_i eq(alpha_hi, i) M_j[i] */
+    fe *eqh = (fe *)malloc(P.m * sizeof(fe));
+    eq_table(alpha, P.nr, eqh);
+    uint8_t *ub = pp;
+    for (uint32_t j = 0; j < c; j++)
+        for (size_t l = 0; l < P.w; l++) {
+            fe a = f_zero();
+            for (size_t i = 0; i < P.m; i++) a = f_add(a, f_mul(eqh[i], M[j][i * P.w + l]));
+            f_to_bytes(a, pp); pp += 32;
+        }
+    tr_absorb(&tr, ub, 32 * (size_t)c * P.w);
+    const fe gamma = tr_squeeze(&tr);
+    /* u' = sum_{j,i} gamma^(j m + i) M_j[i] */
+    fe *up = (fe *)calloc(P.w, sizeof(fe));
+    fe g = f_one();
+    for (uint32_t j = 0; j < c; j++)
+        for (size_t i = 0; i < P.m; i++) {
+            for (size_t l = 0; l < P.w; l++) up[l] = f_add(up[l], f_mul(g, M[j][i * P.w + l]));
+            g = f_mul(g, gamma);
+        }
+    uint8_t *upb = pp;
+    for (size_t l = 0; l < P.w; l++) { f_to_bytes(up[l], pp); pp += 32; }
+    tr_absorb(&tr, upb, 32 * P.w);
+    for (uint32_t s = 0; s < t; s++) {
+        const size_t k = query_index(&tr, &P);
+        for (uint32_t j = 0; j < c; j++)
+            for (size_t i = 0; i < P.m; i++) { f_to_bytes(E[j][i * P.W + k], pp); pp += 32; }
+        size_t off = 0, cnt = P.W, idx = k;
+        for (unsigned lv = 0; lv < P.logW; lv++) {
+            memcpy(pp, tree + (off + (idx ^ 1)) * 32, 32); pp += 32;
+            off += cnt; cnt /= 2; idx >>= 1;
+        }
+    }
+    *len = need;
+    free(up); free(eqh); free(tree); free(leaves); free_cols(M, (int)c); free_cols(E, (int)c);
+    return 0;
+}
+
+int zo_pcs_verify(uint32_t n, uint32_t nc, uint32_t c, uint32_t t, const uint8_t *root,
+                  const uint8_t *alpha_b, const uint8_t *values_b, const uint8_t *proof, size_t len,
+                  int *accept) {
+    field_init();
+    *accept = 0;
+    size_t need;
+    if (zo_pcs_proof_size(n, nc, c, t, &need) || len != need) return 1;
+    uint8_t hdr[20]; memcpy(hdr, "ZCP1", 4);
+    le32(hdr + 4, n); le32(hdr + 8, nc); le32(hdr + 12, c); le32(hdr + 16, t);
+    if (memcmp(hdr, proof, 20) != 0) return 1;
+    pcs_shape P; pcs_shape_of(n, nc, &P);
+    fe alpha[64], v[65];
+    if (!load_fes(alpha_b, n, alpha) || !load_fes(values_b, c, v)) return 1;
+    fe *u = (fe *)malloc((size_t)(c + 1) * P.w * sizeof(fe));
+    const uint8_t *pp = proof + 20;
+    if (!load_fes(pp, (size_t)(c + 1) * P.w, u)) { free(u); return 1; }
+    int ok = 1;
+    /* v_j = <u_j, eq(alpha_lo, .)> */
+    fe *eql = (fe *)malloc(P.w * sizeof(fe)), *eqh = (fe *)malloc(P.m * sizeof(fe));
+    eq_table(alpha + P.nr, P.nc, eql);
+    eq_table(alpha, P.nr, eqh);
+    for (uint32_t j = 0; j < c; j++) {
+        fe a = f_zero();
+        for (size_t l = 0; l < P.w; l++) a = f_add(a, f_mul(u[j * P.w + l], eql[l]));
+        if (!f_eq(a, v[j])) ok = 0;
+    }
+    transcript tr; pcs_transcript(&tr, n, nc, c, t, root, alpha, v);
+    tr_absorb(&tr, pp, 32 * (size_t)c * P.w);
+    const fe gamma = tr_squeeze(&tr);
+    tr_absorb(&tr, pp + 32 * (size_t)c * P.w, 32 * P.w);
+    pp += 32 * (size_t)(c + 1) * P.w;
+    fe *gp = (fe *)malloc((size_t)c * P.m * sizeof(fe));
+    powers(gamma, (size_t)c * P.m, gp);
+    const fe wW = root_of_unity(P.logW), seven = f_from_u64(7);
+    fe *col = (fe *)malloc((size_t)c * P.m * sizeof(fe));
+    uint8_t *buf = (uint8_t *)malloc(P.m * 32), *dg = (uint8_t *)malloc(32 * (size_t)c);
+    for (uint32_t s = 0; s < t && ok; s++) {
+        const size_t k = query_index(&tr, &P);
+        if (!load_fes(pp, (size_t)c * P.m, col)) { ok = 0; break; }
+        /* hash the column up to the root */
+        for (uint32_t j = 0; j < c; j++) sha256(pp + 32 * (size_t)j * P.m, P.m * 32, dg + 32 * j);
+        uint8_t node[32], pair[64];
+        sha256(dg, 32 * (size_t)c, node);
+        pp += 32 * (size_t)c * P.m;
+        size_t idx = k;
+        for (unsigned lv = 0; lv < P.logW; lv++) {
+            if (idx & 1) { memcpy(pair, pp, 32); memcpy(pair + 32, node, 32); }
+            else { memcpy(pair, node, 32); memcpy(pair + 32, pp, 32); }
+            sha256(pair, 64, node);
+            pp += 32; idx >>= 1;
+        }
+        uint8_t msg[40], r2[32];
+        for (int i = 0; i < 8; i++) msg[i] = (uint8_t)((uint64_t)P.W >> (8 * i));
+        memcpy(msg + 8, node, 32);
+        sha256(msg, 40, r2);
+        if (memcmp(r2, root, 32) != 0) ok = 0;
+        /* encodings of u_j and u' at x_k against the column's combinations */
+        const fe xk = f_mul(seven, f_pow_u64(wW, k));
+        for (uint32_t j = 0; j <= c; j++) {
+            fe enc_u = f_zero();                            /* Horner: sum_l u[l] x_k^l */
+            for (size_t l = P.w; l-- > 0;) enc_u = f_add(f_mul(enc_u, xk), u[j * P.w + l]);
+            fe comb = f_zero();
+            if (j < c) {
+                for (size_t i = 0; i < P.m; i++) comb = f_add(comb, f_mul(eqh[i], col[j * P.m + i]));
+            } else {
+                for (size_t q = 0; q < (size_t)c * P.m; q++) comb = f_add(comb, f_mul(gp[q], col[q]));
+            }
+            if (!f_eq(enc_u, comb)) ok = 0;
+        }
+    }
+    free(u); free(eql); free(eqh); free(gp); free(col); free(buf); free(dg);
+    *accept = ok;
+    return 0;
+}
+
 /* -------------------------------------------- hooks for the pin tests -- */
 /* canonical little-endian bytes in and out */
 

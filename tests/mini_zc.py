@@ -283,3 +283,69 @@ def prove_ntt(gate, n, d, cols_int, logb=None):
         out += enc(horner(cf, z))
     out += enc(horner(q, z))
     return out, q, z
+
+
+# ------------------------------------------------- hash-based PCS ---
+
+def pcs_rows(col, nc):
+    w = 1 << nc
+    return [col[i:i + w] for i in range(0, len(col), w)]
+
+
+def rs_encode(row, logW):
+    """Values of the polynomial with coefficients `row` at 7 w_W^k, k < W (Horner)."""
+    W = 1 << logW
+    wW = omega(logW)
+    return [horner(row, 7 * pow(wW, k, R) % R) for k in range(W)]
+
+
+def pcs_tree(cols_int, nc):
+    """Leaves (per codeword position: SHA of the per-column digests) and root."""
+    logW = nc + 2
+    E_all = [[rs_encode(r, logW) for r in pcs_rows(col, nc)] for col in cols_int]
+    W = 1 << logW
+    leaves = []
+    for k in range(W):
+        dg = b"".join(sha(b"".join(enc(E[i][k]) for i in range(len(E)))) for E in E_all)
+        leaves.append(sha(dg))
+    levels = [leaves]
+    while len(levels[-1]) > 1:
+        lv = levels[-1]
+        levels.append([sha(lv[2 * u] + lv[2 * u + 1]) for u in range(len(lv) // 2)])
+    return E_all, levels, sha(W.to_bytes(8, "little") + levels[-1][0])
+
+
+def eq_tab(x):
+    k = len(x)
+    return [eq(x, bits_msb(b, k)) if k else 1 for b in range(1 << k)]
+
+
+def pcs_open(n, nc, cols_int, alpha, values, t):
+    """The PCS opening restated: u_j with eq over alpha_1..nr, gamma, u' with
+    gamma^(j m + i), t queried columns with their sibling paths."""
+    E_all, levels, root = pcs_tree(cols_int, nc)
+    nr = n - nc
+    m, w, W = 1 << nr, 1 << nc, 1 << (nc + 2)
+    st = sha(b"zerocheck-gb300/pcs-v1" + b"".join(x.to_bytes(4, "little") for x in (n, nc, len(cols_int), t))
+             + root + b"".join(enc(a) for a in alpha) + b"".join(enc(v) for v in values))
+    tr = Transcript.__new__(Transcript)
+    tr.s = st
+    eh = eq_tab(alpha[:nr])
+    rows = [pcs_rows(col, nc) for col in cols_int]
+    us = [[sum(eh[i] * rows[j][i][l] for i in range(m)) % R for l in range(w)] for j in range(len(cols_int))]
+    ub = b"".join(enc(x) for u in us for x in u)
+    tr.absorb(ub)
+    g = tr.squeeze()
+    up = [sum(pow(g, j * m + i, R) * rows[j][i][l] for j in range(len(cols_int)) for i in range(m)) % R
+          for l in range(w)]
+    upb = b"".join(enc(x) for x in up)
+    tr.absorb(upb)
+    out = b"ZCP1" + b"".join(x.to_bytes(4, "little") for x in (n, nc, len(cols_int), t)) + ub + upb
+    for _ in range(t):
+        k = tr.squeeze() & (W - 1)
+        out += b"".join(enc(enc_row[k]) for E in E_all for enc_row in E)
+        idx = k
+        for lv in levels[:-1]:
+            out += lv[idx ^ 1]
+            idx >>= 1
+    return out, root, us

@@ -456,3 +456,66 @@ def test_sumcheck_eq_verifier(gate, n, d):
         x = bytearray(pb)
         x[off] ^= 2
         assert not oracle.verify_sumcheck_eq(gate, n, d, cols, bytes(x))
+
+
+# ---- hash-based PCS (Ligero-style) around the ZeroCheck
+
+
+
+
+def _sc_point(gate, n, d, cols, root):
+    pb, r, al = oracle.prove_sumcheck(gate, n, d, cols, roots=[root] * len(cols), with_challenges=True)
+    c = len(cols)
+    vals = [pb[len(pb) - 32 * (c - j):len(pb) - 32 * (c - j) + 32] for j in range(c)]
+    return pb, al, vals
+
+
+@pytest.mark.parametrize("gate,n,nc,d", [(g, n, nc, d) for g, n, nc, d in
+                                         [(1, 3, 2, 3), (2, 4, 2, 2), (2, 5, 3, 3), (witness.gate_sum(1), 4, 4, 2)]])
+def test_pcs_matches_restatement(gate, n, nc, d):
+    """Commitment root and opening bytes (u_j, u', queried columns, Merkle
+    paths) equal the big-integer restatement; the opening's u_j reproduce the
+    columns' MLE values at alpha (Sec. 3.3 interpolation form)."""
+    cols = witness.generate(gate, n, d, 1200 + n)
+    ci = _cols_int(cols)
+    root = oracle.pcs_commit(n, cols, nc=nc)
+    pb, al, vals = _sc_point(gate, n, d, cols, root)
+    t = 5
+    pr = oracle.pcs_open(n, cols, al, vals, t, nc=nc)
+    alpha = [int.from_bytes(a, "little") for a in al]
+    ref, rroot, us = mz.pcs_open(n, nc, ci, alpha, [int.from_bytes(v, "little") for v in vals], t)
+    assert root == rroot
+    assert pr == ref
+    el = mz.eq_tab(alpha[n - nc:])
+    for j, col in enumerate(ci):
+        mle = mz.mle(col, alpha)
+        assert mle == int.from_bytes(vals[j], "little")
+        assert sum(u * e for u, e in zip(us[j], el)) % R == mle
+    assert oracle.pcs_verify(n, len(cols), t, root, al, vals, pr, nc=nc)
+
+
+def test_pcs_rejections():
+    gate, n, nc, d, t = 2, 6, 3, 3, 24
+    cols = witness.generate(gate, n, d, 1300)
+    root = oracle.pcs_commit(n, cols, nc=nc)
+    pb, al, vals = _sc_point(gate, n, d, cols, root)
+    pr = oracle.pcs_open(n, cols, al, vals, t, nc=nc)
+    c = len(cols)
+    assert oracle.pcs_verify(n, c, t, root, al, vals, pr, nc=nc)
+    w, m = 1 << nc, 1 << (n - nc)
+    off_u, off_up, off_q = 20, 20 + 32 * c * w, 20 + 32 * (c + 1) * w
+    for off in (off_u + 7, off_up + 40, off_q + 3, off_q + 32 * c * m + 5, len(pr) - 1):
+        x = bytearray(pr)
+        x[off] ^= 1
+        assert not oracle.pcs_verify(n, c, t, root, al, vals, bytes(x), nc=nc), off
+    v2 = list(vals)
+    v2[1] = bytes([vals[1][0] ^ 1]) + vals[1][1:]
+    assert not oracle.pcs_verify(n, c, t, root, al, v2, pr, nc=nc)
+    a2 = list(al)
+    a2[0] = bytes([al[0][0] ^ 1]) + al[0][1:]
+    assert not oracle.pcs_verify(n, c, t, root, a2, vals, pr, nc=nc)
+    other = witness.generate(gate, n, d, 1301)
+    assert not oracle.pcs_verify(n, c, t, oracle.pcs_commit(n, other, nc=nc), al, vals, pr, nc=nc)
+    # the committed matrix of another witness cannot be opened to this one's values
+    pr_o = oracle.pcs_open(n, other, al, vals, t, nc=nc)
+    assert not oracle.pcs_verify(n, c, t, oracle.pcs_commit(n, other, nc=nc), al, vals, pr_o, nc=nc)
