@@ -277,6 +277,72 @@ zc_status zc_prove_sumcheck_static(const zc_params* params, const void* const* c
                                    const uint8_t (*col_roots)[32], void* cuda_stream,
                                    uint8_t* proof, size_t cap, size_t* len);
 
+/* ------------------------------------------ commitment around it --
+ * Stages (1) and (3) of the prover workflow (Sec. 3.1) around the ZeroCheck,
+ * with the lightweight hash-based commitment the paper points to (Ligero):
+ * commit to the c witness columns before proving, then open them at the
+ * point alpha the SumCheck form ends in, so that a verifier checks the
+ * proof's final values v_j against the commitment instead of reading the
+ * columns.  Layout: each column (an MLE table of N = 2^n values, x_1 the
+ * most significant index bit) is an m x w matrix, w = 2^nc, m = N / w.
+ * Commit: every row is Reed-Solomon encoded at rate 1/4 (the values of the
+ * row polynomial at the W = 4w points 7 w_W^k); leaf k = SHA-256 of the
+ * SHA-256 digests of position k of each encoded column (its m entries);
+ * root = SHA-256(u64 W | top of the binary Merkle tree of the W leaves).
+ * Open: u_j = sum_i eq(alpha_1..nr, i) row_i of column j, a random
+ * combination u' of all rows (proximity test), and t queried positions with
+ * their encoded columns and Merkle paths; transcript SHA-256(
+ * "zerocheck-gb300/pcs-v1" | u32 n | u32 nc | u32 c | u32 t | root |
+ * enc(alpha_i) | enc(v_j)), absorb/squeeze as above, query k = low 64 bits
+ * of a challenge mod W.  Proof "ZCP1" | u32 n | u32 nc | u32 c | u32 t |
+ * u_j | u' | per query: the c m entries, then log2 W sibling digests from
+ * the leaf up.  With the ZeroCheck, the caller passes the PCS root as every
+ * column's root (col_roots[j] = root), which binds the commitment into the
+ * ZeroCheck transcript.  Soundness of a query set: each query catches a
+ * matrix far from the code with probability >= 3/8 (t = 189 for 2^-128). */
+typedef struct {
+  uint32_t n;   /* columns of 2^n values, 1 <= n <= 24 */
+  uint32_t nc;  /* rows of 2^nc values, 1 <= nc <= min(n, 12); 0: min(n, 12) */
+  uint32_t c;   /* columns, 1..65 */
+  uint32_t t;   /* queried positions of an opening, >= 1 */
+} zc_pcs_params;
+
+typedef struct zc_pcs zc_pcs;
+
+/* Opening proof size: 20 + 32 (c w + w + t c m + t (nc + 2)). */
+zc_status zc_pcs_proof_size(const zc_pcs_params* params, size_t* bytes);
+
+/* Encode and commit to the c columns (host or device, canonical).  The
+ * handle keeps the encoded columns (4 c N 32 bytes of device memory) and,
+ * for device columns, the caller's pointers, whose contents must not change
+ * until the handle is destroyed.  root: 32 bytes out.  Synchronous. */
+zc_status zc_pcs_commit(zc_ctx* ctx, const zc_pcs_params* params, const void* const* cols,
+                        int cols_on_device, void* cuda_stream, zc_pcs** out, uint8_t root[32]);
+
+/* Opening of every column at alpha (n canonical elements) with the claimed
+ * values (c canonical elements).  proof: host memory of cap bytes, *len the
+ * size.  Synchronous. */
+zc_status zc_pcs_open(zc_pcs* pcs, const uint8_t (*alpha)[32], const uint8_t (*values)[32],
+                      void* cuda_stream, uint8_t* proof, size_t cap, size_t* len);
+
+/* Host verifier of an opening against root: *accept = 1 iff every check
+ * passes; ZC_ERR_ARG for a malformed proof. */
+zc_status zc_pcs_verify(const zc_pcs_params* params, const uint8_t root[32], const uint8_t (*alpha)[32],
+                        const uint8_t (*values)[32], const uint8_t* proof, size_t len, int* accept);
+
+void zc_pcs_destroy(zc_pcs* pcs);
+
+/* The point a SumCheck-form proof ends in: replays its transcript with the
+ * given column roots (host, no columns needed) and writes alpha (n
+ * canonical elements) and the proof's final values (c elements); *rounds_ok
+ * = 1 iff every round's check and the final check gate(v) eq(r, alpha) =
+ * claim pass (Sec. 3.3, 3.4).  With zc_pcs_verify on (alpha, values) this
+ * verifies a ZeroCheck without the columns.  form: ZC_FORM_SUMCHECK or
+ * ZC_FORM_SUMCHECK_EQ. */
+zc_status zc_sumcheck_point(const zc_params* params, zc_form form, const uint8_t (*col_roots)[32],
+                            const uint8_t* proof, size_t len, uint8_t (*alpha_out)[32],
+                            uint8_t (*values_out)[32], int* rounds_ok);
+
 /* ----------------------------------------------------------- serving --
  * A request loop over a list of timed requests (the paper proves one
  * instance at a time; serving is a deployment mode of the same arithmetic).

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libzc.so")
-SOURCES = ["zc_api.cu", "zc_sumcheck.cu", "zc_merkle.cu", "zc_ntt.cu", "zc_batch.cu", "zc_serve.cu"]
+SOURCES = ["zc_api.cu", "zc_sumcheck.cu", "zc_merkle.cu", "zc_ntt.cu", "zc_batch.cu", "zc_serve.cu", "zc_pcs.cu"]
 HEADERS = ["zc_field.cuh", "zc_sha256.cuh", "zc_internal.cuh", "zc_transcript.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -134,6 +134,15 @@ fr h_pow(const fr& a, uint64_t e, const DevConst& C) {
   return acc;
 }
 
+fr h_root_of_unity(uint32_t logn, const DevConst& C) {
+  // 7^((r-1) / 2^32) generates the 2^32-element subgroup; square down to 2^logn
+  uint32_t sh[8];
+  for (int i = 0; i < 8; i++) sh[i] = i < 7 ? p_limb(i + 1) : 0;
+  fr w = h_pow_limbs(h_from_u64(7), sh, C);
+  for (uint32_t i = logn; i < 32; i++) w = h_canon_mul(w, w, C);
+  return w;
+}
+
 fr h_inv(const fr& a, const DevConst& C) {
   uint32_t e[8];  // r - 2 (r's low limb is 1, so the subtraction borrows)
   uint64_t br = 2;
@@ -389,9 +398,13 @@ static fr host_lagrange(const fr* y, int m, const fr& x, const DevConst& C) {
 // c_i l_i H_i (check c_i ((1 - r_i) H(0) + r_i H(1)) = claim, then
 // c_{i+1} = c_i l_i(alpha), claim <- c_{i+1} H(alpha)).  Both end with
 // claim = gate(v) eq(r, alpha) and v_j = MLE_j(alpha).
-static zc_status verify_sumcheck(const zc_params* p, const void* const* cols,
-                                 const uint8_t (*roots)[32], const uint8_t* proof, size_t len,
-                                 int* accept, const DevConst& C, bool v2) {
+// Replay a SumCheck proof: the transcript (column roots given, or computed
+// from host columns), every round's check and the final check of the claim
+// against gate(v) eq(r, alpha).  Out: alpha (canonical), v (the final
+// values), ok.  ZC_ERR_ARG if the proof is malformed.
+static zc_status sumcheck_replay(const zc_params* p, const void* const* cols, const uint8_t (*roots)[32],
+                                 const uint8_t* proof, size_t len, const DevConst& C, bool v2,
+                                 std::vector<fr>& al, std::vector<fr>& v, bool& ok) {
   const uint32_t n = p->n, d = p->d, gate = p->gate;
   const int c = gate_ncols(gate, d);
   const uint64_t N = 1ull << n;
@@ -409,9 +422,10 @@ static zc_status verify_sumcheck(const zc_params* p, const void* const* cols,
     else if (!host_root(static_cast<const uint8_t*>(cols[j]), N, rt)) return ZC_ERR_ARG;
     tr.absorb(rt, 32);
   }
-  std::vector<fr> r(n), al(n);
+  std::vector<fr> r(n);
+  al.assign(n, fr_zero());
   for (uint32_t i = 0; i < n; i++) r[i] = tr.squeeze();
-  bool ok = true;
+  ok = true;
   fr claim = fr_zero(), ci = h_from_u64(1);
   const fr one1 = h_from_u64(1);
   const uint8_t* pp = proof + 16;
@@ -436,7 +450,7 @@ static zc_status verify_sumcheck(const zc_params* p, const void* const* cols,
       claim = h_canon_mul(ci, claim, C);
     }
   }
-  std::vector<fr> v(c);
+  v.assign(c, fr_zero());
   for (int j = 0; j < c; j++)
     if (!h_from_bytes(pp + 32 * j, &v[j])) return ZC_ERR_ARG;
   fr eqra = h_from_u64(1);
@@ -447,6 +461,20 @@ static zc_status verify_sumcheck(const zc_params* p, const void* const* cols,
     eqra = h_canon_mul(eqra, e, C);
   }
   if (!fr_equal(claim, h_canon_mul(host_gate(gate, d, v.data(), C), eqra, C))) ok = false;
+  return ZC_OK;
+}
+
+static zc_status verify_sumcheck(const zc_params* p, const void* const* cols,
+                                 const uint8_t (*roots)[32], const uint8_t* proof, size_t len,
+                                 int* accept, const DevConst& C, bool v2) {
+  const uint32_t n = p->n, d = p->d, gate = p->gate;
+  const int c = gate_ncols(gate, d);
+  const uint64_t N = 1ull << n;
+  std::vector<fr> al, v;
+  bool ok = true;
+  zc_status rs = sumcheck_replay(p, cols, roots, proof, len, C, v2, al, v, ok);
+  if (rs != ZC_OK) return rs;
+  (void)gate;
   // v_j = sum_b col_j[b] eq_alpha(b): eq table at level 1, columns canonical
   std::vector<fr> E(1, C.one);
   E.reserve(N);
@@ -612,7 +640,7 @@ static bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-static const DevConst& host_constants() {
+const DevConst& host_constants() {
   static DevConst C;
   static std::once_flag once;
   std::call_once(once, [] {
@@ -805,6 +833,25 @@ zc_status zc_verify(const zc_params* params, zc_form form, const void* const* co
   if (form == ZC_FORM_SUMCHECK || form == ZC_FORM_SUMCHECK_EQ)
     return verify_sumcheck(params, cols, col_roots, proof, len, accept, C, form == ZC_FORM_SUMCHECK_EQ);
   return verify_ntt(params, cols, col_roots, proof, len, q, accept, C);
+}
+
+zc_status zc_sumcheck_point(const zc_params* params, zc_form form, const uint8_t (*col_roots)[32],
+                            const uint8_t* proof, size_t len, uint8_t (*alpha_out)[32],
+                            uint8_t (*values_out)[32], int* rounds_ok) {
+  if (!col_roots || !proof || !alpha_out || !values_out || !rounds_ok) return ZC_ERR_ARG;
+  *rounds_ok = 0;
+  if (form != ZC_FORM_SUMCHECK && form != ZC_FORM_SUMCHECK_EQ) return ZC_ERR_ARG;
+  zc_status s = check_params(nullptr, params, form);
+  if (s != ZC_OK) return s;
+  std::vector<fr> al, v;
+  bool ok = false;
+  s = sumcheck_replay(params, nullptr, col_roots, proof, len, host_constants(), form == ZC_FORM_SUMCHECK_EQ,
+                      al, v, ok);
+  if (s != ZC_OK) return s;
+  for (uint32_t i = 0; i < params->n; i++) h_to_bytes(al[i], alpha_out[i]);
+  for (size_t j = 0; j < v.size(); j++) h_to_bytes(v[j], values_out[j]);
+  *rounds_ok = ok ? 1 : 0;
+  return ZC_OK;
 }
 
 zc_status zc_roots(zc_ctx* ctx, const zc_params* params, const void* const* cols,

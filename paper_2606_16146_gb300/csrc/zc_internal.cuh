@@ -173,6 +173,8 @@ fr h_canon_mul(const fr& a, const fr& b, const DevConst& C);  // a*b mod r, cano
 fr h_pow(const fr& a, uint64_t e, const DevConst& C);          // canonical
 fr h_inv(const fr& a, const DevConst& C);                      // canonical, a != 0
 fr h_from_u64(uint64_t x);
+fr h_root_of_unity(uint32_t logn, const DevConst& C);        // canonical generator of the 2^logn subgroup
+const DevConst& host_constants();                            // the field constants, built once
 void h_to_bytes(const fr& a, uint8_t* out);
 bool h_from_bytes(const uint8_t* in, fr* out);
 void transcript_init_words(uint32_t S[8], uint32_t form, uint32_t gate, uint32_t n, uint32_t d,
@@ -198,6 +200,14 @@ bool ntt_domain(uint32_t n, uint32_t d, uint32_t log_blowup, NttDomain* D);
 zc_status launch_roots(zc_ctx* ctx, const fr* const* dcols, int c, uint64_t L, uint8_t* droots,
                        cudaStream_t st);
 size_t root_scratch_bytes(int c, uint64_t L);
+// hash-based commitment: rate-1/4 Reed-Solomon encoding of the 2^nr rows of
+// 2^nc entries of each column into enc[j][k m + i] (W = 2^(nc+2)), and the
+// column digests, leaves and tree levels (2W - 1 nodes of 8 words, leaves
+// first) of the encoded columns
+zc_status pcs_encode(zc_ctx* ctx, const fr* const* cols, int c, uint32_t nr, uint32_t nc, fr* const* enc,
+                     fr* tab, cudaStream_t st);
+zc_status pcs_hash_tree(zc_ctx* ctx, const fr* const* enc, int c, uint64_t m, uint64_t W, uint32_t* dig,
+                        uint32_t* tree, cudaStream_t st);
 void static_constants(DevConst* C, std::vector<fr>* tabs);
 
 // v2: the eq-factored form (rounds carry H_i(0..d), transcript v2)

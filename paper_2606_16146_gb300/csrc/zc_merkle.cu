@@ -13,6 +13,7 @@
 // first seven levels (a ragged last CTA's node arrives at level 7 unchanged,
 // as the odd last node of every level above it).
 #include "zc_internal.cuh"
+#include "zc_transcript.cuh"
 
 namespace zc {
 
@@ -212,6 +213,75 @@ size_t root_scratch_bytes(int c, uint64_t L) {
   uint64_t nl = (L + per - 1) / per;
   uint64_t ctas = (nl + kLeafCta - 1) / kLeafCta;
   return 2 * ((size_t)c * ctas * 32 + 256);
+}
+
+// ---- hash-based commitment (zc_pcs.cu): digest of codeword position k of
+// column j = SHA-256 of its m canonical entries enc[j][k m .. k m + m);
+// leaf k = SHA-256 of the c digests of position k; tree levels above.
+
+struct PcsDigestArgs {
+  const fr* enc[kMaxCols];
+  uint32_t c;
+  uint64_t m, W;
+  uint32_t* dig;      // [k][j][8] words
+};
+
+__global__ void __launch_bounds__(128) k_pcs_digests(PcsDigestArgs A) {
+  const uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= A.W * A.c) return;
+  const uint64_t k = e / A.c;
+  const uint32_t j = (uint32_t)(e - k * A.c);
+  uint32_t h[8];
+  sha256_device_mem(reinterpret_cast<const uint8_t*>(A.enc[j] + k * A.m), (uint32_t)(A.m * 32), h);
+#pragma unroll
+  for (int i = 0; i < 8; i++) A.dig[8 * e + i] = h[i];
+}
+
+struct PcsLevelArgs {
+  const uint32_t* in;  // nodes of the level below (8 words each), or the digests
+  uint32_t* out;
+  uint64_t count;      // nodes written
+  uint32_t words;      // words hashed per node (16 for a pair, 8 c for a leaf)
+};
+
+__global__ void k_pcs_level(PcsLevelArgs A) {
+  const uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= A.count) return;
+  uint32_t h[8];
+  sha256_words(A.in + (uint64_t)A.words * u, A.words, h);
+#pragma unroll
+  for (int i = 0; i < 8; i++) A.out[8 * u + i] = h[i];
+}
+
+zc_status pcs_hash_tree(zc_ctx* ctx, const fr* const* enc, int c, uint64_t m, uint64_t W, uint32_t* dig,
+                        uint32_t* tree, cudaStream_t st) {
+  PcsDigestArgs da{};
+  for (int j = 0; j < c; j++) da.enc[j] = enc[j];
+  da.c = (uint32_t)c;
+  da.m = m;
+  da.W = W;
+  da.dig = dig;
+  const uint64_t nd = W * (uint64_t)c;
+  k_pcs_digests<<<(unsigned)((nd + 127) / 128), 128, 0, st>>>(da);
+  ctx->launches++;
+  PcsLevelArgs la{};
+  la.in = dig;
+  la.out = tree;
+  la.count = W;
+  la.words = 8u * (uint32_t)c;
+  k_pcs_level<<<(unsigned)((W + 127) / 128), 128, 0, st>>>(la);
+  ctx->launches++;
+  uint64_t off = 0;
+  for (uint64_t cnt = W; cnt > 1; cnt /= 2) {
+    la.in = tree + 8 * off;
+    la.out = tree + 8 * (off + cnt);
+    la.count = cnt / 2;
+    la.words = 16;
+    k_pcs_level<<<(unsigned)((cnt / 2 + 127) / 128), 128, 0, st>>>(la);
+    ctx->launches++;
+    off += cnt;
+  }
+  return cudaGetLastError() == cudaSuccess ? ZC_OK : ZC_ERR_CUDA;
 }
 
 }  // namespace zc

@@ -985,6 +985,67 @@ static bool step_tables(zc_ctx* user, zc_ctx::NttSizeTables* e, const NttTables*
   return true;
 }
 
+// ---- Reed-Solomon row encoding for the hash-based commitment (zc_pcs.cu):
+// row i of column j (w = 2^nc coefficients) evaluated at the W = 4w points
+// 7 w_W^k, written to enc[j][k m + i].  Slice s (k = s + 4 k') is one pass
+// of w-point transforms over the m rows with the factor (7 w_W^s)^l applied
+// on load; canonical columns in, canonical codewords out.
+
+struct PcsTabArgs {
+  fr* tab;            // [s w + l] = (7 w_W^s)^l, level 1
+  uint32_t nc;        // w = 2^nc
+  uint32_t shiftW;    // 30 - log2 W
+  NttTables T;
+};
+
+__global__ void k_pcs_tables(PcsTabArgs A) {
+  const uint32_t w = 1u << A.nc, total = 4 * w;
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const uint32_t s = e >> A.nc, l = e & (w - 1);
+    const fr p7 = fr_mul(ld_fr(A.T.p7_hi + (l >> kLoBits)), ld_fr(A.T.p7_lo + (l & kLoMask)));  // 7^l
+    const uint32_t ex = (uint32_t)((((uint64_t)s * l) << A.shiftW) & ((1ull << kLog30) - 1));
+    st_fr(A.tab + e, fr_mul(p7, root_pow(A.T.wf_lo, A.T.wf_hi, ex)));
+  }
+}
+
+zc_status pcs_encode(zc_ctx* ctx, const fr* const* cols, int c, uint32_t nr, uint32_t nc, fr* const* enc,
+                     fr* tab, cudaStream_t st) {
+  if (nc < 1 || nc > 12 || c < 1 || c > kMaxCols) {
+    ctx->err = "pcs: rows of 2 .. 2^12 elements";
+    return ZC_ERR_UNSUPPORTED;
+  }
+  ensure_pass_attributes(ctx->device);
+  NttTables* T = nullptr;
+  zc_status s0 = ensure_tables(ctx, st, &T);
+  if (s0 != ZC_OK) return s0;
+  const uint64_t w = 1ull << nc, m = 1ull << nr;
+  PcsTabArgs ta{};
+  ta.tab = tab;
+  ta.nc = nc;
+  ta.shiftW = kLog30 - (nc + 2);
+  ta.T = *T;
+  k_pcs_tables<<<(unsigned)std::min<uint64_t>((4 * w + 255) / 256, 1024), 256, 0, st>>>(ta);
+  ctx->launches++;
+  ctx->cur_n = nc;
+  for (uint32_t sl = 0; sl < 4; sl++) {
+    NttPassArgs a;
+    pass_defaults(a);
+    for (int j = 0; j < c; j++) {
+      a.in[j] = cols[j];
+      a.out[j] = enc[j] + sl * m;     // position k = sl + 4 k'
+    }
+    a.logL = nc;
+    a.in_bs_lo = w; a.in_ts = 1;      // row b, coefficient t
+    a.out_bs_lo = 1; a.out_ts = 4 * m;
+    a.dft = T->dft_fwd;
+    a.pre = PRE_TAB; a.pre_tab = tab + sl * w;
+    a.pre_kb = 0; a.pre_kt = 1;
+    zc_status rs = run_pass(ctx, st, a, c, m);
+    if (rs != ZC_OK) return rs;
+  }
+  return cudaGetLastError() == cudaSuccess ? ZC_OK : ZC_ERR_CUDA;
+}
+
 zc_status ntt_prepare(zc_ctx* ctx, const zc_params* p, cudaStream_t st) {
   ensure_pass_attributes(ctx->device);
   NttTables* T = nullptr;

@@ -62,6 +62,10 @@ class zc_result(ctypes.Structure):
                 ("waited_for_memory", ctypes.c_uint32), ("status", ctypes.c_int)]
 
 
+class zc_pcs_params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("nc", ctypes.c_uint32), ("c", ctypes.c_uint32), ("t", ctypes.c_uint32)]
+
+
 class zc_serve_opts(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_uint32), ("hbm_budget_bytes", ctypes.c_uint64),
                 ("in_order", ctypes.c_uint32), ("timeout_s", ctypes.c_double),
@@ -120,6 +124,18 @@ def lib(path: str | None = None):
         L.zc_batch_destroy.restype = None
         L.zc_prove_sumcheck_static.argtypes = [P(zc_params), vp, vp, vp, u8p, sz, P(sz)]
         L.zc_prove_sumcheck_static.restype = ctypes.c_int
+        L.zc_pcs_proof_size.argtypes = [P(zc_pcs_params), P(sz)]
+        L.zc_pcs_proof_size.restype = ctypes.c_int
+        L.zc_pcs_commit.argtypes = [vp, P(zc_pcs_params), vp, ctypes.c_int, vp, P(vp), u8p]
+        L.zc_pcs_commit.restype = ctypes.c_int
+        L.zc_pcs_open.argtypes = [vp, vp, vp, vp, u8p, sz, P(sz)]
+        L.zc_pcs_open.restype = ctypes.c_int
+        L.zc_pcs_verify.argtypes = [P(zc_pcs_params), u8p, vp, vp, u8p, sz, P(ctypes.c_int)]
+        L.zc_pcs_verify.restype = ctypes.c_int
+        L.zc_pcs_destroy.argtypes = [vp]
+        L.zc_pcs_destroy.restype = None
+        L.zc_sumcheck_point.argtypes = [P(zc_params), ctypes.c_int, vp, u8p, sz, vp, vp, P(ctypes.c_int)]
+        L.zc_sumcheck_point.restype = ctypes.c_int
         L.zc_last_error.argtypes = [vp]
         L.zc_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -259,6 +275,10 @@ class Context:
                                 q_dev)
         self._check(st, "zc_prove_ntt")
         return out, q
+
+    def pcs_commit(self, n, cols, t, nc=0, stream=None) -> "PcsCommitment":
+        """Commit to the columns with the hash-based PCS (zc_pcs_commit)."""
+        return PcsCommitment(self, n, cols, t, nc, stream)
 
     def roots(self, gate, n, d, cols, stream=None) -> list[bytes]:
         p = zc_params(gate, n, d, 0)
@@ -419,3 +439,97 @@ def prove_sumcheck_static(gate, n, d, cols, proof_out, roots=None, stream=None) 
                                         _addr(proof_out), proof_out.numel(), ctypes.byref(ln))
     if st != ZC_OK:
         raise ZCError(st, "zc_prove_sumcheck_static")
+
+
+# ---------------------------------------------------- commitment around it
+
+def pcs_proof_size(n: int, c: int, t: int, nc: int = 0) -> int:
+    out = ctypes.c_size_t()
+    p = zc_pcs_params(n, nc, c, t)
+    st = lib().zc_pcs_proof_size(ctypes.byref(p), ctypes.byref(out))
+    if st != ZC_OK:
+        raise ZCError(st, "zc_pcs_proof_size")
+    return int(out.value)
+
+
+def _bytes_array(items, count) -> np.ndarray:
+    b = b"".join(bytes(x) for x in items)
+    if len(b) != 32 * count:
+        raise ValueError(f"expected {count} elements of 32 bytes")
+    return np.frombuffer(b, dtype=np.uint8).copy()
+
+
+class PcsCommitment:
+    """zc_pcs handle: the encoded columns on the device and the Merkle tree."""
+
+    def __init__(self, ctx: "Context", n: int, cols, t: int, nc: int = 0, stream=None):
+        self.ctx = ctx
+        self.n, self.c, self.t, self.nc = n, len(cols), t, nc
+        P, on_dev = ctx._cols(cols)
+        self._keep = (P, cols)
+        p = zc_pcs_params(n, nc, self.c, t)
+        h = ctypes.c_void_p()
+        root = np.zeros(32, np.uint8)
+        st = lib().zc_pcs_commit(ctx.h, ctypes.byref(p), P.p, on_dev, _stream_ptr(stream), ctypes.byref(h),
+                                 root.ctypes.data)
+        ctx._check(st, "zc_pcs_commit")
+        self.h = h
+        self.root = root.tobytes()
+
+    def open(self, alpha, values, stream=None) -> bytes:
+        a = _bytes_array(alpha, self.n)
+        v = _bytes_array(values, self.c)
+        cap = pcs_proof_size(self.n, self.c, self.t, self.nc)
+        out = np.zeros(cap, np.uint8)
+        ln = ctypes.c_size_t()
+        st = lib().zc_pcs_open(self.h, a.ctypes.data, v.ctypes.data, _stream_ptr(stream),
+                               out.ctypes.data, cap, ctypes.byref(ln))
+        self.ctx._check(st, "zc_pcs_open")
+        return out.tobytes()[: ln.value]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().zc_pcs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pcs_verify(n: int, c: int, t: int, root: bytes, alpha, values, proof, nc: int = 0) -> bool:
+    """Host verifier of an opening (no GPU needed)."""
+    p = zc_pcs_params(n, nc, c, t)
+    a = _bytes_array(alpha, n)
+    v = _bytes_array(values, c)
+    r = np.frombuffer(bytes(root), dtype=np.uint8).copy()
+    pr = _host_array(proof)
+    acc = ctypes.c_int(0)
+    st = lib().zc_pcs_verify(ctypes.byref(p), r.ctypes.data, a.ctypes.data,
+                             v.ctypes.data, pr.ctypes.data, pr.size,
+                             ctypes.byref(acc))
+    if st == ZC_ERR_ARG:
+        return False
+    if st != ZC_OK:
+        raise ZCError(st, "zc_pcs_verify")
+    return bool(acc.value)
+
+
+def sumcheck_point(gate, n, d, form, roots, proof):
+    """(alpha, values, rounds_ok) of a SumCheck-form proof, replayed on the host."""
+    p = zc_params(gate, n, d, 0)
+    c = len(roots)
+    rb = _bytes_array(roots, c)
+    pr = _host_array(proof)
+    a = np.zeros(32 * n, np.uint8)
+    v = np.zeros(32 * c, np.uint8)
+    ok = ctypes.c_int(0)
+    st = lib().zc_sumcheck_point(ctypes.byref(p), form, rb.ctypes.data,
+                                 pr.ctypes.data, pr.size, a.ctypes.data,
+                                 v.ctypes.data, ctypes.byref(ok))
+    if st != ZC_OK:
+        raise ZCError(st, "zc_sumcheck_point")
+    return ([a[32 * i:32 * i + 32].tobytes() for i in range(n)],
+            [v[32 * j:32 * j + 32].tobytes() for j in range(c)], bool(ok.value))

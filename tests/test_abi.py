@@ -111,3 +111,32 @@ def test_host_verifier_eq_factored(gate, n, d):
     x = bytearray(pb)
     x[16 + 32 * (d + 1) + 1] ^= 8
     assert not zc.verify(gate, n, d, zc.ZC_FORM_SUMCHECK_EQ, cols, bytes(x))
+
+
+@pytest.mark.parametrize("n,nc,gate,d", [(4, 2, 1, 3), (5, 5, 2, 3), (6, 3, 2, 2)])
+def test_host_pcs_verifier_and_sumcheck_point(n, nc, gate, d):
+    """The library's host side of the commitment: zc_sumcheck_point replays
+    an oracle SumCheck proof (PCS root as every column root) to the oracle's
+    alpha and final values, and zc_pcs_verify accepts the oracle's opening
+    there and rejects a flipped byte or a wrong value."""
+    cols = witness.generate(gate, n, d, 130 + n)
+    c, t = len(cols), 7
+    root = oracle.pcs_commit(n, cols, nc=nc)
+    for form in (zc.ZC_FORM_SUMCHECK, zc.ZC_FORM_SUMCHECK_EQ):
+        prove = oracle.prove_sumcheck if form == zc.ZC_FORM_SUMCHECK else oracle.prove_sumcheck_eq
+        pb, _, al = prove(gate, n, d, cols, roots=[root] * c, with_challenges=True)
+        alpha, vals, ok = zc.sumcheck_point(gate, n, d, form, [root] * c, pb)
+        assert ok and alpha == al
+        assert vals == [pb[len(pb) - 32 * (c - j):len(pb) - 32 * (c - j) + 32] for j in range(c)]
+        pr = oracle.pcs_open(n, cols, alpha, vals, t, nc=nc)
+        assert len(pr) == zc.pcs_proof_size(n, c, t, nc)
+        assert zc.pcs_verify(n, c, t, root, alpha, vals, pr, nc)
+        x = bytearray(pr)
+        x[len(pr) // 2] ^= 1
+        assert not zc.pcs_verify(n, c, t, root, alpha, vals, bytes(x), nc)
+        v2 = list(vals)
+        v2[0] = bytes([vals[0][0] ^ 1]) + vals[0][1:]
+        assert not zc.pcs_verify(n, c, t, root, alpha, v2, pr, nc)
+    bad = bytearray(pb)
+    bad[20] ^= 1
+    assert not zc.sumcheck_point(gate, n, d, zc.ZC_FORM_SUMCHECK_EQ, [root] * c, bytes(bad))[2]
