@@ -588,6 +588,72 @@ def run_family(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_pcs(args, world, rank, local):
+    """The hash-based commitment around the ZeroCheck (stages (1) and (3) of
+    the prover workflow): commit to the Plonk n = 22 witness, prove the
+    SumCheck form with the commitment as every column root, recover the
+    point from the proof, open there, verify on the host."""
+    import torch
+    from paper_2606_16146_gb300 import witness, zc
+    torch.cuda.set_device(local)
+    device_info = set_alu_peak(local)
+    ctx = zc.Context(local, max_n=24, max_d=8)
+    n, t = N_LOG, args.pcs_queries
+    cols = witness.generate(GATE, n, DEG, 1000 + n)
+    dcols = [torch.from_numpy(c).cuda() for c in cols]
+    c = len(cols)
+    stream = torch.cuda.Stream()
+    K, W = max(1, args.steps), max(3, args.warmup)
+
+    def timed(fn, reps):
+        ts, out = [], None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = fn()
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e3)
+        return float(np.median(ts)), out
+
+    for _ in range(W):
+        ctx.pcs_commit(n, dcols, t, stream=stream).close()
+    cms = []
+    for _ in range(K):
+        ms, com = timed(lambda: ctx.pcs_commit(n, dcols, t, stream=stream), 1)
+        cms.append(ms)
+        if len(cms) < K:
+            com.close()
+    commit_ms = float(np.median(cms))
+    roots = [com.root] * c
+    proof = torch.zeros(zc.proof_size(GATE, n, DEG, 1), dtype=torch.uint8, device="cuda")
+    sc_ms, _ = timed(lambda: ctx.prove_sumcheck(GATE, n, DEG, dcols, roots=roots, stream=stream,
+                                                proof_out=proof), K)
+    pb = proof.cpu().numpy().tobytes()
+    pt_ms, (alpha, vals, ok) = timed(lambda: zc.sumcheck_point(GATE, n, DEG, 1, roots, pb), 1)
+    open_ms, pr = timed(lambda: com.open(alpha, vals, stream=stream), K)
+    t0 = time.perf_counter()
+    accept = zc.pcs_verify(n, c, t, com.root, alpha, vals, pr)
+    verify_ms = (time.perf_counter() - t0) * 1e3
+    com.close()
+    N = 1 << n
+    config = {"workload": f"hash-based commitment around the ZeroCheck: Plonk n={n} (8 columns), rate-1/4 "
+                          f"Reed-Solomon rows of 2^{min(n, 12)}, {t} queries; commit, SumCheck proof with "
+                          "the commitment as every column root, point replay, opening, host verification",
+              "n": n, "columns": c, "queries": t, "parallelism": f"replicas x{world}"}
+    line = _base_line(args, world, commit_ms + sc_ms + open_ms, "ms", False, config)
+    line["value_is"] = "commit + SumCheck proof + opening (device work, host-timed with synchronisation)"
+    line["phases_ms"] = {"commit": commit_ms, "sumcheck": sc_ms, "point_replay_host": pt_ms, "open": open_ms,
+                         "verify_host": verify_ms}
+    line["sizes_bytes"] = {"columns": c * N * 32, "encoded": 4 * c * N * 32, "opening_proof": len(pr),
+                           "sumcheck_proof": len(pb)}
+    line["verified"] = bool(accept and ok)
+    line["device"] = device_info
+    line["e2e"] = None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_served(args, world, rank, local):
     """Poisson request loop (n 12..24, d in {3, 8, 16}), admission by HBM
     footprint against a 180 GB pool, cost-model routing; against the same
@@ -674,10 +740,12 @@ def main():
     ap.add_argument("--gate", type=int, default=1, choices=[1, 2])
     ap.add_argument("--form", default="both", choices=["both", "sumcheck", "ntt"],
                     help="restrict the step to one form (profiling); the bench line uses both")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "served", "sweep", "family"],
+    ap.add_argument("--pcs-queries", type=int, default=189, help="pcs: queried positions of an opening")
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "served", "sweep", "family", "pcs"],
                     help="plain: one Plonk n=22 proof per form (the headline line); batched: 64 "
                          "mixed instances in one graph; served: Poisson request loop; sweep: "
-                         "sizes and degrees; family: the paper's polynomials as sum gates")
+                         "sizes and degrees; family: the paper's polynomials as sum gates; pcs: the "
+                         "hash-based commitment around the ZeroCheck")
     ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="served: arrival rates (req/s)")
     ap.add_argument("--requests", type=int, default=200, help="served: requests per rate")
     args = ap.parse_args()
@@ -701,6 +769,9 @@ def main():
         return
     if args.workload == "family":
         run_family(args, world, rank, local)
+        return
+    if args.workload == "pcs":
+        run_pcs(args, world, rank, local)
         return
     import torch
     from paper_2606_16146_gb300 import witness, zc
