@@ -421,6 +421,147 @@ ZC_D fr fr_mul_inl(const fr& a, const fr& b) {
   return fr_reduce_final(t0, t1, t2, t3, t4, t5, t6, t7);
 }
 
+// Sums of products with one reduction: (a0 b0 + ... + a_{K-1} b_{K-1}) R^-1
+// mod r, for inputs below r, K = 2 or 3.  Each CIOS row adds a_p b_p[i] for
+// every p into a 10-word accumulator, then one reduction step m r (m = -t0)
+// and a one-word shift.  Between rows the accumulator stays below (K+1) r
+// < 2^257 (nine words), before the shift below 2^289 (ten); at the end it is
+// (sum a_p b_p + M r) / 2^256 < r (K r / 2^256 + 1) < 2.36 r for K = 3, so
+// at most two subtractions of r give the canonical result.  Against K
+// separate products and K - 1 additions this saves K - 1 reductions and the
+// final corrections (~30 % fewer instructions for K = 3).
+
+// t[0..9] += a * bi
+ZC_D void zc_acc_row(const fr& a, uint32_t bi, uint32_t& t0, uint32_t& t1, uint32_t& t2, uint32_t& t3,
+                     uint32_t& t4, uint32_t& t5, uint32_t& t6, uint32_t& t7, uint32_t& t8, uint32_t& t9) {
+  uint64_t q0, q1, q2, q3, q4, q5, q6, q7;
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(q0) : "r"(a.v[0]), "r"(bi));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(q1) : "r"(a.v[1]), "r"(bi));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(q2) : "r"(a.v[2]), "r"(bi));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(q3) : "r"(a.v[3]), "r"(bi));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(q4) : "r"(a.v[4]), "r"(bi));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(q5) : "r"(a.v[5]), "r"(bi));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(q6) : "r"(a.v[6]), "r"(bi));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(q7) : "r"(a.v[7]), "r"(bi));
+  uint32_t s1, s2, s3, s4, s5, s6, s7, s8;
+  asm("add.cc.u32 %0, %8, %9;\n\t"
+      "addc.cc.u32 %1, %10, %11;\n\t"
+      "addc.cc.u32 %2, %12, %13;\n\t"
+      "addc.cc.u32 %3, %14, %15;\n\t"
+      "addc.cc.u32 %4, %16, %17;\n\t"
+      "addc.cc.u32 %5, %18, %19;\n\t"
+      "addc.cc.u32 %6, %20, %21;\n\t"
+      "addc.u32 %7, %22, 0;"
+      : "=r"(s1), "=r"(s2), "=r"(s3), "=r"(s4), "=r"(s5), "=r"(s6), "=r"(s7), "=r"(s8)
+      : "r"(ZC_LO(q1)), "r"(ZC_HI(q0)), "r"(ZC_LO(q2)), "r"(ZC_HI(q1)), "r"(ZC_LO(q3)),
+        "r"(ZC_HI(q2)), "r"(ZC_LO(q4)), "r"(ZC_HI(q3)), "r"(ZC_LO(q5)), "r"(ZC_HI(q4)),
+        "r"(ZC_LO(q6)), "r"(ZC_HI(q5)), "r"(ZC_LO(q7)), "r"(ZC_HI(q6)), "r"(ZC_HI(q7)));
+  asm("add.cc.u32 %0, %0, %10;\n\t"
+      "addc.cc.u32 %1, %1, %11;\n\t"
+      "addc.cc.u32 %2, %2, %12;\n\t"
+      "addc.cc.u32 %3, %3, %13;\n\t"
+      "addc.cc.u32 %4, %4, %14;\n\t"
+      "addc.cc.u32 %5, %5, %15;\n\t"
+      "addc.cc.u32 %6, %6, %16;\n\t"
+      "addc.cc.u32 %7, %7, %17;\n\t"
+      "addc.cc.u32 %8, %8, %18;\n\t"
+      "addc.u32 %9, %9, 0;"
+      : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3), "+r"(t4), "+r"(t5), "+r"(t6), "+r"(t7), "+r"(t8), "+r"(t9)
+      : "r"(ZC_LO(q0)), "r"(s1), "r"(s2), "r"(s3), "r"(s4), "r"(s5), "r"(s6), "r"(s7), "r"(s8));
+}
+
+// t <- (t + m r) / 2^32 with m = -t0 (r0 = 1, r1 = 2^32 - 1); t9 becomes 0
+ZC_D void zc_reduce_row(uint32_t& t0, uint32_t& t1, uint32_t& t2, uint32_t& t3, uint32_t& t4, uint32_t& t5,
+                        uint32_t& t6, uint32_t& t7, uint32_t& t8, uint32_t& t9) {
+  const uint32_t m = 0u - t0, c0 = t0 != 0 ? 1u : 0u;
+  const uint32_t r1lo = t0, r1hi = m - c0;  // m (2^32 - 1)
+  uint64_t r2, r3, r4, r5, r6, r7;
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(r2) : "r"(m), "n"(ZC_P2));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(r3) : "r"(m), "n"(ZC_P3));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(r4) : "r"(m), "n"(ZC_P4));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(r5) : "r"(m), "n"(ZC_P5));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(r6) : "r"(m), "n"(ZC_P6));
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(r7) : "r"(m), "n"(ZC_P7));
+  uint32_t v1, v2, v3, v4, v5, v6, v7, v8;
+  asm("add.cc.u32 %0, %8, %9;\n\t"
+      "addc.cc.u32 %1, %10, %11;\n\t"
+      "addc.cc.u32 %2, %12, %13;\n\t"
+      "addc.cc.u32 %3, %14, %15;\n\t"
+      "addc.cc.u32 %4, %16, %17;\n\t"
+      "addc.cc.u32 %5, %18, %19;\n\t"
+      "addc.cc.u32 %6, %20, %21;\n\t"
+      "addc.u32 %7, %22, 0;"
+      : "=r"(v1), "=r"(v2), "=r"(v3), "=r"(v4), "=r"(v5), "=r"(v6), "=r"(v7), "=r"(v8)
+      : "r"(r1lo), "r"(c0), "r"(ZC_LO(r2)), "r"(r1hi), "r"(ZC_LO(r3)), "r"(ZC_HI(r2)),
+        "r"(ZC_LO(r4)), "r"(ZC_HI(r3)), "r"(ZC_LO(r5)), "r"(ZC_HI(r4)), "r"(ZC_LO(r6)),
+        "r"(ZC_HI(r5)), "r"(ZC_LO(r7)), "r"(ZC_HI(r6)), "r"(ZC_HI(r7)));
+  // t0 + (m r mod 2^32) = 0 with a carry exactly when t0 != 0 (c0 above);
+  // the shifted sum goes to fresh registers
+  uint32_t n0, n1, n2, n3, n4, n5, n6, n7, n8;
+  asm("add.cc.u32 %0, %9, %18;\n\t"
+      "addc.cc.u32 %1, %10, %19;\n\t"
+      "addc.cc.u32 %2, %11, %20;\n\t"
+      "addc.cc.u32 %3, %12, %21;\n\t"
+      "addc.cc.u32 %4, %13, %22;\n\t"
+      "addc.cc.u32 %5, %14, %23;\n\t"
+      "addc.cc.u32 %6, %15, %24;\n\t"
+      "addc.cc.u32 %7, %16, %25;\n\t"
+      "addc.u32 %8, %17, 0;"
+      : "=r"(n0), "=r"(n1), "=r"(n2), "=r"(n3), "=r"(n4), "=r"(n5), "=r"(n6), "=r"(n7), "=r"(n8)
+      : "r"(t1), "r"(t2), "r"(t3), "r"(t4), "r"(t5), "r"(t6), "r"(t7), "r"(t8), "r"(t9), "r"(v1),
+        "r"(v2), "r"(v3), "r"(v4), "r"(v5), "r"(v6), "r"(v7), "r"(v8));
+  t0 = n0; t1 = n1; t2 = n2; t3 = n3; t4 = n4; t5 = n5; t6 = n6; t7 = n7; t8 = n8;
+  t9 = 0;
+}
+
+// t (nine words, below 3r) minus r when it is at least r
+ZC_D void zc_sub_r_if(uint32_t& t0, uint32_t& t1, uint32_t& t2, uint32_t& t3, uint32_t& t4, uint32_t& t5,
+                      uint32_t& t6, uint32_t& t7, uint32_t& t8) {
+  uint32_t s0, s1, s2, s3, s4, s5, s6, s7, s8, bw;
+  asm("sub.cc.u32 %0, %10, %19;\n\t"
+      "subc.cc.u32 %1, %11, %20;\n\t"
+      "subc.cc.u32 %2, %12, %21;\n\t"
+      "subc.cc.u32 %3, %13, %22;\n\t"
+      "subc.cc.u32 %4, %14, %23;\n\t"
+      "subc.cc.u32 %5, %15, %24;\n\t"
+      "subc.cc.u32 %6, %16, %25;\n\t"
+      "subc.cc.u32 %7, %17, %26;\n\t"
+      "subc.cc.u32 %8, %18, 0;\n\t"
+      "subc.u32 %9, 0, 0;"
+      : "=r"(s0), "=r"(s1), "=r"(s2), "=r"(s3), "=r"(s4), "=r"(s5), "=r"(s6), "=r"(s7), "=r"(s8), "=r"(bw)
+      : "r"(t0), "r"(t1), "r"(t2), "r"(t3), "r"(t4), "r"(t5), "r"(t6), "r"(t7), "r"(t8), "n"(ZC_P0),
+        "n"(ZC_P1), "n"(ZC_P2), "n"(ZC_P3), "n"(ZC_P4), "n"(ZC_P5), "n"(ZC_P6), "n"(ZC_P7));
+  // bw == 0xffffffff: t < r, keep it
+  t0 = bw ? t0 : s0; t1 = bw ? t1 : s1; t2 = bw ? t2 : s2; t3 = bw ? t3 : s3; t4 = bw ? t4 : s4;
+  t5 = bw ? t5 : s5; t6 = bw ? t6 : s6; t7 = bw ? t7 : s7; t8 = bw ? t8 : s8;
+}
+
+template <int K>
+ZC_D fr fr_mul_sum_inl(const fr (&a)[K], const fr (&b)[K]) {
+  uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0, t7 = 0, t8 = 0, t9 = 0;
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+#pragma unroll
+    for (int p = 0; p < K; p++) zc_acc_row(a[p], b[p].v[i], t0, t1, t2, t3, t4, t5, t6, t7, t8, t9);
+    zc_reduce_row(t0, t1, t2, t3, t4, t5, t6, t7, t8, t9);
+  }
+  zc_sub_r_if(t0, t1, t2, t3, t4, t5, t6, t7, t8);
+  if (K > 2) zc_sub_r_if(t0, t1, t2, t3, t4, t5, t6, t7, t8);
+  fr x;
+  x.v[0] = t0; x.v[1] = t1; x.v[2] = t2; x.v[3] = t3; x.v[4] = t4; x.v[5] = t5; x.v[6] = t6; x.v[7] = t7;
+  return x;
+}
+
+// out-of-line copy shared by the kernels (see fr_mul_call)
+static __device__ __noinline__ fr fr_mul_sum3_call(fr a0, fr b0, fr a1, fr b1, fr a2, fr b2) {
+  const fr a[3] = {a0, a1, a2}, b[3] = {b0, b1, b2};
+  return fr_mul_sum_inl<3>(a, b);
+}
+// (a0 b0 + a1 b1 + a2 b2) R^-1, canonical
+ZC_D fr fr_mul_sum3(const fr& a0, const fr& b0, const fr& a1, const fr& b1, const fr& a2, const fr& b2) {
+  return fr_mul_sum3_call(a0, b0, a1, b1, a2, b2);
+}
+
 // The multiplier is ~400 instructions; kernels call one out-of-line copy so
 // that their code fits the instruction cache (inlined at every call site, a
 // round body of ~30 products missed the cache on almost every instruction).

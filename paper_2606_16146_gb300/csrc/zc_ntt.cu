@@ -436,11 +436,10 @@ __global__ void __launch_bounds__(256) k_ntt_gate(NttGateArgs A) {
        p += (uint64_t)gridDim.x * blockDim.x) {
     fr f;
     if (A.gate == ZC_GATE_PLONK) {
-      fr b = ld_fr(A.col[6] + p);
-      fr u = fr_add(ld_fr(A.col[0] + p), fr_mul(ld_fr(A.col[2] + p), b));
-      f = fr_mul(ld_fr(A.col[5] + p), u);
-      f = fr_add(f, fr_mul(ld_fr(A.col[1] + p), b));
-      f = fr_add(f, fr_mul(ld_fr(A.col[3] + p), ld_fr(A.col[7] + p)));
+      // a (qL + qM b) + qR b + qO c with one reduction for the three products
+      const fr b = ld_fr(A.col[6] + p);
+      const fr u = fr_add(ld_fr(A.col[0] + p), fr_mul(ld_fr(A.col[2] + p), b));
+      f = fr_mul_sum3(ld_fr(A.col[5] + p), u, ld_fr(A.col[1] + p), b, ld_fr(A.col[3] + p), ld_fr(A.col[7] + p));
       f = fr_add(f, ld_fr(A.col[4] + p));
     } else {
       f = ld_fr(A.col[0] + p);
