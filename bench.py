@@ -629,7 +629,8 @@ def run_pcs(args, world, rank, local):
     sc_ms, _ = timed(lambda: ctx.prove_sumcheck(GATE, n, DEG, dcols, roots=roots, stream=stream,
                                                 proof_out=proof), K)
     pb = proof.cpu().numpy().tobytes()
-    pt_ms, (alpha, vals, ok) = timed(lambda: zc.sumcheck_point(GATE, n, DEG, 1, roots, pb), 1)
+    zc.sumcheck_point(GATE, n, DEG, 1, roots, pb)  # first call builds the host constants
+    pt_ms, (alpha, vals, ok) = timed(lambda: zc.sumcheck_point(GATE, n, DEG, 1, roots, pb), K)
     open_ms, pr = timed(lambda: com.open(alpha, vals, stream=stream), K)
     t0 = time.perf_counter()
     accept = zc.pcs_verify(n, c, t, com.root, alpha, vals, pr)

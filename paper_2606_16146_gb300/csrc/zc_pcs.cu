@@ -29,25 +29,44 @@ namespace zc {
 struct PcsCombineArgs {
   const fr* col[kMaxCols];
   const fr* coef;     // level 1: [i] (per column) or [j m + i] (summed over columns)
-  fr* out;            // [j w + l] (per column) or [l]
+  fr* part;           // [chunk][out][l] partial sums
   uint32_t c;
   uint64_t m, w;
   uint32_t sum_all;   // 1: one output summing every column
+  uint32_t rows;      // rows per chunk (blockIdx.z)
 };
 
-// out = sum_i coef[i] M_j[i][l] per column j, or sum_{j,i} coef[j m + i]
-// M_j[i][l]; canonical columns times level-1 coefficients: canonical out.
+// Partial sums over one chunk of rows: per column j (blockIdx.y) sum_i
+// coef[i] M_j[i][l], or over the chunk of the c m stacked rows sum coef[q]
+// M[q][l]; canonical columns times level-1 coefficients: canonical out.
 // Consecutive threads take consecutive l: every row read is coalesced.
 __global__ void __launch_bounds__(256) k_pcs_combine(PcsCombineArgs A) {
   const uint64_t l = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= A.w) return;
-  const uint32_t j0 = A.sum_all ? 0 : blockIdx.y, j1 = A.sum_all ? A.c : blockIdx.y + 1;
+  const uint64_t q0 = (uint64_t)blockIdx.z * A.rows;
   fr acc = fr_zero();
-  for (uint32_t j = j0; j < j1; j++) {
-    const fr* co = A.coef + (A.sum_all ? (uint64_t)j * A.m : 0);
-    for (uint64_t i = 0; i < A.m; i++) acc = fr_add(acc, fr_mul(ld_fr(co + i), ld_fr(A.col[j] + i * A.w + l)));
+  if (A.sum_all) {
+    const uint64_t q1 = min(q0 + A.rows, (uint64_t)A.c * A.m);
+    for (uint64_t q = q0; q < q1; q++) {
+      const uint64_t j = q / A.m, i = q - j * A.m;
+      acc = fr_add(acc, fr_mul(ld_fr(A.coef + q), ld_fr(A.col[j] + i * A.w + l)));
+    }
+  } else {
+    const uint32_t j = blockIdx.y;
+    const uint64_t q1 = min(q0 + A.rows, A.m);
+    for (uint64_t i = q0; i < q1; i++) acc = fr_add(acc, fr_mul(ld_fr(A.coef + i), ld_fr(A.col[j] + i * A.w + l)));
   }
-  st_fr(A.out + (A.sum_all ? 0 : (uint64_t)blockIdx.y * A.w) + l, acc);
+  const uint64_t outs = A.sum_all ? 1 : A.c;
+  st_fr(A.part + ((uint64_t)blockIdx.z * outs + blockIdx.y) * A.w + l, acc);
+}
+
+// out[e] = sum over the chunks of part[chunk][e], e < count
+__global__ void k_pcs_sum_chunks(const fr* part, uint64_t count, uint32_t chunks, fr* out) {
+  const uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= count) return;
+  fr acc = fr_zero();
+  for (uint32_t z = 0; z < chunks; z++) acc = fr_add(acc, ld_fr(part + (uint64_t)z * count + e));
+  st_fr(out + e, acc);
 }
 
 struct PcsGatherArgs {
@@ -329,8 +348,13 @@ zc_status zc_pcs_open(zc_pcs* P, const uint8_t (*alpha)[32], const uint8_t (*val
   const size_t ncoef = std::max<uint64_t>(S.m, (uint64_t)S.c * S.m);
   const size_t bcoef = align_up(ncoef * sizeof(fr), 256), bu = align_up((S.c + 1) * S.w * sizeof(fr), 256);
   const size_t bq = align_up(S.t * 4, 256), bg = align_up((size_t)S.t * S.c * S.m * sizeof(fr), 256);
+  // partial sums: chunks of kRows rows, enough CTAs to fill the GPU
+  constexpr uint32_t kRows = 32;
+  const uint32_t ch_u = (uint32_t)((S.m + kRows - 1) / kRows);
+  const uint32_t ch_g = (uint32_t)(((uint64_t)S.c * S.m + kRows - 1) / kRows);
+  const size_t bp = align_up(std::max<uint64_t>((uint64_t)ch_u * S.c, ch_g) * S.w * sizeof(fr), 256);
   void* mem = nullptr;
-  if (cudaMalloc(&mem, bcoef + bu + bq + bg) != cudaSuccess) {
+  if (cudaMalloc(&mem, bcoef + bu + bq + bg + bp) != cudaSuccess) {
     cudaGetLastError();
     ctx->err = "pcs: cudaMalloc of the opening buffers failed";
     return ZC_ERR_OOM;
@@ -344,6 +368,7 @@ zc_status zc_pcs_open(zc_pcs* P, const uint8_t (*alpha)[32], const uint8_t (*val
   fr* du = reinterpret_cast<fr*>(q + bcoef);
   uint32_t* dk = reinterpret_cast<uint32_t*>(q + bcoef + bu);
   fr* dg = reinterpret_cast<fr*>(q + bcoef + bu + bq);
+  fr* dpart = reinterpret_cast<fr*>(q + bcoef + bu + bq + bg);
 
   PcsTranscript tr;
   tr.init(S, P->root, alpha, values);
@@ -363,10 +388,12 @@ zc_status zc_pcs_open(zc_pcs* P, const uint8_t (*alpha)[32], const uint8_t (*val
   ca.m = S.m;
   ca.w = S.w;
   ca.coef = dcoef;
-  ca.out = du;
+  ca.part = dpart;
   ca.sum_all = 0;
+  ca.rows = kRows;
   PCS_TRY(ctx, cudaMemcpyAsync(dcoef, co.data(), S.m * sizeof(fr), cudaMemcpyHostToDevice, st));
-  k_pcs_combine<<<dim3((unsigned)((S.w + 255) / 256), S.c), 256, 0, st>>>(ca);
+  k_pcs_combine<<<dim3((unsigned)((S.w + 255) / 256), S.c, ch_u), 256, 0, st>>>(ca);
+  k_pcs_sum_chunks<<<(unsigned)((S.c * S.w + 255) / 256), 256, 0, st>>>(dpart, S.c * S.w, ch_u, du);
   PCS_TRY(ctx, cudaMemcpyAsync(pp, du, (size_t)S.c * S.w * sizeof(fr), cudaMemcpyDeviceToHost, st));
   PCS_TRY(ctx, cudaStreamSynchronize(st));
   tr.absorb(pp, (size_t)S.c * S.w * 32);
@@ -381,7 +408,8 @@ zc_status zc_pcs_open(zc_pcs* P, const uint8_t (*alpha)[32], const uint8_t (*val
   }
   ca.sum_all = 1;
   PCS_TRY(ctx, cudaMemcpyAsync(dcoef, co.data(), co.size() * sizeof(fr), cudaMemcpyHostToDevice, st));
-  k_pcs_combine<<<dim3((unsigned)((S.w + 255) / 256), 1), 256, 0, st>>>(ca);
+  k_pcs_combine<<<dim3((unsigned)((S.w + 255) / 256), 1, ch_g), 256, 0, st>>>(ca);
+  k_pcs_sum_chunks<<<(unsigned)((S.w + 255) / 256), 256, 0, st>>>(dpart, S.w, ch_g, du);
   PCS_TRY(ctx, cudaMemcpyAsync(pp, du, S.w * sizeof(fr), cudaMemcpyDeviceToHost, st));
   PCS_TRY(ctx, cudaStreamSynchronize(st));
   tr.absorb(pp, S.w * 32);
