@@ -246,7 +246,8 @@ void zc_batch_destroy(zc_batch* batch);
  * bytes each) on the current device.  col_roots: host array of c roots, or
  * NULL to compute them inside the static scratch; given roots are copied
  * from the caller's (pageable) host array by a host-to-device copy queued on
- * cuda_stream.  cuda_stream: the stream the work is queued on.  proof:
+ * cuda_stream, which a stream capture cannot record: under capture pass
+ * col_roots = NULL.  cuda_stream: the stream the work is queued on.  proof:
  * DEVICE buffer of cap bytes; *len receives the proof size.  The call is
  * asynchronous: the proof is ready when the stream reaches it.  The bytes
  * equal zc_prove_sumcheck's.
