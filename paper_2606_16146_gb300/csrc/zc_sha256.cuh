@@ -97,6 +97,53 @@ ZC_HD void sha256_compress(uint32_t h[8], const uint32_t w_in[16]) {
   h[4] += e; h[5] += f; h[6] += g; h[7] += hh;
 }
 
+#if defined(__CUDACC__)
+// Two out-of-line copies of the compression for the transcript, where one
+// thread hashes a few blocks per challenge.  Both are single shared copies
+// (__noinline__): an inlined unrolled body is ~25 KB per call site, fetched
+// cold each round.  sha256_compress_hot is the unrolled body, fastest once
+// it is in the instruction cache (rounds that follow one another inside one
+// launch); sha256_compress_small is a 16-round body run four times (the
+// schedule update skipped in the first pass by a uniform branch, the round
+// constants read by index), for a challenge that runs once in a launch and
+// finds its code cold.
+static __device__ __noinline__ void sha256_compress_hot(uint32_t h[8], const uint32_t w_in[16]) {
+  sha256_compress(h, w_in);
+}
+
+static __device__ __noinline__ void sha256_compress_small(uint32_t h[8], const uint32_t w_in[16]) {
+  uint32_t w[16];
+#pragma unroll
+  for (int i = 0; i < 16; i++) w[i] = w_in[i];
+  uint32_t a = h[0], b = h[1], c = h[2], d = h[3], e = h[4], f = h[5], g = h[6], hh = h[7];
+#pragma unroll 1
+  for (int j = 0; j < 64; j += 16) {
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+      if (j > 0) {
+        const uint32_t x15 = w[(i + 1) & 15], x2 = w[(i + 14) & 15];
+        const uint32_t s0 = sha_rotr(x15, 7) ^ sha_rotr(x15, 18) ^ (x15 >> 3);
+        const uint32_t s1 = sha_rotr(x2, 17) ^ sha_rotr(x2, 19) ^ (x2 >> 10);
+        w[i] = w[i] + s0 + w[(i + 9) & 15] + s1;
+      }
+      const uint32_t t1 = hh + (sha_rotr(e, 6) ^ sha_rotr(e, 11) ^ sha_rotr(e, 25)) + ((e & f) ^ (~e & g)) +
+                          kShaK[j + i] + w[i];
+      const uint32_t t2 = (sha_rotr(a, 2) ^ sha_rotr(a, 13) ^ sha_rotr(a, 22)) + ((a & b) | (c & (a | b)));
+      hh = g;
+      g = f;
+      f = e;
+      e = d + t1;
+      d = c;
+      c = b;
+      b = a;
+      a = t1 + t2;
+    }
+  }
+  h[0] += a; h[1] += b; h[2] += c; h[3] += d;
+  h[4] += e; h[5] += f; h[6] += g; h[7] += hh;
+}
+#endif
+
 ZC_HD void sha256_init(uint32_t h[8]) {
   h[0] = 0x6a09e667; h[1] = 0xbb67ae85; h[2] = 0x3c6ef372; h[3] = 0xa54ff53a;
   h[4] = 0x510e527f; h[5] = 0x9b05688c; h[6] = 0x1f83d9ab; h[7] = 0x5be0cd19;

@@ -178,12 +178,24 @@ struct ChalSmem {
   fr Hc[kMaxPts];
   fr H[kMaxPts + 1];   // H(0..d+1)
   fr Hinf;
+  fr tinf[2];          // Hinf times the two extrapolation weights
+  fr hd[kMaxPts];      // H(t) times the Lagrange denominator's inverse
   fr tmp[2][kMaxPts];
   fr cl[kMaxPts];      // c_i l_i(t)
   fr alpha;
   uint32_t msg[8 + 8 * kMaxPts];
 };
 static_assert(2 * kMaxPts >= 32, "tmp holds one partial sum per warp of a 1024-thread CTA");
+
+// Round i's value t (G_i(t), or H_i(t) for v2): into the transcript message
+// (big-endian words) and the proof (little-endian bytes).
+__device__ __forceinline__ void sc_put_value(ChalSmem& S, uint8_t* proof, int i, int per, int t, const fr& g) {
+  uint8_t* pout = proof + 16 + 32 * ((size_t)i * per + t);
+  for (int q = 0; q < 8; q++) {
+    S.msg[8 + 8 * t + q] = sha_bswap(g.v[q]);
+    for (int b = 0; b < 4; b++) pout[4 * q + b] = (uint8_t)(g.v[q] >> (8 * b));
+  }
+}
 
 // Finish round `i` from the sums Hc (shared memory, np values): either all
 // of H(0..d-1) and H(inf) (np = d + 1) or H(p0), H(2..d-1), H(inf) (np = d,
@@ -192,17 +204,22 @@ static_assert(2 * kMaxPts >= 32, "tmp holds one partial sum per warp of a 1024-t
 // message), absorb, squeeze alpha_i, update c_i and, when the next round
 // derives a point, the claim H_i(alpha_i).  All threads of the CTA (at least
 // 128).  Independent steps run on different warps so the serial chain is
-// eight multiplications and the hash.
+// four multiplications and the hash up to alpha (two or three more for c_i
+// and the claim).  COLD: the hash uses the compact compression (a launch
+// that runs one challenge).  release: a flag that receives i + 1 as soon as
+// alpha_i is out (the persistent round kernel's hand-off).
+template <bool COLD>
 __device__ void sc_challenge(ChalSmem& S, int np, int d, int i, ScState* st, uint8_t* proof,
-                             const DevConst* C, const fr* tabs, bool need_claim, bool v2) {
+                             const DevConst* C, const fr* tabs, bool need_claim, bool v2,
+                             uint32_t* release = nullptr) {
   const bool full = np == d + 1;
   const fr r = st->r[i];
   const fr two_r_m1 = fr_sub(fr_add(r, r), C->one);
   const fr one_m_r = fr_sub(C->one, r);
   const int t = threadIdx.x;
   const int hs = (d + 2 + 31) / 32 * 32;  // first thread of the warp after the c_i l_i(t) threads
-  if (t < d + 2) {  // c_i l_i(t)
-    if (!v2) S.cl[t] = fr_mul(st->ci, fr_add(one_m_r, fr_mul(C->small[t], two_r_m1)));
+  if (t < d + 2) {  // c_i l_i(t), l_i(t) = (1 - r) + t (2 r - 1): t times by additions
+    if (!v2) S.cl[t] = fr_mul(st->ci, fr_add(one_m_r, fr_mul_small(two_r_m1, (uint32_t)t)));
   } else if (t == hs) {  // another warp: H(0..d-1), H(inf)
     S.Hinf = S.Hc[np - 1];
     if (full) {
@@ -222,50 +239,55 @@ __device__ void sc_challenge(ChalSmem& S, int np, int d, int i, ScState* st, uin
   }
   if (t < 8) S.msg[t] = st->S[t];
   __syncthreads();
-  // extrapolate H(d), H(d+1) from H(0..d-1) and the leading coefficient
+  // extrapolate H(d), H(d+1) from H(0..d-1) and the leading coefficient:
+  // every product in parallel, then two sums
   const fr* ext = tabs + C->ext_base[d];
-  if (t < 2 * d) {
-    const int which = t / d, q = t % d;
-    S.tmp[which][q] = fr_mul(S.H[q], ext[2 + which * d + q]);
+  for (int k = t; k < 2 * d + 2; k += blockDim.x) {
+    if (k < 2 * d) {
+      const int which = k / d, q = k % d;
+      S.tmp[which][q] = fr_mul(S.H[q], ext[2 + which * d + q]);
+    } else {
+      S.tinf[k - 2 * d] = fr_mul(S.Hinf, ext[k - 2 * d]);
+    }
   }
   __syncthreads();
   if (t < 2) {
-    fr v = fr_mul(S.Hinf, ext[t]);
+    fr v = S.tinf[t];
     for (int q = 0; q < d; q++) v = fr_add(v, S.tmp[t][q]);
     S.H[d + t] = v;
   }
   __syncthreads();
   // G(t) = c_i l_i(t) H(t) at t = 0..d+1, or (v2) H(t) at t = 0..d; H is
-  // at level 0 = canonical
+  // at level 0 = canonical.  Other threads: H(t) / prod_{q != t} (t - q)
+  // for the next claim.
   const int per = v2 ? d + 1 : d + 2;
-  if (t < per) {
-    const fr g = v2 ? S.H[t] : fr_mul(S.H[t], S.cl[t]);
-    uint8_t* pout = proof + 16 + 32 * ((size_t)i * per + t);
-    for (int q = 0; q < 8; q++) {
-      S.msg[8 + 8 * t + q] = sha_bswap(g.v[q]);
-      for (int b = 0; b < 4; b++) pout[4 * q + b] = (uint8_t)(g.v[q] >> (8 * b));
-    }
-  }
+  if (t < per) sc_put_value(S, proof, i, per, t, v2 ? S.H[t] : fr_mul(S.H[t], S.cl[t]));
+  const fr* dinv = tabs + C->lag_base[d];
+  if (need_claim && t >= 32 && t - 32 <= d) S.hd[t - 32] = fr_mul(S.H[t - 32], dinv[t - 32]);
   __syncthreads();
   if (t == 0) {
     uint32_t Sn[8];
-    sha256_words(S.msg, 8 + 8 * per, Sn);
-    const fr a = fr_mul(tr_squeeze(Sn), C->r2);
+    sha256_words<COLD>(S.msg, 8 + 8 * per, Sn);
+    const fr a = fr_mul(tr_squeeze<COLD>(Sn), C->r2);
     for (int q = 0; q < 8; q++) st->S[q] = Sn[q];
     st->alpha[i] = a;
     S.alpha = a;
+    if (release) {  // the next round needs only alpha: hand it off before c_i and the claim
+      __threadfence();
+      atomicExch(release, (uint32_t)(i + 1));
+    }
   }
   __syncthreads();
   const fr a = S.alpha;
   if (t == hs) st->ci = fr_mul(st->ci, fr_add(one_m_r, fr_mul(a, two_r_m1)));
   if (need_claim) {
     // next claim H_i(alpha) by Lagrange over the nodes 0..d
-    const fr* dinv = tabs + C->lag_base[d];
     if (t <= d) {
-      fr num = C->one;
-      for (int q = 0; q <= d; q++)
+      const int q0 = t == 0 ? 1 : 0;
+      fr num = fr_sub(a, C->small[q0]);
+      for (int q = q0 + 1; q <= d; q++)
         if (q != t) num = fr_mul(num, fr_sub(a, C->small[q]));
-      S.tmp[0][t] = fr_mul(fr_mul(S.H[t], num), dinv[t]);
+      S.tmp[0][t] = fr_mul(S.hd[t], num);
     }
     __syncthreads();
     if (t == 0) {
@@ -325,7 +347,7 @@ __device__ void sc_finish_round(const ScRoundArgs& A, int np) {
   if (!am_last) return;
   __threadfence();
   sc_sum_partials(S, A.partials, A.nwork, np);
-  sc_challenge(S, np, (int)A.d, A.round, A.st, A.proof, A.C, A.tabs, A.next_derives != 0, A.v2 != 0);
+  sc_challenge<true>(S, np, (int)A.d, A.round, A.st, A.proof, A.C, A.tabs, A.next_derives != 0, A.v2 != 0);
 }
 
 // ------------------------------------------------------- per-pair work --
@@ -785,11 +807,7 @@ __global__ void __launch_bounds__(16 * kSmallPB) k_sc_plonk_rounds(ScRoundArgs A
     if (flag == 1) {
       __threadfence();
       sc_sum_partials(CS, A.partials, nwork, 4);
-      sc_challenge(CS, 4, 3, i, A.st, A.proof, A.C, A.tabs, false, A.v2 != 0);
-      if (threadIdx.x == 0) {
-        __threadfence();
-        atomicExch(&A.st->go, (uint32_t)(i + 1));
-      }
+      sc_challenge<false>(CS, 4, 3, i, A.st, A.proof, A.C, A.tabs, false, A.v2 != 0, &A.st->go);
     } else {
       if (threadIdx.x == 0) {
         uint32_t polls = 0;
@@ -1018,7 +1036,7 @@ __global__ void __launch_bounds__(PLONK ? kTailThreads : 256, 1) k_sc_tail(ScRou
     }
     for (int p = threadIdx.x; p < np; p += blockDim.x) S.Hc[p] = pg[p];
     __syncthreads();
-    sc_challenge(S, np, d, i, A.st, A.proof, C, A.tabs, false, A.v2 != 0);
+    sc_challenge<false>(S, np, d, i, A.st, A.proof, C, A.tabs, false, A.v2 != 0);
   }
   if (bad) atomicOr(&A.st->err, 1u);
   __syncthreads();

@@ -13,30 +13,52 @@ namespace zc {
 
 #if defined(__CUDACC__)
 
-// SHA-256 over nwords big-endian message words (any count), digest in out.
-__device__ inline void sha256_words(const uint32_t* w, uint32_t nwords, uint32_t out[8]) {
-  sha256_init(out);
+// One compression for transcript hashing: COLD picks the compact copy, for a
+// hash that runs once in a launch (see zc_sha256.cuh).
+template <bool COLD>
+__device__ __forceinline__ void tr_compress(uint32_t h[8], const uint32_t w[16]) {
+  if (COLD) sha256_compress_small(h, w);
+  else sha256_compress_hot(h, w);
+}
+
+// SHA-256 of a word message in pieces: tr_blocks compresses the complete
+// 16-word blocks [b0, b1); tr_last compresses what remains after the last
+// complete block, with the padding and the bit length.
+template <bool COLD>
+__device__ inline void tr_blocks(uint32_t h[8], const uint32_t* w, uint32_t b0, uint32_t b1) {
   uint32_t blk[16];
-  const uint32_t full = nwords / 16;
-  for (uint32_t b = 0; b < full; b++) {
+  for (uint32_t b = b0; b < b1; b++) {
 #pragma unroll
     for (int i = 0; i < 16; i++) blk[i] = w[16 * b + i];
-    sha256_compress(out, blk);
+    tr_compress<COLD>(h, blk);
   }
-  const uint32_t rem = nwords - 16 * full;
+}
+
+template <bool COLD>
+__device__ inline void tr_last(uint32_t h[8], const uint32_t* w, uint32_t nwords) {
+  uint32_t blk[16];
+  const uint32_t full = nwords / 16, rem = nwords - 16 * full;
 #pragma unroll
   for (int i = 0; i < 16; i++) blk[i] = 0;
   for (uint32_t i = 0; i < rem; i++) blk[i] = w[16 * full + i];
   blk[rem] = 0x80000000u;
   const uint64_t bits = (uint64_t)nwords * 32;
   if (rem + 1 > 14) {
-    sha256_compress(out, blk);
+    tr_compress<COLD>(h, blk);
 #pragma unroll
     for (int i = 0; i < 16; i++) blk[i] = 0;
   }
   blk[14] = (uint32_t)(bits >> 32);
   blk[15] = (uint32_t)bits;
-  sha256_compress(out, blk);
+  tr_compress<COLD>(h, blk);
+}
+
+// SHA-256 over nwords big-endian message words (any count), digest in out.
+template <bool COLD = false>
+__device__ inline void sha256_words(const uint32_t* w, uint32_t nwords, uint32_t out[8]) {
+  sha256_init(out);
+  tr_blocks<COLD>(out, w, 0, nwords / 16);
+  tr_last<COLD>(out, w, nwords);
 }
 
 // S <- SHA-256(S | m) for a 32-byte message given as bytes
@@ -67,6 +89,7 @@ __device__ inline fr digest_mod_r(const uint32_t h[8]) {
 }
 
 // S <- SHA-256(S | 0x43); returns the canonical challenge
+template <bool COLD = false>
 __device__ inline fr tr_squeeze(uint32_t S[8]) {
   uint32_t w[16];
   for (int i = 0; i < 8; i++) w[i] = S[i];
@@ -75,7 +98,7 @@ __device__ inline fr tr_squeeze(uint32_t S[8]) {
   w[15] = 33 * 8;
   uint32_t h[8];
   sha256_init(h);
-  sha256_compress(h, w);
+  tr_compress<COLD>(h, w);
   for (int i = 0; i < 8; i++) S[i] = h[i];
   return digest_mod_r(h);
 }
