@@ -18,7 +18,10 @@
 //   device; the transcript, the query indices and the paths on the host.
 //   Verify (host): inner products, paths, and each queried column's
 //   combinations against the encodings of u_j and u' at x_k.
+#include <algorithm>
+#include <atomic>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "zc_internal.cuh"
@@ -486,45 +489,66 @@ zc_status zc_pcs_verify(const zc_pcs_params* params, const uint8_t root[32], con
     g = h_canon_mul(g, gamma, C);
   }
   const fr wW = h_root_of_unity(S.logW, C), seven = h_from_u64(7);
-  std::vector<fr> col;
-  for (uint32_t s2 = 0; s2 < S.t && ok; s2++) {
-    const uint64_t k = tr.query(S.W);
-    if (!load_canon(reinterpret_cast<const uint8_t(*)[32]>(pp), (size_t)S.c * S.m, col)) return ZC_ERR_ARG;
-    // the column up to the root
+  // The query positions come from the transcript alone; each query is then
+  // checked on its own (its path, and the encodings of u_j and u' at x_k
+  // against the column's combinations), the queries spread over host threads.
+  std::vector<uint64_t> ks(S.t);
+  for (uint32_t s2 = 0; s2 < S.t; s2++) ks[s2] = tr.query(S.W);
+  const size_t qbytes = (size_t)S.c * S.m * 32 + (size_t)S.logW * 32;
+  std::atomic<int> bad_fmt{0}, bad{ok ? 0 : 1};
+  std::atomic<uint32_t> next{0};
+  auto worker = [&]() {
+    std::vector<fr> col;
     std::vector<uint8_t> dg(32 * (size_t)S.c);
-    for (uint32_t j = 0; j < S.c; j++) sha256_bytes(pp + 32 * (size_t)j * S.m, S.m * 32, &dg[32 * j]);
-    uint8_t node[32], pair[64];
-    sha256_bytes(dg.data(), dg.size(), node);
-    pp += (size_t)S.c * S.m * 32;
-    uint64_t idx = k;
-    for (uint32_t lv = 0; lv < S.logW; lv++) {
-      if (idx & 1) {
-        std::memcpy(pair, pp, 32);
-        std::memcpy(pair + 32, node, 32);
-      } else {
-        std::memcpy(pair, node, 32);
-        std::memcpy(pair + 32, pp, 32);
+    for (uint32_t s2; (s2 = next.fetch_add(1)) < S.t;) {
+      if (bad.load() || bad_fmt.load()) return;
+      const uint64_t k = ks[s2];
+      const uint8_t* q = pp + s2 * qbytes;
+      if (!load_canon(reinterpret_cast<const uint8_t(*)[32]>(q), (size_t)S.c * S.m, col)) {
+        bad_fmt = 1;
+        return;
       }
-      sha256_bytes(pair, 64, node);
-      pp += 32;
-      idx >>= 1;
+      // the column up to the root
+      for (uint32_t j = 0; j < S.c; j++) sha256_bytes(q + 32 * (size_t)j * S.m, S.m * 32, &dg[32 * j]);
+      uint8_t node[32], pair[64];
+      sha256_bytes(dg.data(), dg.size(), node);
+      q += (size_t)S.c * S.m * 32;
+      uint64_t idx = k;
+      for (uint32_t lv = 0; lv < S.logW; lv++) {
+        if (idx & 1) {
+          std::memcpy(pair, q, 32);
+          std::memcpy(pair + 32, node, 32);
+        } else {
+          std::memcpy(pair, node, 32);
+          std::memcpy(pair + 32, q, 32);
+        }
+        sha256_bytes(pair, 64, node);
+        q += 32;
+        idx >>= 1;
+      }
+      uint8_t r2[32];
+      root_of_top(S.W, node, r2);
+      if (std::memcmp(r2, root, 32) != 0) bad = 1;
+      const fr xk = h_canon_mul(seven, h_pow(wW, k, C), C);
+      for (uint32_t j = 0; j <= S.c; j++) {
+        fr enc_u = fr_zero();
+        for (uint64_t l = S.w; l-- > 0;) enc_u = fr_add_g(h_canon_mul(enc_u, xk, C), u[j * S.w + l]);
+        fr comb = fr_zero();
+        if (j < S.c)
+          for (uint64_t i = 0; i < S.m; i++) comb = fr_add_g(comb, h_canon_mul(eqh[i], col[j * S.m + i], C));
+        else
+          for (size_t e = 0; e < gp.size(); e++) comb = fr_add_g(comb, h_canon_mul(gp[e], col[e], C));
+        if (!fr_equal(enc_u, comb)) bad = 1;
+      }
     }
-    uint8_t r2[32];
-    root_of_top(S.W, node, r2);
-    if (std::memcmp(r2, root, 32) != 0) ok = false;
-    // the encodings of u_j and u' at x_k against the column's combinations
-    const fr xk = h_canon_mul(seven, h_pow(wW, k, C), C);
-    for (uint32_t j = 0; j <= S.c; j++) {
-      fr enc_u = fr_zero();
-      for (uint64_t l = S.w; l-- > 0;) enc_u = fr_add_g(h_canon_mul(enc_u, xk, C), u[j * S.w + l]);
-      fr comb = fr_zero();
-      if (j < S.c)
-        for (uint64_t i = 0; i < S.m; i++) comb = fr_add_g(comb, h_canon_mul(eqh[i], col[j * S.m + i], C));
-      else
-        for (size_t e = 0; e < gp.size(); e++) comb = fr_add_g(comb, h_canon_mul(gp[e], col[e], C));
-      if (!fr_equal(enc_u, comb)) ok = false;
-    }
-  }
+  };
+  const unsigned nthr = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), S.t));
+  std::vector<std::thread> pool;
+  for (unsigned w = 1; w < nthr; w++) pool.emplace_back(worker);
+  worker();
+  for (auto& th : pool) th.join();
+  if (bad_fmt) return ZC_ERR_ARG;
+  ok = bad.load() == 0;
   *accept = ok ? 1 : 0;
   return ZC_OK;
 }
