@@ -684,6 +684,8 @@ def run_served(args, world, rank, local):
     warm = [(0.0, s) for s in sorted(srv.pool, key=lambda s: (s.n, s.d))]
     srv.run(srv.build(warm))
     one.run(one.build(warm))
+    if args.served_ntt > 0:
+        srv.run(srv.build(warm, [zc.ZC_FORM_NTT] * len(warm)))
     torch.cuda.synchronize()
     rows = {}
     clocks = ClockSampler(local)
@@ -702,6 +704,22 @@ def run_served(args, world, rank, local):
                     == c["proof"].cpu().numpy().tobytes() for a, b, c in zip(reqs, base_reqs, flat_reqs))
         rows[str(int(r))] = {"served": rep, "one_at_a_time": base, "served_no_priority_slot": flat_rep,
                              "exact_vs_one_at_a_time": exact}
+    # the NTT form through the same loop: every request forced to NTT (the cost
+    # model never picks it for this mix), served against one at a time
+    ntt_rows = {}
+    if args.served_ntt > 0:
+        for r in [float(x) for x in args.served_ntt_rates.split(",")]:
+            lst = workloads.served_requests(r, args.served_ntt)
+            srv.load_pool([sh for _, sh in lst])
+            forms = [zc.ZC_FORM_NTT] * len(lst)
+            reqs = srv.build(lst, forms)
+            rep = serve.report(reqs, srv.run(reqs))
+            launches += ctx.stats()[9]
+            base_reqs = one.build(lst, forms)
+            base = serve.report(base_reqs, one.run(base_reqs))
+            exact = all(a["proof"].cpu().numpy().tobytes() == b["proof"].cpu().numpy().tobytes()
+                        for a, b in zip(reqs, base_reqs))
+            ntt_rows[str(int(r))] = {"served": rep, "one_at_a_time": base, "exact_vs_one_at_a_time": exact}
     clk = clocks.stop()
     mid = rows[str(int(rates[len(rates) // 2]))]["served"]
     config = {"workload": "served: Poisson arrivals, n uniform 12..24, d in {3 (Plonk), 8, 16 (product)}, "
@@ -715,6 +733,9 @@ def run_served(args, world, rank, local):
     line = _base_line(args, world, mid["p99_ms"], "ms", False, config)
     line["value_is"] = f"p99 latency at {int(rates[len(rates) // 2])} req/s"
     line["by_rate"] = rows
+    if ntt_rows:
+        line["ntt_forced_by_rate"] = ntt_rows
+        line["ntt_forced_requests_per_rate"] = args.served_ntt
     line["gpu_launches"] = int(launches)
     line["clocks"] = clk
     line["pool_setup_s"] = t_pool
@@ -749,6 +770,9 @@ def main():
                          "hash-based commitment around the ZeroCheck")
     ap.add_argument("--rates", default="50,100,200,500,1000,2000", help="served: arrival rates (req/s)")
     ap.add_argument("--requests", type=int, default=200, help="served: requests per rate")
+    ap.add_argument("--served-ntt", type=int, default=0,
+                    help="served: also run this many requests per rate with every request forced to the NTT form")
+    ap.add_argument("--served-ntt-rates", default="5,20", help="served: arrival rates of the forced-NTT runs")
     args = ap.parse_args()
     global N_LOG, GATE, DEG
     if args.n:
