@@ -33,15 +33,24 @@ from paper_2606_16146_gb300 import witness  # noqa: E402
 OUT = os.path.join(HERE, "oracle_digests.jsonl")
 
 # (form, gate, n, d, log_blowup, seed): the configuration sizes whose oracle
-# run is too long for the GPU test session.
+# run is too long for the GPU test session.  form 1 SumCheck, 2 NTT, 3 the
+# eq-factored SumCheck.
 #   configs: Plonk n = 20, 22 (seed 1000 + n); product gate n = 22,
 #   d in {2, 4, 8, 16, 32} (seed 2000 + d), both forms; the served mix's
 #   largest shapes at n = 24 (seed 6000 + d); Plonk n = 22 on the
 #   quotient-sized 2N domain.
+#   the sweep's other n = 22 rows: product d = 6 on 8N and 5N = 4N + N,
+#   Plonk and product d = 4 on 3N = 2N + N, the eq-factored Plonk proof;
+#   the family at n = 22 (sum gate, seed 7000 + 100 m + 10 d + n):
+#   g1g2g3g4 and g1g2+g3+g4+g5, both forms.
+_FAMILY = [((3 << 8) | 3, 2, 7000 + 300 + 20 + 22), (3, 4, 7000 + 40 + 22)]
 CASES = (
     [(1, 1, 22, 3, 0, 1022), (2, 1, 22, 3, 0, 1022), (2, 1, 22, 3, 1, 1022)]
     + [(form, 2, 22, d, 0, 2000 + d) for d in (2, 4, 8, 16, 32) for form in (1, 2)]
     + [(1, 2, 24, 8, 0, 6008), (1, 2, 24, 16, 0, 6016), (1, 1, 24, 3, 0, 6003), (2, 1, 24, 3, 0, 6003)]
+    + [(3, 1, 22, 3, 0, 1022), (2, 1, 22, 3, 257, 1022), (2, 2, 22, 4, 257, 2004),
+       (1, 2, 22, 6, 0, 2006), (2, 2, 22, 6, 0, 2006), (2, 2, 22, 6, 258, 2006)]
+    + [(form, g, 22, d, 0, seed) for g, d, seed in _FAMILY for form in (1, 2)]
 )
 # cheapest first, so an interrupted run still leaves the most records
 CASES = sorted(CASES, key=lambda c: (1 << c[2]) * (c[3] + 2) * (1 if c[0] == 1 else 8 * max(c[3], 4)))
@@ -66,8 +75,8 @@ def load(path: str = OUT) -> dict:
 def compute(form, gate, n, d, lb, seed) -> dict:
     cols = witness.generate(gate, n, d, seed)
     rec = {"form": form, "gate": gate, "n": n, "d": d, "log_blowup": lb, "seed": seed}
-    if form == 1:
-        proof = oracle.prove_sumcheck(gate, n, d, cols)
+    if form in (1, 3):
+        proof = (oracle.prove_sumcheck if form == 1 else oracle.prove_sumcheck_eq)(gate, n, d, cols)
         rec.update(proof_len=len(proof), proof_sha256=hashlib.sha256(proof).hexdigest())
     else:
         proof, q = oracle.prove_ntt(gate, n, d, cols, log_blowup=lb)

@@ -1,7 +1,9 @@
 """Configuration-size parity: the library's proofs and quotients equal the
 oracle's byte for byte at the workload sizes (Plonk n = 22 and 24, the
 product gate at n = 22 for every degree of the sweep d = 2..32, the served
-mix's n = 24 shapes), both forms.
+mix's n = 24 shapes, the sweep's 2N, 3N and 5N domains and the
+eq-factored proof at n = 22, two of the paper's polynomials at n = 22),
+both forms.
 
 The oracle's outputs at these sizes take it minutes, so they are stored as
 SHA-256 digests in ``golden/oracle_digests.jsonl``, written by
@@ -27,7 +29,7 @@ RECORDS = digests.load()
 
 def _ids(case):
     form, gate, n, d, lb, seed = case
-    return f"{'sc' if form == 1 else 'ntt'}-g{gate}-n{n}-d{d}" + (f"-lb{lb}" if lb else "")
+    return f"{ {1: 'sc', 2: 'ntt', 3: 'sceq'}[form]}-g{gate}-n{n}-d{d}" + (f"-lb{lb}" if lb else "")
 
 
 @pytest.fixture(scope="module")
@@ -45,8 +47,8 @@ def test_config_size_matches_oracle(ctx, case):
     form, gate, n, d, lb, seed = case
     cols = to_device(witness.generate(gate, n, d, seed))
     try:
-        if form == zc.ZC_FORM_SUMCHECK:
-            p = proof_bytes(ctx.prove_sumcheck(gate, n, d, cols))
+        if form in (zc.ZC_FORM_SUMCHECK, zc.ZC_FORM_SUMCHECK_EQ):
+            p = proof_bytes(ctx.prove_sumcheck(gate, n, d, cols, eq_factored=form == zc.ZC_FORM_SUMCHECK_EQ))
         else:
             q = torch.zeros(rec["q_len"], dtype=torch.uint8, device="cuda")
             p, _ = ctx.prove_ntt(gate, n, d, cols, q_out=q, log_blowup=lb)
