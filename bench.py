@@ -924,7 +924,7 @@ def main():
                           "phases_ms": [round(x, 4) for x in st_nt[:6]]}
         by_form["ntt"]["roofline_frac"] = by_form["ntt"]["roofline_ms"] / by_form["ntt"]["ms"]
     else:
-        by_form["ntt"] = {"status": "not built"}
+        by_form["ntt"] = {"status": "not run (--form sumcheck)" if args.form == "sumcheck" else "not built"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
