@@ -133,6 +133,7 @@ struct NttPassArgs {
   const fr* post_tab;
   uint32_t p_lbdiv;
   uint64_t p_hs, p_ls, p_ts;
+  uint32_t* err;          // if set: the pass reads the proof's input columns, and a value >= r sets bit 0
 };
 
 // radix-2/4/8 butterflies on x[0..R) in registers, X[k] = sum_r x[r] w_R^(rk)
@@ -275,6 +276,7 @@ __global__ void __launch_bounds__(TILE / 8, MINB) k_ntt_pass(NttPassArgs A) {
     const uint64_t b = b0 + w;
     const uint64_t a = (b >> A.in_lbdiv) * A.in_bs_hi + (b & in_bdiv_mask) * A.in_bs_lo + t * A.in_ts;
     fr x = ld_fr(in + a);
+    if (A.err && !fr_is_canonical(x)) atomicOr(A.err, 1u);
     if (A.pre == PRE_TAB) {
       x = fr_mul(x, ld_fr(A.pre_tab + b * A.pre_kb + t * A.pre_kt));
     } else if (A.pre == PRE_COSET) {
@@ -587,10 +589,14 @@ __global__ void __launch_bounds__(256) k_ntt_open(NttOpenArgs A, const DevConst*
     const uint32_t mcount = (uint32_t)((cnt + 31) / 32);
     fr acc = fr_zero();
     for (int32_t m = (int32_t)mcount - 1; m >= 0; m--) {
-      acc = fr_mul(acc, z32);
       const uint64_t k = base + lane + 32ull * (uint32_t)m;
-      if (k < len) acc = fr_add(acc, ld_fr(x + k));
+      const fr xk = k < len ? ld_fr(x + k) : fr_zero();
+      // while the warp's accumulators and values are all zero (the zero top
+      // of an honest quotient) the step would multiply zeros: skip it
+      if (__all_sync(0xffffffffu, fr_is_zero(acc) && fr_is_zero(xk))) continue;
+      acc = fr_add(fr_mul(acc, z32), xk);
     }
+    if (__all_sync(0xffffffffu, fr_is_zero(acc))) continue;
     acc = fr_mul(acc, zpow_of(A.zpow, base + lane, C->one));
     tot = fr_add(tot, acc);
   }
@@ -638,23 +644,6 @@ __global__ void k_ntt_final(NttFinalArgs A) {
       for (int b = 0; b < 4; b++) A.proof[4 + 4 * q + b] = (uint8_t)(hv[q] >> (8 * b));
     for (int b = 0; b < 32; b++) A.proof[20 + b] = A.qroot[b];
   }
-}
-
-struct NttCheckArgs {
-  const fr* col[kMaxCols];
-  uint64_t N;
-  int c;
-  NttState* st;
-};
-
-// canonical check of the input columns (a value >= r sets the error flag)
-__global__ void k_ntt_check(NttCheckArgs A) {
-  const int j = blockIdx.y;
-  uint32_t bad = 0;
-  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < A.N;
-       p += (uint64_t)gridDim.x * blockDim.x)
-    bad |= !fr_is_canonical(ld_fr(A.col[j] + p));
-  if (bad) atomicOr(&A.st->err, 1u);
 }
 
 __global__ void k_ntt_state_init(NttState* st) {
@@ -1144,6 +1133,7 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
     a.in_bs_lo = 1; a.in_ts = L1;      // element (i1, i2) read from e[i1 + L1 i2]
     a.out_bs_lo = L2; a.out_ts = 1;
     a.dft = T->dft_inv;
+    a.err = &dstate->err;              // every input element passes through here once
     a.post = POST_TW; a.tw_lo = T->wi_lo; a.tw_hi = T->wi_hi;
     a.tw_lbmod = l1; a.tw_shift = kLog30 - n;
     if (ST) {  // w_N^-(i1 k2) = tw_inv[i1 L2 + k2]
@@ -1152,6 +1142,9 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
     }
     return run_pass(ctx, st, a, j1 - j0, L1);
   };
+
+  k_ntt_state_init<<<1, 32, 0, st>>>(dstate);
+  ctx->launches++;
 
   // Host columns: uploaded one by one on a side stream; with two passes the
   // first N1 pass of column j starts as soon as column j has arrived.
@@ -1181,18 +1174,6 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
     }
   }
   ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[0], st));
-  k_ntt_state_init<<<1, 32, 0, st>>>(dstate);
-  ctx->launches++;
-  {
-    NttCheckArgs ca{};
-    for (int j = 0; j < c; j++) ca.col[j] = src[j];
-    ca.N = N;
-    ca.c = c;
-    ca.st = dstate;
-    uint32_t gx = (uint32_t)std::min<uint64_t>((N + 255) / 256, 64);
-    k_ntt_check<<<dim3(gx, c), 256, 0, st>>>(ca);
-    ctx->launches++;
-  }
   if (roots) {
     std::memcpy(ctx->pinned, roots, 32 * (size_t)c);
     ZC_CUDA_TRY(ctx, cudaMemcpyAsync(droots, ctx->pinned, 32 * (size_t)c, cudaMemcpyHostToDevice, st));
@@ -1249,6 +1230,7 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
     a.in_bs_lo = 0; a.in_ts = 1;
     a.out_bs_lo = 0; a.out_ts = 1;
     a.dft = T->dft_inv;
+    a.err = &dstate->err;
     if ((rs = run_pass(ctx, st, a, c, 1)) != ZC_OK) return rs;
   }
   ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[2], st));
