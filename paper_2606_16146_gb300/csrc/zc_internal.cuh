@@ -211,6 +211,9 @@ zc_status pcs_hash_tree(zc_ctx* ctx, const fr* const* enc, int c, uint64_t m, ui
 void static_constants(DevConst* C, std::vector<fr>* tabs);
 
 // v2: the eq-factored form (rounds carry H_i(0..d), transcript v2)
+// The context's side stream for host-to-device copies and at least n events
+// on it (created on first use, destroyed with the context).
+zc_status ensure_upload_stream(zc_ctx* ctx, int n);
 zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, int on_dev,
                          const uint8_t (*roots)[32], cudaStream_t st, uint8_t* proof,
                          bool proof_on_dev, bool v2 = false);

@@ -878,7 +878,7 @@ size_t ntt_scratch_bytes(const zc_params* p, int sm_count, bool q_direct) {
 
 // Side stream and per-column events for pipelined uploads of host columns
 // (created on first use, freed by zc_destroy).
-static zc_status ensure_upload_stream(zc_ctx* ctx, int c) {
+zc_status ensure_upload_stream(zc_ctx* ctx, int c) {
   if (!ctx->up_stream) {
     if (cudaStreamCreateWithFlags(&ctx->up_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->up_fork, cudaEventDisableTiming) != cudaSuccess) {

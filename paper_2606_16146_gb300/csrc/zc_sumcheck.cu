@@ -100,6 +100,9 @@ struct ScRoundArgs {
   uint32_t v2;         // eq-factored proof: rounds carry H_i(0..d), not G_i(0..d+1)
   int round_end;       // persistent round kernel: rounds [round, round_end)
   uint32_t spin_limit; // persistent round kernel: polls of a hand-off before giving up
+  uint64_t k0, k1;     // round 1 in pair-range launches: pairs [k0, k1) (k1 = 0: all h)
+  uint32_t cta0;       // ... this launch's first partial-sum slot
+  uint32_t nwork_total;  // ... CTAs over all the launches of the round (0: nwork)
   ScState* st;
   fr* partials;
   uint8_t* proof;
@@ -338,15 +341,16 @@ __device__ void sc_sum_partials(ChalSmem& S, const fr* partials, uint32_t nwork,
 __device__ void sc_finish_round(const ScRoundArgs& A, int np) {
   __shared__ bool am_last;
   __shared__ ChalSmem S;
+  const uint32_t total = A.nwork_total ? A.nwork_total : A.nwork;
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned prev = atomicAdd(&A.st->counter[A.round], 1u);
-    am_last = prev == A.nwork - 1;
+    am_last = prev == total - 1;
   }
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  sc_sum_partials(S, A.partials, A.nwork, np);
+  sc_sum_partials(S, A.partials, total, np);
   sc_challenge<true>(S, np, (int)A.d, A.round, A.st, A.proof, A.C, A.tabs, A.next_derives != 0, A.v2 != 0);
 }
 
@@ -723,20 +727,22 @@ __global__ void __launch_bounds__(256, MINB) k_sc_plonk_round(ScRoundArgs A) {
   const fr* elo = A.E + A.eq_lo[i];
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t T = (uint64_t)A.nwork * blockDim.x;
+  const uint64_t kend = A.k1 ? A.k1 : h;
   fr acc[NP];
 #pragma unroll
   for (int p = 0; p < NP; p++) acc[p] = fr_zero();
   const fr alpha = FIRST ? fr_zero() : A.st->alpha[i - 1];
   const uint32_t p0 = FIRST ? 0u : A.st->p0[i];
   uint32_t bad = 0;
-  for (uint64_t k = tid; k < h; k += T)
+  for (uint64_t k = A.k0 + tid; k < kend; k += T)
     plonk_pair<FIRST, false>(A.src, A.dst, A.C, k, h, alpha, p0, ld_fr(ehi + (k >> mlo)), acc, bad);
   if (FIRST && bad) atomicOr(&A.st->err, 1u);
-  // each thread handled pairs with one fixed low part k_lo
+  // each thread handled pairs with one fixed low part k_lo (k0 and T are
+  // multiples of 2^mlo)
   const fr wl = ld_fr(elo + (tid & ((1ull << mlo) - 1)));
 #pragma unroll
   for (int p = 0; p < NP; p++) acc[p] = fr_mul(acc[p], wl);
-  block_sum<NP>(acc, A.partials + (size_t)blockIdx.x * NP);
+  block_sum<NP>(acc, A.partials + (size_t)(A.cta0 + blockIdx.x) * NP);
   sc_finish_round(A, NP);
 }
 
@@ -886,7 +892,8 @@ __global__ void __launch_bounds__(256, PP == 1 ? 3 : 2) k_sc_prod_round(ScRoundA
     tpt[p] = p < pcnt ? prod_point(pbeg + p, np, full, p0) : 0u;
   }
   if (slot < spb) {
-    for (uint64_t k = (uint64_t)blockIdx.x * spb + slot; k < A.h; k += (uint64_t)A.nwork * spb) {
+    const uint64_t kend = A.k1 ? A.k1 : A.h;
+    for (uint64_t k = A.k0 + (uint64_t)blockIdx.x * spb + slot; k < kend; k += (uint64_t)A.nwork * spb) {
       const fr w = fr_mul(ld_fr(ehi + (k >> mlo)), ld_fr(elo + (k & ((1ull << mlo) - 1))));
       prod_pair<PP, false>(A, A.src, k, A.h, pcnt, tpt, first && g == 0, w, acc, bad);
     }
@@ -896,7 +903,7 @@ __global__ void __launch_bounds__(256, PP == 1 ? 3 : 2) k_sc_prod_round(ScRoundA
 #pragma unroll
   for (int p = 0; p < PP; p++) red[threadIdx.x][p] = acc[p];
   __syncthreads();
-  prod_cta_sums<PP>(red, np, G, spb, A.partials + (size_t)blockIdx.x * np);
+  prod_cta_sums<PP>(red, np, G, spb, A.partials + (size_t)(A.cta0 + blockIdx.x) * np);
   __syncthreads();
   sc_finish_round(A, np);
 }
@@ -1090,6 +1097,7 @@ struct ScPlan {
   int minb;  // Plonk round kernels: resident CTAs per SM they are compiled for
   int ppt;   // product round kernel: points per thread (1 or kPP; 0: by round, prod_ppt)
   uint64_t fuse_pairs;  // product rounds 2.. with at most this many pairs fold inside the evaluation
+  int upload_chunks = 0;  // round 1 in this many pair-range launches (host columns), 0: one launch
   uint32_t eq_total, eq_hi[kMaxN], eq_lo[kMaxN], mlo[kMaxN];
   EqTask tasks[2 * kMaxN];
 };
@@ -1186,9 +1194,26 @@ static ScPlan sc_plan(const zc_params* p, int SMs, int grid = 0, int tail_log = 
 }
 
 static size_t sc_partials_count(const ScPlan& P) {
-  return (size_t)(std::max(std::max(P.grid_plonk, P.grid_prod), std::max(P.grid_chunk, P.grid_quad)) + 1) *
-         (P.npmax + 1);
+  const size_t g = (size_t)std::max(std::max(P.grid_plonk, P.grid_prod), std::max(P.grid_chunk, P.grid_quad));
+  return (g * (size_t)std::max(1, P.upload_chunks) + 1) * (P.npmax + 1);
 }
+
+// Host columns of a large instance are copied in kUploadChunks pair ranges
+// (rows [a, a + h/K) and [h + a, h + a + h/K) of every column), and round 1
+// runs on each range as soon as it has landed, so the copy overlaps it.
+constexpr int kUploadChunks = 8;
+constexpr uint32_t kUploadMinN = 18;
+
+static bool sc_upload_chunkable(const zc_params* p) { return p->n >= kUploadMinN; }
+
+struct ScUpload {
+  const void* const* cols;  // host columns (canonical, N * 32 bytes each)
+  int chunks;
+  uint64_t hc;              // pairs per range
+  cudaStream_t stream;
+  cudaEvent_t fork;
+  const cudaEvent_t* ev;    // one per range
+};
 
 // Carve the proof's buffers from an arena; false when it is too small.
 static bool sc_carve(Arena& ar, const ScPlan& P, uint64_t N, size_t psize, ScBuffers& B) {
@@ -1232,11 +1257,29 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
                             const ScBuffers& B, const DevConst* dC, const fr* dtabs,
                             const DevConst& hC, int skip_point, cudaStream_t st,
                             uint32_t* launches, cudaEvent_t* ev, bool v2 = false,
-                            bool persistent = false) {
+                            bool persistent = false, const ScUpload* up = nullptr) {
   const uint32_t gate = p->gate, n = p->n, d = p->d;
   const int c = P.c;
   const uint64_t N = 1ull << n;
   const bool plonk = gate == ZC_GATE_PLONK;
+  if (up) {  // the copies start at once, behind earlier work on st
+    if (cudaEventRecord(up->fork, st) != cudaSuccess || cudaStreamWaitEvent(up->stream, up->fork, 0) != cudaSuccess)
+      return ZC_ERR_CUDA;
+  }
+  // range q of the host columns to the tables, then st waits for it
+  auto upload_range = [&](int q) -> bool {
+    const uint64_t h0 = N / 2, a = (uint64_t)q * up->hc;
+    for (int j = 0; j < c; j++) {
+      const char* hs = static_cast<const char*>(up->cols[j]);
+      if (cudaMemcpyAsync(B.tab[j] + a, hs + a * sizeof(fr), up->hc * sizeof(fr), cudaMemcpyHostToDevice,
+                          up->stream) != cudaSuccess ||
+          cudaMemcpyAsync(B.tab[j] + h0 + a, hs + (h0 + a) * sizeof(fr), up->hc * sizeof(fr),
+                          cudaMemcpyHostToDevice, up->stream) != cudaSuccess)
+        return false;
+    }
+    return cudaEventRecord(up->ev[q], up->stream) == cudaSuccess &&
+           cudaStreamWaitEvent(st, up->ev[q], 0) == cudaSuccess;
+  };
   ScSetupArgs sa{};
   sa.st = B.st;
   sa.roots = B.roots;
@@ -1342,7 +1385,25 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
       *launches += 1;
     } else if (plonk) {
       R.nwork = (uint32_t)std::min<uint64_t>((h + 255) / 256, (uint64_t)P.grid_plonk);
-      if (i == 0) {
+      if (i == 0 && up) {
+        const uint32_t nwc = (uint32_t)std::min<uint64_t>((up->hc + 255) / 256, (uint64_t)P.grid_plonk);
+        R.nwork = nwc;
+        R.nwork_total = nwc * (uint32_t)up->chunks;
+        for (int q = 0; q < up->chunks; q++) {
+          if (!upload_range(q)) return ZC_ERR_CUDA;
+          R.k0 = (uint64_t)q * up->hc;
+          R.k1 = R.k0 + up->hc;
+          R.cta0 = (uint32_t)q * nwc;
+          const uint32_t g = nwc + (q == 0 ? inv_cta : 0u);
+          if (P.minb == 2) k_sc_plonk_round<true, 2><<<g, 256, 0, st>>>(R);
+          else k_sc_plonk_round<true, 1><<<g, 256, 0, st>>>(R);
+          *launches += 1;
+        }
+        *launches -= 1;  // counted once below
+        R.k0 = R.k1 = 0;
+        R.cta0 = R.nwork_total = 0;
+        for (int j = 5; j < 8; j++) cur[j] = B.tab[j];
+      } else if (i == 0) {
         if (P.minb == 2) k_sc_plonk_round<true, 2><<<R.nwork + inv_cta, 256, 0, st>>>(R);
         else k_sc_plonk_round<true, 1><<<R.nwork + inv_cta, 256, 0, st>>>(R);
         for (int j = 5; j < 8; j++) cur[j] = B.tab[j];
@@ -1391,10 +1452,29 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
       const uint64_t slots_per_blk = 256 / ((npr + ppt - 1) / ppt);
       R.spb = (uint32_t)slots_per_blk;
       R.nwork = (uint32_t)std::min<uint64_t>((h + slots_per_blk - 1) / slots_per_blk, (uint64_t)P.grid_prod);
-      const uint32_t ctas = R.nwork + (i == 0 ? inv_cta : 0u);
-      if (ppt == 1) k_sc_prod_round<1><<<ctas, 256, 0, st>>>(R);
-      else k_sc_prod_round<3><<<ctas, 256, 0, st>>>(R);
-      *launches += 1;
+      if (i == 0 && up) {
+        const uint32_t nwc =
+            (uint32_t)std::min<uint64_t>((up->hc + slots_per_blk - 1) / slots_per_blk, (uint64_t)P.grid_prod);
+        R.nwork = nwc;
+        R.nwork_total = nwc * (uint32_t)up->chunks;
+        for (int q = 0; q < up->chunks; q++) {
+          if (!upload_range(q)) return ZC_ERR_CUDA;
+          R.k0 = (uint64_t)q * up->hc;
+          R.k1 = R.k0 + up->hc;
+          R.cta0 = (uint32_t)q * nwc;
+          const uint32_t g = nwc + (q == 0 ? inv_cta : 0u);
+          if (ppt == 1) k_sc_prod_round<1><<<g, 256, 0, st>>>(R);
+          else k_sc_prod_round<3><<<g, 256, 0, st>>>(R);
+          *launches += 1;
+        }
+        R.k0 = R.k1 = 0;
+        R.cta0 = R.nwork_total = 0;
+      } else {
+        const uint32_t ctas = R.nwork + (i == 0 ? inv_cta : 0u);
+        if (ppt == 1) k_sc_prod_round<1><<<ctas, 256, 0, st>>>(R);
+        else k_sc_prod_round<3><<<ctas, 256, 0, st>>>(R);
+        *launches += 1;
+      }
     }
     if (i == 0 && ev) cudaEventRecord(ev[3], st);
   }
@@ -1425,7 +1505,9 @@ size_t sumcheck_scratch_bytes(const zc_ctx* ctx, const zc_params* p) {
                            ctx->tuned(ZC_FORM_SUMCHECK, p->n, ZC_TUNE_SC_PROD_FUSE));
   const uint64_t N = 1ull << p->n;
   const size_t psize = 16 + 32 * ((size_t)p->n * (p->d + 2) + P.c);
-  return align_up(sizeof(fr) * N, 256) * P.c + align_up(sizeof(fr) * sc_partials_count(P), 256) +
+  ScPlan Pc = P;
+  if (sc_upload_chunkable(p)) Pc.upload_chunks = kUploadChunks;  // host columns may come in ranges
+  return align_up(sizeof(fr) * N, 256) * P.c + align_up(sizeof(fr) * sc_partials_count(Pc), 256) +
          align_up(sizeof(fr) * P.eq_total, 256) + align_up(sizeof(ScState), 256) + align_up(psize, 256) +
          align_up(32 * (size_t)P.c, 256) + 4096 + root_scratch_bytes(P.c, N);
 }
@@ -1445,18 +1527,41 @@ zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* col
   const int c = P.c;
   const uint64_t N = 1ull << n;
   const size_t psize = 16 + 32 * ((size_t)n * (v2 ? d + 1 : d + 2) + c);
+  // Host columns with their roots given: copied in pair ranges beside round 1.
+  // The Plonk round kernel takes a pair's low eq factor from its thread
+  // index, so a range start and the launch's thread count must be multiples
+  // of the low table's length.
+  const uint64_t hc = (N / 2) / kUploadChunks;
+  bool chunked = !on_dev && roots && sc_upload_chunkable(p);
+  if (chunked && p->gate == ZC_GATE_PLONK) {
+    const uint64_t nwc = std::min<uint64_t>((hc + 255) / 256, (uint64_t)P.grid_plonk), m = 1ull << P.mlo[0];
+    chunked = (nwc * 256) % m == 0 && hc % m == 0;
+  }
+  ScPlan Pm = P;
+  if (chunked) Pm.upload_chunks = kUploadChunks;
   zc_status s = ensure_arena(ctx, sumcheck_scratch_bytes(ctx, p));
   if (s != ZC_OK) return s;
   Arena& ar = ctx->arena;
   ar.reset();
   ScBuffers B{};
-  if (!sc_carve(ar, P, N, psize, B)) {
+  if (!sc_carve(ar, Pm, N, psize, B)) {
     ctx->err = "scratch arena too small";
     return ZC_ERR_OOM;
   }
   const fr* src[kMaxCols];
+  ScUpload up{};
   if (on_dev) {
     for (int j = 0; j < c; j++) src[j] = reinterpret_cast<const fr*>(cols[j]);
+  } else if (chunked) {
+    s = ensure_upload_stream(ctx, kUploadChunks);
+    if (s != ZC_OK) return s;
+    up.cols = cols;
+    up.chunks = kUploadChunks;
+    up.hc = hc;
+    up.stream = ctx->up_stream;
+    up.fork = ctx->up_fork;
+    up.ev = ctx->up_ev.data();
+    for (int j = 0; j < c; j++) src[j] = B.tab[j];
   } else {
     for (int j = 0; j < c; j++) {
       ZC_CUDA_TRY(ctx, cudaMemcpyAsync(B.tab[j], cols[j], N * sizeof(fr), cudaMemcpyHostToDevice, st));
@@ -1481,8 +1586,8 @@ zc_status sumcheck_prove(zc_ctx* ctx, const zc_params* p, const void* const* col
   }
   ZC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev[1], st));
   uint32_t launches = 0;
-  s = sc_enqueue(p, P, src, B, ctx->dconst, ctx->dtabs, ctx->hconst, ctx->skip_point, st, &launches,
-                 ctx->ev, v2, persistent_allowed(ctx, st));
+  s = sc_enqueue(p, Pm, src, B, ctx->dconst, ctx->dtabs, ctx->hconst, ctx->skip_point, st, &launches,
+                 ctx->ev, v2, persistent_allowed(ctx, st), chunked ? &up : nullptr);
   ctx->launches += launches;
   if (s != ZC_OK) {
     ctx->err = "kernel launch failed";

@@ -54,6 +54,29 @@ def test_host_device_inputs_and_given_roots(ctx, device, roots):
     _check(ctx, 2, 12, 5, 6, device=device, roots=roots)
 
 
+@pytest.mark.parametrize("gate,n,d,seed,tamper", [(1, 18, 3, 1018, False), (1, 20, 3, 1020, False),
+                                                   (2, 18, 2, 2102, False), (2, 19, 5, 2105, False),
+                                                   (1, 18, 3, 91, True)])
+def test_host_columns_in_ranges(ctx, gate, n, d, seed, tamper):
+    """Host columns from n = 18 on, with their roots given, are copied in
+    pair ranges while round 1 runs on the ranges already copied (one
+    round-1 launch per range): the bytes equal the oracle's."""
+    _check(ctx, gate, n, d, seed, tamper=tamper, device=False, roots=True)
+
+
+def test_host_columns_in_ranges_eq_factored_and_rejection(ctx):
+    gate, n, d = 1, 18, 3
+    cols = witness.generate(gate, n, d, 1018)
+    rts = [oracle.root(c) for c in cols]
+    got = ctx.prove_sumcheck(gate, n, d, cols, roots=rts, eq_factored=True)
+    assert proof_bytes(got) == oracle.prove_sumcheck_eq(gate, n, d, cols)
+    bad = [np.array(c, copy=True) for c in cols]
+    bad[6][32 * ((1 << n) - 3) + 31] = 0xf7          # a value >= r in the last range
+    with pytest.raises(zc.ZCError) as e:
+        ctx.prove_sumcheck(gate, n, d, bad, roots=rts)
+    assert e.value.status == 1
+
+
 def test_device_proof_buffer_async(ctx):
     import torch
     gate, n, d = 1, 12, 3
