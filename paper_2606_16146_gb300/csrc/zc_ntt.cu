@@ -1142,6 +1142,20 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
     }
     return run_pass(ctx, st, a, j1 - j0, L1);
   };
+  // N1's second pass (columns of length L1, in place) for the columns [j0, j1)
+  auto n1_second = [&](int j0, int j1) -> zc_status {
+    NttPassArgs a;
+    pass_defaults(a);
+    for (int j = j0; j < j1; j++) {
+      a.in[j - j0] = coef[j];
+      a.out[j - j0] = coef[j];
+    }
+    a.logL = l1;
+    a.in_bs_lo = 1; a.in_ts = L2;
+    a.out_bs_lo = 1; a.out_ts = L2;
+    a.dft = T->dft_inv;
+    return run_pass(ctx, st, a, j1 - j0, L2);
+  };
 
   k_ntt_state_init<<<1, 32, 0, st>>>(dstate);
   ctx->launches++;
@@ -1208,17 +1222,7 @@ zc_status ntt_prove(zc_ctx* ctx, const zc_params* p, const void* const* cols, in
   // ---- N1: g_j = DFT^-1(e_j) (the factor 1/N is applied later), natural out
   if (two) {
     if (!pipelined && (rs = n1_first(src, 0, c)) != ZC_OK) return rs;
-    NttPassArgs a;
-    pass_defaults(a);
-    for (int j = 0; j < c; j++) {
-      a.in[j] = coef[j];
-      a.out[j] = coef[j];
-    }
-    a.logL = l1;                       // columns of length L1
-    a.in_bs_lo = 1; a.in_ts = L2;
-    a.out_bs_lo = 1; a.out_ts = L2;
-    a.dft = T->dft_inv;
-    if ((rs = run_pass(ctx, st, a, c, L2)) != ZC_OK) return rs;
+    if ((rs = n1_second(0, c)) != ZC_OK) return rs;  // all columns in one launch
   } else {
     NttPassArgs a;
     pass_defaults(a);

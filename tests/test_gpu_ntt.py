@@ -64,6 +64,25 @@ def test_buffers(ctx, device, roots, q_device):
     _check(ctx, 1, 14, 3, 14, device=device, roots=roots, q_device=q_device)
 
 
+@pytest.mark.parametrize("gate,n,d,seed", [(1, 18, 3, 1018), (2, 17, 5, 2017)])
+def test_host_columns_pipelined(ctx, gate, n, d, seed):
+    """Host columns at two-pass sizes: each column's N1 passes start as soon as
+    that column has been copied; the bytes equal the oracle's."""
+    _check(ctx, gate, n, d, seed, device=False, roots=True)
+
+
+@pytest.mark.parametrize("where", [0, -1])
+def test_noncanonical_rejected_two_pass(ctx, where):
+    """A value >= r in the first or the last host column at a two-pass size
+    (the check rides in N1's first pass)."""
+    gate, n, d = 1, 14, 3
+    cols = [np.array(c, copy=True) for c in witness.generate(gate, n, d, 4)]
+    cols[where][32 * 100 + 31] = 0xf3
+    with pytest.raises(zc.ZCError) as e:
+        ctx.prove_ntt(gate, n, d, cols)
+    assert e.value.status == 1
+
+
 def test_noncanonical_rejected(ctx):
     gate, n, d = 1, 6, 3
     cols = witness.generate(gate, n, d, 3)
