@@ -199,6 +199,84 @@ ZC_D fr fr_add(const fr& a, const fr& b) {
   return s;
 }
 
+// Lazily reduced sum and difference of canonical a, b: results in [0, 2r)
+// (2r < 2^256) without the conditional correction.  Such a value may be the
+// SECOND operand of fr_mul: its rows run over b's limbs with a < r, so every
+// row stays below 2r + 1 and the product below 2r before its final
+// subtraction, whatever b < 2^256 is.  fr_reduce1 brings it to [0, r).
+ZC_D fr fr_add_lazy(const fr& a, const fr& b) {
+  fr s;
+  asm("add.cc.u32 %0, %8, %16;\n\t"
+      "addc.cc.u32 %1, %9, %17;\n\t"
+      "addc.cc.u32 %2, %10, %18;\n\t"
+      "addc.cc.u32 %3, %11, %19;\n\t"
+      "addc.cc.u32 %4, %12, %20;\n\t"
+      "addc.cc.u32 %5, %13, %21;\n\t"
+      "addc.cc.u32 %6, %14, %22;\n\t"
+      "addc.u32 %7, %15, %23;"
+      : "=r"(s.v[0]), "=r"(s.v[1]), "=r"(s.v[2]), "=r"(s.v[3]), "=r"(s.v[4]), "=r"(s.v[5]),
+        "=r"(s.v[6]), "=r"(s.v[7])
+      : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]),
+        "r"(a.v[6]), "r"(a.v[7]), "r"(b.v[0]), "r"(b.v[1]), "r"(b.v[2]), "r"(b.v[3]),
+        "r"(b.v[4]), "r"(b.v[5]), "r"(b.v[6]), "r"(b.v[7]));
+  return s;
+}
+
+// a - b + r mod 2^256, in (0, 2r) for canonical a, b
+ZC_D fr fr_sub_lazy(const fr& a, const fr& b) {
+  fr s;
+  asm("sub.cc.u32 %0, %8, %16;\n\t"
+      "subc.cc.u32 %1, %9, %17;\n\t"
+      "subc.cc.u32 %2, %10, %18;\n\t"
+      "subc.cc.u32 %3, %11, %19;\n\t"
+      "subc.cc.u32 %4, %12, %20;\n\t"
+      "subc.cc.u32 %5, %13, %21;\n\t"
+      "subc.cc.u32 %6, %14, %22;\n\t"
+      "subc.u32 %7, %15, %23;"
+      : "=r"(s.v[0]), "=r"(s.v[1]), "=r"(s.v[2]), "=r"(s.v[3]), "=r"(s.v[4]), "=r"(s.v[5]),
+        "=r"(s.v[6]), "=r"(s.v[7])
+      : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]),
+        "r"(a.v[6]), "r"(a.v[7]), "r"(b.v[0]), "r"(b.v[1]), "r"(b.v[2]), "r"(b.v[3]),
+        "r"(b.v[4]), "r"(b.v[5]), "r"(b.v[6]), "r"(b.v[7]));
+  asm("add.cc.u32 %0, %0, %8;\n\t"
+      "addc.cc.u32 %1, %1, %9;\n\t"
+      "addc.cc.u32 %2, %2, %10;\n\t"
+      "addc.cc.u32 %3, %3, %11;\n\t"
+      "addc.cc.u32 %4, %4, %12;\n\t"
+      "addc.cc.u32 %5, %5, %13;\n\t"
+      "addc.cc.u32 %6, %6, %14;\n\t"
+      "addc.u32 %7, %7, %15;"
+      : "+r"(s.v[0]), "+r"(s.v[1]), "+r"(s.v[2]), "+r"(s.v[3]), "+r"(s.v[4]), "+r"(s.v[5]),
+        "+r"(s.v[6]), "+r"(s.v[7])
+      : "n"(ZC_P0), "n"(ZC_P1), "n"(ZC_P2), "n"(ZC_P3), "n"(ZC_P4), "n"(ZC_P5), "n"(ZC_P6),
+        "n"(ZC_P7));
+  return s;
+}
+
+// x - r when x >= r, for x < 2r
+ZC_D fr fr_reduce1(const fr& x) {
+  fr t;
+  uint32_t bw;
+  asm("sub.cc.u32 %0, %9, %17;\n\t"
+      "subc.cc.u32 %1, %10, %18;\n\t"
+      "subc.cc.u32 %2, %11, %19;\n\t"
+      "subc.cc.u32 %3, %12, %20;\n\t"
+      "subc.cc.u32 %4, %13, %21;\n\t"
+      "subc.cc.u32 %5, %14, %22;\n\t"
+      "subc.cc.u32 %6, %15, %23;\n\t"
+      "subc.cc.u32 %7, %16, %24;\n\t"
+      "subc.u32 %8, 0, 0;"
+      : "=r"(t.v[0]), "=r"(t.v[1]), "=r"(t.v[2]), "=r"(t.v[3]), "=r"(t.v[4]), "=r"(t.v[5]),
+        "=r"(t.v[6]), "=r"(t.v[7]), "=r"(bw)
+      : "r"(x.v[0]), "r"(x.v[1]), "r"(x.v[2]), "r"(x.v[3]), "r"(x.v[4]), "r"(x.v[5]),
+        "r"(x.v[6]), "r"(x.v[7]), "n"(ZC_P0), "n"(ZC_P1), "n"(ZC_P2), "n"(ZC_P3), "n"(ZC_P4),
+        "n"(ZC_P5), "n"(ZC_P6), "n"(ZC_P7));
+  fr r;
+#pragma unroll
+  for (int i = 0; i < 8; i++) r.v[i] = bw ? x.v[i] : t.v[i];
+  return r;
+}
+
 ZC_D fr fr_sub(const fr& a, const fr& b) {
   fr s;
   uint32_t bw;

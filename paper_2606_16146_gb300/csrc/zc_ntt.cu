@@ -136,33 +136,40 @@ struct NttPassArgs {
   uint32_t* err;          // if set: the pass reads the proof's input columns, and a value >= r sets bit 0
 };
 
-// radix-2/4/8 butterflies on x[0..R) in registers, X[k] = sum_r x[r] w_R^(rk)
+// radix-2/4/8 butterflies on x[0..R) in registers, X[k] = sum_r x[r] w_R^(rk).
+// Inputs are canonical.  A value that only feeds a multiplication (as
+// fr_mul's second operand, which may be any value below 2r) is left lazily
+// reduced in [0, 2r): the stage outputs (the next stage multiplies all but
+// one of them by its twiddle and reduces that one, the pass's store reduces
+// or multiplies every one), and the terms multiplied by w_4, w_8, w_8^3.
+// OUT: 0 every output canonical, 1 a0 canonical and a1..a3 lazy, 2 all lazy.
+template <int OUT>
 __device__ __forceinline__ void dft4(fr& a0, fr& a1, fr& a2, fr& a3, const fr& w4) {
-  fr u0 = fr_add(a0, a2), u1 = fr_sub(a0, a2);
-  fr v0 = fr_add(a1, a3), v1 = fr_mul(fr_sub(a1, a3), w4);
-  a0 = fr_add(u0, v0);
-  a2 = fr_sub(u0, v0);
-  a1 = fr_add(u1, v1);
-  a3 = fr_sub(u1, v1);
+  const fr u0 = fr_add(a0, a2), u1 = fr_sub(a0, a2);
+  const fr v0 = fr_add(a1, a3), v1 = fr_mul(w4, fr_sub_lazy(a1, a3));
+  a0 = OUT == 2 ? fr_add_lazy(u0, v0) : fr_add(u0, v0);
+  a2 = OUT >= 1 ? fr_sub_lazy(u0, v0) : fr_sub(u0, v0);
+  a1 = OUT >= 1 ? fr_add_lazy(u1, v1) : fr_add(u1, v1);
+  a3 = OUT >= 1 ? fr_sub_lazy(u1, v1) : fr_sub(u1, v1);
 }
 
+// outputs lazy
 __device__ __forceinline__ void dft8(fr (&x)[8], const fr* tab) {
-  const fr w4 = ld_fr(tab + 1024), w8 = ld_fr(tab + 512), w83 = ld_fr(tab + 1536);
   fr e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
   fr o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
-  dft4(e0, e1, e2, e3, w4);
-  dft4(o0, o1, o2, o3, w4);
-  o1 = fr_mul(o1, w8);
-  o2 = fr_mul(o2, w4);
-  o3 = fr_mul(o3, w83);
-  x[0] = fr_add(e0, o0);
-  x[4] = fr_sub(e0, o0);
-  x[1] = fr_add(e1, o1);
-  x[5] = fr_sub(e1, o1);
-  x[2] = fr_add(e2, o2);
-  x[6] = fr_sub(e2, o2);
-  x[3] = fr_add(e3, o3);
-  x[7] = fr_sub(e3, o3);
+  dft4<0>(e0, e1, e2, e3, ld_fr(tab + 1024));
+  dft4<1>(o0, o1, o2, o3, ld_fr(tab + 1024));
+  o1 = fr_mul(ld_fr(tab + 512), o1);    // w_8
+  o2 = fr_mul(ld_fr(tab + 1024), o2);   // w_4
+  o3 = fr_mul(ld_fr(tab + 1536), o3);   // w_8^3
+  x[0] = fr_add_lazy(e0, o0);
+  x[4] = fr_sub_lazy(e0, o0);
+  x[1] = fr_add_lazy(e1, o1);
+  x[5] = fr_sub_lazy(e1, o1);
+  x[2] = fr_add_lazy(e2, o2);
+  x[6] = fr_sub_lazy(e2, o2);
+  x[3] = fr_add_lazy(e3, o3);
+  x[7] = fr_sub_lazy(e3, o3);
 }
 
 // The CTA tile in shared memory: element i's two 16-byte halves live in two
@@ -218,10 +225,12 @@ __device__ __forceinline__ void stockham_stage(const SmTile& sm, uint32_t logL, 
     const uint32_t j = jj[g];
     const uint32_t k = j & ((1u << logNs) - 1);
     if (logNs > 0) {
-      // twiddle w_{Ns R}^{r k} = tab[r k 4096 / (Ns R)]
+      // the previous stage left its outputs lazy: x[0] is reduced, the
+      // others are reduced by their twiddle w_{Ns R}^{r k} = tab[r k 4096 / (Ns R)]
       const uint32_t sh = 12 - (logNs + LR);
+      x[g * R] = fr_reduce1(x[g * R]);
 #pragma unroll
-      for (int r = 1; r < R; r++) x[g * R + r] = fr_mul(x[g * R + r], ld_fr(tab + ((r * k) << sh)));
+      for (int r = 1; r < R; r++) x[g * R + r] = fr_mul(ld_fr(tab + ((r * k) << sh)), x[g * R + r]);
     }
     if (R == 8) {
       fr y[8];
@@ -231,11 +240,11 @@ __device__ __forceinline__ void stockham_stage(const SmTile& sm, uint32_t logL, 
 #pragma unroll
       for (int r = 0; r < 8; r++) x[r] = y[r];
     } else if (R == 4) {
-      dft4(x[g * 4], x[g * 4 + 1], x[g * 4 + 2], x[g * 4 + 3], ld_fr(tab + 1024));
+      dft4<2>(x[g * 4], x[g * 4 + 1], x[g * 4 + 2], x[g * 4 + 3], ld_fr(tab + 1024));
     } else {
       fr a = x[g * 2], b = x[g * 2 + 1];
-      x[g * 2] = fr_add(a, b);
-      x[g * 2 + 1] = fr_sub(a, b);
+      x[g * 2] = fr_add_lazy(a, b);
+      x[g * 2 + 1] = fr_sub_lazy(a, b);
     }
   }
 #pragma unroll
@@ -305,24 +314,26 @@ __global__ void __launch_bounds__(TILE / 8, MINB) k_ntt_pass(NttPassArgs A) {
     if (out_t_fast) { t = idx & (L - 1); w = idx >> logL; }
     else { w = idx & (W - 1); t = idx >> logW; }
     const uint64_t b = b0 + w;
-    fr y = sm.get(t * W + w);
+    fr y = sm.get(t * W + w);  // lazily reduced: multiplied (as the second operand) or reduced here
     if (A.post == POST_TAB) {
       const uint64_t ti = (b >> A.p_lbdiv) * A.p_hs + (b & ((1ull << A.p_lbdiv) - 1)) * A.p_ls + t * A.p_ts;
-      y = fr_mul(y, ld_fr(A.post_tab + ti));
+      y = fr_mul(ld_fr(A.post_tab + ti), y);
     } else if (A.post == POST_TW) {
       const uint64_t e = (b & ((1ull << A.tw_lbmod) - 1)) * t;
       const uint32_t ex = (uint32_t)((e << A.tw_shift) & ((1ull << kLog30) - 1));
-      if (ex) y = fr_mul(y, root_pow(A.tw_lo, A.tw_hi, ex));
+      y = ex ? fr_mul(root_pow(A.tw_lo, A.tw_hi, ex), y) : fr_reduce1(y);
     } else if (A.post == POST_OUTER) {
       const uint64_t jsl = b >> A.outer_lbdiv;
       const uint64_t kp = ((uint64_t)t << A.outer_lbdiv) + (b & ((1ull << A.outer_lbdiv) - 1));
       const uint64_t e = jsl * kp;
       const uint32_t ex = (uint32_t)((e << A.tw_shift) & ((1ull << kLog30) - 1));
-      if (ex) y = fr_mul(y, root_pow(A.tw_lo, A.tw_hi, ex));
+      y = ex ? fr_mul(root_pow(A.tw_lo, A.tw_hi, ex), y) : fr_reduce1(y);
     } else if (A.post == POST_FINAL) {
       const uint64_t k = A.fin_N * t + b;
       fr f = fr_mul(ld_fr(A.tw_hi + (k >> kLoBits)), ld_fr(A.tw_lo + (k & kLoMask)));  // level 0
-      y = fr_mul(y, f);
+      y = fr_mul(f, y);
+    } else {
+      y = fr_reduce1(y);
     }
     const uint64_t a = (b >> A.out_lbdiv) * A.out_bs_hi + (b & out_bdiv_mask) * A.out_bs_lo + t * A.out_ts;
     st_fr(out + a, y);
