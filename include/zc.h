@@ -137,7 +137,9 @@ zc_status zc_proof_size(const zc_params* params, zc_form form, size_t* bytes);
 /* SumCheck-form ZeroCheck proof (Fig. side-by-side-zc right; Sec. 3.3).
  * cols: c pointers to N*32-byte canonical columns, device pointers when
  * cols_on_device != 0, host pointers otherwise (copied to the device inside
- * the call).  col_roots: the c column commitments root(col_j) if the caller
+ * the call; from n = 18 on, with col_roots given, in eight pair ranges on the
+ * context's copy stream while round 1 runs on the ranges already copied, so
+ * pinned host memory lets the copy overlap the proof).  col_roots: the c column commitments root(col_j) if the caller
  * has them (stage (1) of the prover workflow, Sec. 3.1), or NULL to compute
  * them on the device.  cuda_stream: a cudaStream_t (NULL = legacy default).
  * proof: cap bytes, host or device memory; *len receives the proof size.
