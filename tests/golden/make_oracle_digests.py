@@ -7,8 +7,9 @@ here by the CPU oracle (``oracle/``) on the seeded witness of
 ``paper_2606_16146_gb300.witness``; nothing else is called.
 
 Record format (one JSON object per line of ``oracle_digests.jsonl``):
-  form (1 SumCheck, 2 NTT), gate, n, d, log_blowup (NTT; 0 = default),
-  seed, proof_len, proof_sha256, q_len, q_sha256 (NTT only).
+  form (1 SumCheck, 2 NTT, 3 eq-factored SumCheck, 5 commitment), gate, n,
+  d, log_blowup (NTT; 0 = default; the query count for form 5), seed,
+  proof_len, proof_sha256, q_len, q_sha256 (NTT only), root (form 5).
 
 Usage (repository root):
   python tests/golden/make_oracle_digests.py            # every missing case
@@ -42,7 +43,10 @@ OUT = os.path.join(HERE, "oracle_digests.jsonl")
 #   the sweep's other n = 22 rows: product d = 6 on 8N and 5N = 4N + N,
 #   Plonk and product d = 4 on 3N = 2N + N, the eq-factored Plonk proof;
 #   the family at n = 22 (sum gate, seed 7000 + 100 m + 10 d + n):
-#   g1g2g3g4 and g1g2+g3+g4+g5, both forms.
+#   g1g2g3g4 and g1g2+g3+g4+g5, both forms;
+#   form 5: the hash-based commitment of the bench's Plonk n = 22 columns
+#   (root, and the opening at PCS_ALPHA to PCS_VALUES with t queries; t sits
+#   in the log_blowup slot).
 _FAMILY = [((3 << 8) | 3, 2, 7000 + 300 + 20 + 22), (3, 4, 7000 + 40 + 22)]
 CASES = (
     [(1, 1, 22, 3, 0, 1022), (2, 1, 22, 3, 0, 1022), (2, 1, 22, 3, 1, 1022)]
@@ -51,7 +55,16 @@ CASES = (
     + [(3, 1, 22, 3, 0, 1022), (2, 1, 22, 3, 257, 1022), (2, 2, 22, 4, 257, 2004),
        (1, 2, 22, 6, 0, 2006), (2, 2, 22, 6, 0, 2006), (2, 2, 22, 6, 258, 2006)]
     + [(form, g, 22, d, 0, seed) for g, d, seed in _FAMILY for form in (1, 2)]
+    + [(5, 1, 22, 3, 189, 1022)]
 )
+
+
+def pcs_point(n: int, c: int):
+    """The opening point and claimed values of the commitment records: small
+    integers (any values give well-defined opening bytes)."""
+    alpha = [oracle.ints_to_bytes([x]).tobytes() for x in range(3, 3 + n)]
+    values = [oracle.ints_to_bytes([7 + j]).tobytes() for j in range(c)]
+    return alpha, values
 # cheapest first, so an interrupted run still leaves the most records
 CASES = sorted(CASES, key=lambda c: (1 << c[2]) * (c[3] + 2) * (1 if c[0] == 1 else 8 * max(c[3], 4)))
 
@@ -75,7 +88,12 @@ def load(path: str = OUT) -> dict:
 def compute(form, gate, n, d, lb, seed) -> dict:
     cols = witness.generate(gate, n, d, seed)
     rec = {"form": form, "gate": gate, "n": n, "d": d, "log_blowup": lb, "seed": seed}
-    if form in (1, 3):
+    if form == 5:
+        root = oracle.pcs_commit(n, cols)
+        alpha, values = pcs_point(n, len(cols))
+        proof = oracle.pcs_open(n, cols, alpha, values, lb)
+        rec.update(root=root.hex(), proof_len=len(proof), proof_sha256=hashlib.sha256(proof).hexdigest())
+    elif form in (1, 3):
         proof = (oracle.prove_sumcheck if form == 1 else oracle.prove_sumcheck_eq)(gate, n, d, cols)
         rec.update(proof_len=len(proof), proof_sha256=hashlib.sha256(proof).hexdigest())
     else:

@@ -2,8 +2,8 @@
 oracle's byte for byte at the workload sizes (Plonk n = 22 and 24, the
 product gate at n = 22 for every degree of the sweep d = 2..32, the served
 mix's n = 24 shapes, the sweep's 2N, 3N and 5N domains and the
-eq-factored proof at n = 22, two of the paper's polynomials at n = 22),
-both forms.
+eq-factored proof at n = 22, two of the paper's polynomials at n = 22,
+the commitment of the bench's n = 22 columns), both forms.
 
 The oracle's outputs at these sizes take it minutes, so they are stored as
 SHA-256 digests in ``golden/oracle_digests.jsonl``, written by
@@ -29,7 +29,7 @@ RECORDS = digests.load()
 
 def _ids(case):
     form, gate, n, d, lb, seed = case
-    return f"{ {1: 'sc', 2: 'ntt', 3: 'sceq'}[form]}-g{gate}-n{n}-d{d}" + (f"-lb{lb}" if lb else "")
+    return f"{ {1: 'sc', 2: 'ntt', 3: 'sceq', 5: 'pcs'}[form]}-g{gate}-n{n}-d{d}" + (f"-lb{lb}" if lb else "")
 
 
 @pytest.fixture(scope="module")
@@ -47,7 +47,15 @@ def test_config_size_matches_oracle(ctx, case):
     form, gate, n, d, lb, seed = case
     cols = to_device(witness.generate(gate, n, d, seed))
     try:
-        if form in (zc.ZC_FORM_SUMCHECK, zc.ZC_FORM_SUMCHECK_EQ):
+        if form == 5:  # the commitment: root and opening (t queries in the log_blowup slot)
+            com = ctx.pcs_commit(n, cols, lb)
+            try:
+                assert com.root.hex() == rec["root"], "commitment root differs from the oracle's"
+                alpha, values = digests.pcs_point(n, len(cols))
+                p = com.open(alpha, values)
+            finally:
+                com.close()
+        elif form in (zc.ZC_FORM_SUMCHECK, zc.ZC_FORM_SUMCHECK_EQ):
             p = proof_bytes(ctx.prove_sumcheck(gate, n, d, cols, eq_factored=form == zc.ZC_FORM_SUMCHECK_EQ))
         else:
             q = torch.zeros(rec["q_len"], dtype=torch.uint8, device="cuda")
