@@ -226,11 +226,15 @@ __device__ __forceinline__ void stockham_stage(const SmTile& sm, uint32_t logL, 
     const uint32_t k = j & ((1u << logNs) - 1);
     if (logNs > 0) {
       // the previous stage left its outputs lazy: x[0] is reduced, the
-      // others are reduced by their twiddle w_{Ns R}^{r k} = tab[r k 4096 / (Ns R)]
+      // others are reduced by their twiddle w_{Ns R}^{r k} = tab[r k 4096 / (Ns R)].
+      // These products, and the pass's load and store factors, use the
+      // inlined multiplier (fewer instructions than the shared call); the
+      // DFT-8's own products stay calls (inlined they spilled registers and
+      // measured slower).
       const uint32_t sh = 12 - (logNs + LR);
       x[g * R] = fr_reduce1(x[g * R]);
 #pragma unroll
-      for (int r = 1; r < R; r++) x[g * R + r] = fr_mul(ld_fr(tab + ((r * k) << sh)), x[g * R + r]);
+      for (int r = 1; r < R; r++) x[g * R + r] = fr_mul_inl(ld_fr(tab + ((r * k) << sh)), x[g * R + r]);
     }
     if (R == 8) {
       fr y[8];
@@ -287,7 +291,7 @@ __global__ void __launch_bounds__(TILE / 8, MINB) k_ntt_pass(NttPassArgs A) {
     fr x = ld_fr(in + a);
     if (A.err && !fr_is_canonical(x)) atomicOr(A.err, 1u);
     if (A.pre == PRE_TAB) {
-      x = fr_mul(x, ld_fr(A.pre_tab + b * A.pre_kb + t * A.pre_kt));
+      x = fr_mul_inl(ld_fr(A.pre_tab + b * A.pre_kb + t * A.pre_kt), x);
     } else if (A.pre == PRE_COSET) {
       const uint64_t k = b * A.pre_kb + t * A.pre_kt;
       // one slice per launch: every column uses the same tables
@@ -317,7 +321,7 @@ __global__ void __launch_bounds__(TILE / 8, MINB) k_ntt_pass(NttPassArgs A) {
     fr y = sm.get(t * W + w);  // lazily reduced: multiplied (as the second operand) or reduced here
     if (A.post == POST_TAB) {
       const uint64_t ti = (b >> A.p_lbdiv) * A.p_hs + (b & ((1ull << A.p_lbdiv) - 1)) * A.p_ls + t * A.p_ts;
-      y = fr_mul(ld_fr(A.post_tab + ti), y);
+      y = fr_mul_inl(ld_fr(A.post_tab + ti), y);
     } else if (A.post == POST_TW) {
       const uint64_t e = (b & ((1ull << A.tw_lbmod) - 1)) * t;
       const uint32_t ex = (uint32_t)((e << A.tw_shift) & ((1ull << kLog30) - 1));
