@@ -455,17 +455,17 @@ __global__ void __launch_bounds__(256) k_ntt_gate(NttGateArgs A) {
     if (A.gate == ZC_GATE_PLONK) {
       // a (qL + qM b) + qR b + qO c with one reduction for the three products
       const fr b = ld_fr(A.col[6] + p);
-      const fr u = fr_add(ld_fr(A.col[0] + p), fr_mul(ld_fr(A.col[2] + p), b));
+      const fr u = fr_add(ld_fr(A.col[0] + p), fr_mul_inl(ld_fr(A.col[2] + p), b));
       f = fr_mul_sum3(ld_fr(A.col[5] + p), u, ld_fr(A.col[1] + p), b, ld_fr(A.col[3] + p), ld_fr(A.col[7] + p));
       f = fr_add(f, ld_fr(A.col[4] + p));
     } else {
       f = ld_fr(A.col[0] + p);
-      for (uint32_t j = 1; j < A.d; j++) f = fr_mul(f, ld_fr(A.col[j] + p));
+      for (uint32_t j = 1; j < A.d; j++) f = fr_mul_inl(f, ld_fr(A.col[j] + p));
       if (A.gate == ZC_GATE_PRODUCT) f = fr_sub(f, ld_fr(A.col[A.d] + p));
       else
         for (uint32_t j = A.d; j < A.c; j++) f = fr_add(f, ld_fr(A.col[j] + p));
     }
-    f = fr_mul(f, zi);
+    f = fr_mul_inl(zi, f);
     if (A.sub) f = fr_sub(f, ld_fr(A.sub + p));
     st_fr(A.qhat + p, f);
   }
@@ -609,7 +609,7 @@ __global__ void __launch_bounds__(256) k_ntt_open(NttOpenArgs A, const DevConst*
       // while the warp's accumulators and values are all zero (the zero top
       // of an honest quotient) the step would multiply zeros: skip it
       if (__all_sync(0xffffffffu, fr_is_zero(acc) && fr_is_zero(xk))) continue;
-      acc = fr_add(fr_mul(acc, z32), xk);
+      acc = fr_add(fr_mul_inl(z32, acc), xk);
     }
     if (__all_sync(0xffffffffu, fr_is_zero(acc))) continue;
     acc = fr_mul(acc, zpow_of(A.zpow, base + lane, C->one));
