@@ -282,6 +282,38 @@ __global__ void __launch_bounds__(TILE / 8, MINB) k_ntt_pass(NttPassArgs A) {
   const uint64_t in_bdiv_mask = (1ull << A.in_lbdiv) - 1, out_bdiv_mask = (1ull << A.out_lbdiv) - 1;
 
   // ---- load (with the coset factor when asked)
+  if (A.pre == PRE_NONE && n_el == (uint32_t)TILE) {
+    // no factor to apply: both 16-byte halves of every element go straight
+    // from global to their planes (cp.async, no register staging), all of
+    // this thread's copies in flight together
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const uint32_t idx = threadIdx.x + (uint32_t)u * (TILE / 8);
+      uint32_t w, t;
+      if (in_t_fast) { t = idx & (L - 1); w = idx >> logL; }
+      else { w = idx & (W - 1); t = idx >> logW; }
+      const uint64_t b = b0 + w;
+      const uint64_t a = (b >> A.in_lbdiv) * A.in_bs_hi + (b & in_bdiv_mask) * A.in_bs_lo + t * A.in_ts;
+      const uint32_t s = sm.sw(t * W + w);
+      const uint32_t d0 = (uint32_t)__cvta_generic_to_shared(sm.p + s);
+      const uint32_t d1 = (uint32_t)__cvta_generic_to_shared(sm.p + TILE + s);
+      const char* g = reinterpret_cast<const char*>(in + a);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d0), "l"(g) : "memory");
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d1), "l"(g + 16) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    if (A.err) {
+      // the input check reads back what this thread copied
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        const uint32_t idx = threadIdx.x + (uint32_t)u * (TILE / 8);
+        uint32_t w, t;
+        if (in_t_fast) { t = idx & (L - 1); w = idx >> logL; }
+        else { w = idx & (W - 1); t = idx >> logW; }
+        if (!fr_is_canonical(sm.get(t * W + w))) atomicOr(A.err, 1u);
+      }
+    }
+  } else
   for (uint32_t idx = threadIdx.x; idx < n_el; idx += blockDim.x) {
     uint32_t w, t;
     if (in_t_fast) { t = idx & (L - 1); w = idx >> logL; }
