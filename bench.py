@@ -617,6 +617,9 @@ def run_pcs(args, world, rank, local):
 
     for _ in range(W):
         ctx.pcs_commit(n, dcols, t, stream=stream).close()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
     cms = []
     for _ in range(K):
         ms, com = timed(lambda: ctx.pcs_commit(n, dcols, t, stream=stream), 1)
@@ -632,6 +635,7 @@ def run_pcs(args, world, rank, local):
     zc.sumcheck_point(GATE, n, DEG, 1, roots, pb)  # first call builds the host constants
     pt_ms, (alpha, vals, ok) = timed(lambda: zc.sumcheck_point(GATE, n, DEG, 1, roots, pb), K)
     open_ms, pr = timed(lambda: com.open(alpha, vals, stream=stream), K)
+    clk = clocks.stop()
     t0 = time.perf_counter()
     accept = zc.pcs_verify(n, c, t, com.root, alpha, vals, pr)
     verify_ms = (time.perf_counter() - t0) * 1e3
@@ -648,6 +652,7 @@ def run_pcs(args, world, rank, local):
     line["sizes_bytes"] = {"columns": c * N * 32, "encoded": 4 * c * N * 32, "opening_proof": len(pr),
                            "sumcheck_proof": len(pb)}
     line["verified"] = bool(accept and ok)
+    line["clocks"] = clk
     line["device"] = device_info
     line["e2e"] = None
     if rank == 0:
