@@ -137,6 +137,21 @@ __device__ __forceinline__ fr ldx(const fr* p) {
   return COHERENT ? ld_fr_l2(p) : ld_fr(p);
 }
 
+// table reads of a large round: each value is read once, so its lines are
+// the first L2 evicts (ld.global.cs)
+__device__ __forceinline__ fr ld_fr_cs(const fr* p) {
+  const uint4* q = reinterpret_cast<const uint4*>(p);
+  uint4 a = __ldcs(q), b = __ldcs(q + 1);
+  fr x;
+  x.v[0] = a.x; x.v[1] = a.y; x.v[2] = a.z; x.v[3] = a.w;
+  x.v[4] = b.x; x.v[5] = b.y; x.v[6] = b.z; x.v[7] = b.w;
+  return x;
+}
+template <bool COHERENT>
+__device__ __forceinline__ fr ldt(const fr* p) {
+  return COHERENT ? ld_fr_l2(p) : ld_fr_cs(p);
+}
+
 // small integer t times x by double-and-add, additions only.  The lanes of a
 // warp may hold different t, so the loop starts at the highest bit set in
 // any of them: a warp whose t are at most 6 runs two steps, not seven.
@@ -369,8 +384,8 @@ __device__ __forceinline__ void plonk_pair(const fr* const* src, fr* const* dst,
   auto column = [&](int j, fr (&v)[NF], fr& dl) {
     fr lo, hi;
     if (FIRST) {
-      lo = ldx<COHERENT>(src[j] + k);
-      hi = ldx<COHERENT>(src[j] + k + h);
+      lo = ldt<COHERENT>(src[j] + k);
+      hi = ldt<COHERENT>(src[j] + k + h);
       bad |= (!fr_is_canonical(lo)) | (!fr_is_canonical(hi));
       if (j >= 5) {
         lo = to_mont(lo, C);
@@ -379,8 +394,8 @@ __device__ __forceinline__ void plonk_pair(const fr* const* src, fr* const* dst,
         st_fr(dst[j] + k + h, hi);
       }
     } else {
-      const fr x0 = ldx<COHERENT>(src[j] + k), x1 = ldx<COHERENT>(src[j] + k + 2 * h);
-      const fr y0 = ldx<COHERENT>(src[j] + k + h), y1 = ldx<COHERENT>(src[j] + k + 3 * h);
+      const fr x0 = ldt<COHERENT>(src[j] + k), x1 = ldt<COHERENT>(src[j] + k + 2 * h);
+      const fr y0 = ldt<COHERENT>(src[j] + k + h), y1 = ldt<COHERENT>(src[j] + k + 3 * h);
       lo = fr_add(x0, fr_mul(alpha, fr_sub(x1, x0)));
       hi = fr_add(y0, fr_mul(alpha, fr_sub(y1, y0)));
       st_fr(dst[j] + k, lo);
@@ -507,8 +522,8 @@ __device__ __forceinline__ void prod_pair(const ScRoundArgs& A, const fr* const*
   prod_pair_g<PP>(
       A,
       [&](int j, fr& lo, fr& hi) {
-        lo = ldx<COHERENT>(col[j] + k);
-        hi = ldx<COHERENT>(col[j] + k + h);
+        lo = ldt<COHERENT>(col[j] + k);
+        hi = ldt<COHERENT>(col[j] + k + h);
       },
       pcnt, tpt, first, w, acc, bad);
 }
@@ -556,7 +571,7 @@ __device__ __forceinline__ void plonk_chunk(PlonkChunkSmem<PB>& S, const fr* con
     const int j = item >> 1, half = item & 1;
     const uint64_t e = k + (half ? h : 0);
     if (live) {
-      const fr x0 = ldx<COHERENT>(src[j] + e), x1 = ldx<COHERENT>(src[j] + e + 2 * h);
+      const fr x0 = ldt<COHERENT>(src[j] + e), x1 = ldt<COHERENT>(src[j] + e + 2 * h);
       const fr v = fr_add(x0, fr_mul(alpha, fr_sub(x1, x0)));
       st_fr(dst[j] + e, v);
       S.V[j][half][p] = v;
@@ -841,7 +856,7 @@ __global__ void __launch_bounds__(256) k_sc_fold(ScFoldArgs A) {
        e += (uint64_t)gridDim.x * blockDim.x) {
     const int j = (int)(e / A.h);
     const uint64_t k = e - (uint64_t)j * A.h;
-    const fr x0 = ld_fr(A.src[j] + k), x1 = ld_fr(A.src[j] + k + A.h);
+    const fr x0 = ld_fr_cs(A.src[j] + k), x1 = ld_fr_cs(A.src[j] + k + A.h);
     st_fr(A.dst[j] + k, fr_add(x0, fr_mul(alpha, fr_sub(x1, x0))));
   }
 }
@@ -944,7 +959,7 @@ __global__ void __launch_bounds__(256, 2) k_sc_prod_fused(ScRoundArgs A) {
       const uint64_t k = kb + p;
       if (k < h) {
         const uint64_t idx = k + (half ? h : 0);
-        const fr x0 = ld_fr(A.src[j] + idx), x1 = ld_fr(A.src[j] + idx + 2 * h);
+        const fr x0 = ld_fr_cs(A.src[j] + idx), x1 = ld_fr_cs(A.src[j] + idx + 2 * h);
         const fr v = fr_add(x0, fr_mul(alpha, fr_sub(x1, x0)));
         st_fr(A.dst[j] + idx, v);
         Vs[(size_t)rest * spb + p] = v;
