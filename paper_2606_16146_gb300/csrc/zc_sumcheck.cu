@@ -51,6 +51,11 @@ constexpr uint64_t kFusePairsProd = 1ull << 16;    // product rounds 2.. with at
 constexpr int kPP = 3;  // product gate: points per thread
 constexpr int kSmallPB = 16;  // pairs per chunk of the 16-threads-per-pair kernel (256 threads)
 constexpr int kQuadPB = 32;   // pairs per chunk of the 4-threads-per-pair kernel (128 threads)
+constexpr int kBigPB = 64;    // ... in the cooperative kernel's rounds above small_pairs (256 threads)
+// From this n on the cooperative round kernel also takes the 4-threads-per-pair
+// rounds (measured: n = 20 1.452 -> 1.430 ms, n = 22 3.601 -> 3.585 ms; at
+// n = 18 their separate launches are faster, 0.795 against 0.805 ms).
+constexpr uint32_t kCoopQuadMinN = 20;
 constexpr int kTailPB = 32;   // pairs per chunk in the tail (512 threads)
 constexpr int kTailThreads = 16 * kTailPB;
 
@@ -99,6 +104,7 @@ struct ScRoundArgs {
   uint32_t next_derives;  // the next round derives a point: keep the claim
   uint32_t v2;         // eq-factored proof: rounds carry H_i(0..d), not G_i(0..d+1)
   int round_end;       // persistent round kernel: rounds [round, round_end)
+  uint64_t small_pairs;  // ... rounds with more pairs derive a point, 4 threads per pair
   uint32_t spin_limit; // persistent round kernel: polls of a hand-off before giving up
   uint64_t k0, k1;     // round 1 in pair-range launches: pairs [k0, k1) (k1 = 0: all h)
   uint32_t cta0;       // ... this launch's first partial-sum slot
@@ -789,17 +795,26 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
   return v;
 }
 
-// Plonk rounds [A.round, A.round_end) (16 threads per pair, every point
-// evaluated) in one cooperative launch, so the latency-bound rounds pay no
-// launch between them.  Each CTA folds and evaluates its chunks of a round
-// and writes its partial sums; the last CTA to arrive sums them, runs the
-// challenge and releases the next round through st->go.  The other CTAs poll
-// st->go at most A.spin_limit times; a CTA that gives up sets bit 1 of
-// st->err and returns, after which every later hand-off also gives up, so
-// the launch always ends and the proof reports the timeout.  Tables are read
-// through L2: other CTAs rewrote them in the previous round.
+// Plonk rounds [A.round, A.round_end) in one cooperative launch, so the
+// latency-bound rounds pay no launch between them and their challenge code
+// stays warm.  Rounds with more than A.small_pairs pairs take 4 threads per
+// pair and derive one of H(0), H(1) from the claim (as k_sc_plonk_chunk<4,
+// 32>); smaller ones take 16 threads per pair and evaluate every point.
+// Each CTA folds and evaluates its chunks of a round and writes its partial
+// sums; the last CTA to arrive sums them, runs the challenge and releases the
+// next round through st->go.  The other CTAs poll st->go at most
+// A.spin_limit times; a CTA that gives up sets bit 1 of st->err and returns,
+// after which every later hand-off also gives up, so the launch always ends
+// and the proof reports the timeout.  Tables are read through L2: other CTAs
+// rewrote them in the previous round.  Dynamic shared memory: kRoundsDyn.
+constexpr size_t kRoundsDyn = sizeof(PlonkChunkSmem<kBigPB>) > sizeof(PlonkChunkSmem<kSmallPB>)
+                                  ? sizeof(PlonkChunkSmem<kBigPB>)
+                                  : sizeof(PlonkChunkSmem<kSmallPB>);
 __global__ void __launch_bounds__(16 * kSmallPB) k_sc_plonk_rounds(ScRoundArgs A) {
-  __shared__ PlonkChunkSmem<kSmallPB> S;
+  static_assert(4 * kBigPB == 16 * kSmallPB, "both chunk shapes fill the CTA");
+  extern __shared__ __align__(16) unsigned char rounds_smem[];
+  auto& S = *reinterpret_cast<PlonkChunkSmem<kSmallPB>*>(rounds_smem);
+  auto& SB = *reinterpret_cast<PlonkChunkSmem<kBigPB>*>(rounds_smem);
   __shared__ fr part[4];
   __shared__ ChalSmem CS;
   __shared__ int flag;  // 1: this CTA runs the challenge; 2: a wait gave up
@@ -807,17 +822,29 @@ __global__ void __launch_bounds__(16 * kSmallPB) k_sc_plonk_rounds(ScRoundArgs A
   const uint64_t N = 1ull << A.n;
   for (int i = A.round; i < A.round_end; i++) {
     const uint64_t h = N >> (i + 1);
-    const uint32_t nwork = (uint32_t)min((h + kSmallPB - 1) / kSmallPB, (uint64_t)G);
+    const bool big = h > A.small_pairs;
+    const int np = big ? 3 : 4;
+    const uint64_t pb = big ? kBigPB : kSmallPB;
+    const uint32_t nwork = (uint32_t)min((h + pb - 1) / pb, (uint64_t)G);
     const fr alpha = ld_fr_l2(&A.st->alpha[i - 1]);
+    const fr* const* src = i == A.round ? (const fr* const*)A.src : (const fr* const*)A.dst;
     fr acc = fr_zero();
-    if (blockIdx.x < nwork)
-      for (uint64_t kb = (uint64_t)blockIdx.x * kSmallPB; kb < h; kb += (uint64_t)nwork * kSmallPB)
-        plonk_chunk<kSmallPB, 16, true, true>(
-            S, i == A.round ? (const fr* const*)A.src : (const fr* const*)A.dst, A.dst, h, kb, alpha, 0u,
-            A.E + A.eq_hi[i], A.E + A.eq_lo[i], A.m_lo[i], acc);
-    plonk_chunk_reduce<kSmallPB, 4>(acc, part);
-    if (blockIdx.x < nwork && threadIdx.x < 4)
-      st_fr(A.partials + (size_t)blockIdx.x * 4 + threadIdx.x, part[threadIdx.x]);
+    if (big) {
+      const uint32_t p0 = A.st->p0[i];
+      if (blockIdx.x < nwork)
+        for (uint64_t kb = (uint64_t)blockIdx.x * kBigPB; kb < h; kb += (uint64_t)nwork * kBigPB)
+          plonk_chunk<kBigPB, 4, false, true>(SB, src, A.dst, h, kb, alpha, p0, A.E + A.eq_hi[i],
+                                               A.E + A.eq_lo[i], A.m_lo[i], acc);
+      plonk_chunk_reduce<kBigPB, 3>(acc, part);
+    } else {
+      if (blockIdx.x < nwork)
+        for (uint64_t kb = (uint64_t)blockIdx.x * kSmallPB; kb < h; kb += (uint64_t)nwork * kSmallPB)
+          plonk_chunk<kSmallPB, 16, true, true>(S, src, A.dst, h, kb, alpha, 0u, A.E + A.eq_hi[i],
+                                                A.E + A.eq_lo[i], A.m_lo[i], acc);
+      plonk_chunk_reduce<kSmallPB, 4>(acc, part);
+    }
+    if (blockIdx.x < nwork && (int)threadIdx.x < np)
+      st_fr(A.partials + (size_t)blockIdx.x * np + threadIdx.x, part[threadIdx.x]);
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
@@ -827,8 +854,10 @@ __global__ void __launch_bounds__(16 * kSmallPB) k_sc_plonk_rounds(ScRoundArgs A
     __syncthreads();
     if (flag == 1) {
       __threadfence();
-      sc_sum_partials(CS, A.partials, nwork, 4);
-      sc_challenge<false>(CS, 4, 3, i, A.st, A.proof, A.C, A.tabs, false, A.v2 != 0, &A.st->go);
+      sc_sum_partials(CS, A.partials, nwork, np);
+      // the next round needs the claim when it derives a point too
+      sc_challenge<false>(CS, np, 3, i, A.st, A.proof, A.C, A.tabs, h / 2 > A.small_pairs, A.v2 != 0,
+                          &A.st->go);
     } else {
       if (threadIdx.x == 0) {
         uint32_t polls = 0;
@@ -1130,6 +1159,7 @@ static void ensure_prod_fused_attr() {
   if (dev < 0 || dev >= 64 || done[dev]) return;
   cudaFuncSetAttribute(k_sc_prod_fused<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
   cudaFuncSetAttribute(k_sc_prod_fused<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 << 10);
+  cudaFuncSetAttribute(k_sc_plonk_rounds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRoundsDyn);
   done[dev] = true;
 }
 
@@ -1146,7 +1176,7 @@ static int prod_ppt(int forced, int np, uint64_t h) {
 }
 
 // Resident CTAs per SM of a kernel on the current device (cached).
-static int resident_ctas(const void* fn, int threads = 256) {
+static int resident_ctas(const void* fn, int threads = 256, size_t dyn = 0) {
   static std::mutex mu;
   static std::vector<std::pair<std::pair<int, const void*>, int>> cache;
   int dev = 0;
@@ -1155,7 +1185,7 @@ static int resident_ctas(const void* fn, int threads = 256) {
   for (auto& e : cache)
     if (e.first.first == dev && e.first.second == fn) return e.second;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, 0) != cudaSuccess || nb < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, dyn) != cudaSuccess || nb < 1) {
     cudaGetLastError();
     nb = 1;
   }
@@ -1189,7 +1219,7 @@ static ScPlan sc_plan(const zc_params* p, int SMs, int grid = 0, int tail_log = 
   P.small_pairs = small_log > 0 ? 1ull << small_log : kSmallPairsPlonk;
   P.chunk_pairs = chunk_log > 0 ? 1ull << chunk_log : kChunkPairsPlonk;
   P.grid_chunk = SMs * resident_ctas(reinterpret_cast<const void*>(k_sc_plonk_chunk<16, kSmallPB, false>));
-  P.grid_rounds = SMs * resident_ctas(reinterpret_cast<const void*>(k_sc_plonk_rounds), 16 * kSmallPB);
+  P.grid_rounds = SMs * resident_ctas(reinterpret_cast<const void*>(k_sc_plonk_rounds), 16 * kSmallPB, kRoundsDyn);
   P.quad_pairs = quad_log > 0 ? 1ull << quad_log : kQuadPairsPlonk;
   P.grid_quad = SMs * resident_ctas(reinterpret_cast<const void*>(k_sc_plonk_chunk<4, kQuadPB, false>), 4 * kQuadPB);
   P.minb = minb == 1 ? 1 : 2;
@@ -1366,19 +1396,22 @@ static zc_status sc_enqueue(const zc_params* p, const ScPlan& P, const fr* const
       R.src[j] = cur[j];
       R.dst[j] = B.tab[j];
     }
-    if (plonk && i > 0 && h <= P.chunk_pairs && persistent && R.full && h / 2 > tail_pairs) {
+    const uint64_t coop_max = n >= kCoopQuadMinN ? std::max(P.chunk_pairs, P.quad_pairs) : P.chunk_pairs;
+    if (plonk && i > 0 && h <= coop_max && persistent && (R.full || n >= kCoopQuadMinN) && h / 2 > tail_pairs) {
       // every remaining round before the tail in one cooperative launch
-      // (all of them evaluate every point: h only shrinks)
+      // (those above small_pairs derive a point, the others evaluate every point)
       uint32_t end = i;
       while (end < n && (N >> (end + 1)) > tail_pairs) end++;
       R.round_end = (int)end;
       R.spin_limit = persistent_spin_limit();
+      R.small_pairs = P.small_pairs;
+      const uint64_t pb0 = h > P.small_pairs ? (uint64_t)kBigPB : (uint64_t)kSmallPB;
       const uint32_t G = (uint32_t)std::min<uint64_t>(
-          std::min<uint64_t>((h + kSmallPB - 1) / kSmallPB, (uint64_t)P.grid_chunk), (uint64_t)P.grid_rounds);
+          std::min<uint64_t>((h + pb0 - 1) / pb0, (uint64_t)P.grid_chunk), (uint64_t)P.grid_rounds);
       R.nwork = G;
       void* kargs[] = {&R};
       if (G >= 2 && cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k_sc_plonk_rounds), dim3(G),
-                                                dim3(16 * kSmallPB), kargs, 0, st) == cudaSuccess) {
+                                                dim3(16 * kSmallPB), kargs, kRoundsDyn, st) == cudaSuccess) {
         for (int j = 0; j < 8; j++) cur[j] = B.tab[j];
         *launches += 1;
         i = end;
