@@ -417,7 +417,10 @@ zc_status zc_serve(zc_ctx* ctx, const zc_request* reqs, uint32_t count, const zc
  *                        from the claim; 1..24, default 14.
  *   ZC_TUNE_SC_CHUNK_LOG SumCheck, Plonk gate: rounds 2.. with at most 2^value
  *                        pairs spread each pair over 16 threads; 1..24,
- *                        default 14.
+ *                        default 14.  From n = 20 on, the rounds inside the
+ *                        cooperative round kernel take 16 threads per pair
+ *                        when they evaluate both H(0) and H(1)
+ *                        (ZC_TUNE_SC_SMALL_LOG) and 4 otherwise.
  *   ZC_TUNE_SC_MINB      SumCheck, Plonk gate: resident CTAs per SM the large
  *                        round kernels are compiled for; 1 or 2, default 2.
  *   ZC_TUNE_SC_PROD_PPT  SumCheck, product gate: evaluation points per thread
@@ -427,7 +430,8 @@ zc_status zc_serve(zc_ctx* ctx, const zc_request* reqs, uint32_t count, const zc
  *   ZC_TUNE_SC_QUAD_LOG  SumCheck, Plonk gate: rounds 2.. above the chunk
  *                        threshold with at most 2^value pairs spread each pair
  *                        over 4 threads (larger rounds: one pair per thread);
- *                        1..24, default 17.
+ *                        from n = 20 on they run inside the cooperative round
+ *                        kernel; 1..24, default 17.
  *   ZC_TUNE_SC_PROD_FUSE SumCheck, product gate: rounds 2.. with at most
  *                        2^value pairs fold inside the evaluation kernel
  *                        (larger rounds: a separate MLE-update kernel);
